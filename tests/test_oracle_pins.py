@@ -1,0 +1,373 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed form,
+an invariant, a textbook/library routine, brute force on a tiny grid, or numbers
+the paper prints.  A plausible slip in the oracle (a dropped term, a wrong sign or
+index, a transposed operand) fails at least one of them.
+"""
+import numpy as np
+import numpy.polynomial.chebyshev as npcheb
+import pytest
+
+import thermal_inputs as ti
+from oracle import adjoint, discretisation as disc, krylov, solve
+from conftest import read_golden
+
+
+def uniform_power(stack, nx, ny, q_wcm2=20.0):
+    dens = [np.full((ny, nx), q_wcm2) for _ in stack.power_layers()]
+    return ti.power_cells(stack, nx, ny, dens, np.float64)
+
+
+# ----------------------------------------------------------------- discretisation
+
+@pytest.mark.parametrize("nx,ny", [(8, 8), (5, 3), (1, 1)])
+@pytest.mark.parametrize("half", [False, True])
+def test_slab_golden_c1(nx, ny, half):
+    """Eq. (steady-state) on a laterally uniform slab equals the hand-derived layer temperatures."""
+    rows = read_golden("slab_c1_uniform.txt")
+    want = {r[0]: float(r[2] if half else r[1]) for r in rows}
+    st = ti.stack_c1()
+    T = solve.steady(nx, ny, st, uniform_power(st, nx, ny), half_cell_top=half)
+    T = T.reshape(st.L, ny, nx)
+    for l, layer in enumerate(st.layers):
+        name = {"si": "si", "beol": "beol", "tim": "tim", "cu": "cu"}[layer.name]
+        np.testing.assert_allclose(T[l], want[name], rtol=1e-10, atol=0)
+
+
+def test_slab_series_closed_form_multi_source():
+    """Two powered layers (8-layer stack): column temperatures from the series-resistance chain.
+
+    theta_top = Q_total/(h S); crossing the face between layers l and l+1 downwards adds
+    (power generated in layers <= l) / g_{l,l+1}.
+    """
+    st = ti.stack_c2()
+    nx, ny = 4, 3
+    T = solve.steady(nx, ny, st, uniform_power(st, nx, ny, 37.0)).reshape(st.L, ny, nx)
+    S = st.dx * st.dy
+    Q = np.zeros(st.L)
+    for l in st.power_layers():
+        Q[l] = 37.0 * 1e4 * S
+    theta = np.zeros(st.L)
+    theta[-1] = Q.sum() / (st.h * S)
+    for l in range(st.L - 2, -1, -1):
+        a, b = st.layers[l], st.layers[l + 1]
+        R = a.thickness / (2 * a.k * S) + b.thickness / (2 * b.k * S)
+        theta[l] = theta[l + 1] + Q[: l + 1].sum() * R
+    for l in range(st.L):
+        np.testing.assert_allclose(T[l] - st.t_amb, theta[l], rtol=1e-10)
+
+
+def _bruteforce_apply(nx, ny, stack, x, dt=None):
+    """Face-by-face application of Eq. (steady-state)/(transient) in pure Python loops.
+
+    Enumerates every interior face once and adds g (x_a - x_b) to a and g (x_b - x_a)
+    to b, then the convective and capacity terms: a second, loop-based statement of
+    the discretisation that shares nothing with the row-wise CSR assembly.
+    """
+    L = stack.L
+    dx, dy = stack.dx, stack.dy
+    y = np.zeros(nx * ny * L)
+    ks = [l.k for l in stack.layers]
+    dzs = [l.thickness for l in stack.layers]
+
+    def at(x_, y_, z_):
+        return x_ + nx * (y_ + ny * z_)
+
+    for z in range(L):
+        for j in range(ny):
+            for i in range(nx):
+                a = at(i, j, z)
+                if i + 1 < nx:
+                    g = ks[z] * dy * dzs[z] / dx
+                    b = at(i + 1, j, z)
+                    y[a] += g * (x[a] - x[b]); y[b] += g * (x[b] - x[a])
+                if j + 1 < ny:
+                    g = ks[z] * dx * dzs[z] / dy
+                    b = at(i, j + 1, z)
+                    y[a] += g * (x[a] - x[b]); y[b] += g * (x[b] - x[a])
+                if z + 1 < L:
+                    g = dx * dy / (dzs[z] / (2 * ks[z]) + dzs[z + 1] / (2 * ks[z + 1]))
+                    b = at(i, j, z + 1)
+                    y[a] += g * (x[a] - x[b]); y[b] += g * (x[b] - x[a])
+                if z == L - 1:
+                    y[a] += stack.h * dx * dy * x[a]
+                if dt is not None:
+                    y[a] += stack.layers[z].c * dx * dy * dzs[z] / dt * x[a]
+    return y
+
+
+@pytest.mark.parametrize("nx,ny,mk", [(3, 2, "c1"), (4, 5, "c2"), (1, 3, "mol")])
+@pytest.mark.parametrize("dt", [None, 1e-4])
+def test_assembly_matches_bruteforce(nx, ny, mk, dt):
+    st = {"c1": ti.stack_c1(), "c2": ti.stack_c2(), "mol": ti.stack_mol()}[mk]
+    A = disc.assemble(nx, ny, st, dt=dt)
+    x = ti.random_vector(A.shape[0], 7)
+    np.testing.assert_allclose(A @ x, _bruteforce_apply(nx, ny, st, x, dt), rtol=1e-12, atol=1e-18)
+
+
+@pytest.mark.parametrize("dt", [None, 2e-4])
+def test_matrix_structure(dt):
+    """Symmetry, sign pattern, 7 diagonals (Sec. 3.2) and row sums A 1 = h S (+ C V/dt)."""
+    st = ti.stack_c2()
+    nx, ny = 6, 5
+    A = disc.assemble(nx, ny, st, dt=dt)
+    assert (abs(A - A.T)).max() == 0.0
+    off = A - __import__("scipy.sparse", fromlist=["diags"]).diags(A.diagonal())
+    assert off.max() <= 0.0
+    # at most 7 distinct diagonals: offsets 0, +-1, +-nx, +-nx*ny
+    coo = A.tocoo()
+    assert set(np.unique(coo.col - coo.row)) <= {0, 1, -1, nx, -nx, nx * ny, -nx * ny}
+    expect = disc.top_sink(nx, ny, st)
+    if dt is not None:
+        expect = expect + disc.capacity_over_dt(nx, ny, st, dt)
+    # rounding floor: a few ulps of the largest conductance in a row
+    np.testing.assert_allclose(A @ np.ones(A.shape[0]), expect, rtol=1e-12, atol=1e-15 * abs(A).max())
+    np.testing.assert_allclose(A.diagonal(), -np.asarray(off.sum(axis=1)).ravel() + expect, rtol=1e-14)
+
+
+def test_energy_balance_c1():
+    """Sum of injected power equals convective outflow sum_top h S theta (to 1e-9)."""
+    inst = ti.c1(dtype=np.float64)
+    st = inst.stack
+    T = solve.steady(inst.nx, inst.ny, st, inst.power)
+    top = T[(st.L - 1) * inst.nx * inst.ny:]
+    out = np.sum(st.h * st.dx * st.dy * (top - st.t_amb))
+    assert abs(out - inst.power.sum()) / inst.power.sum() < 1e-9
+
+
+def test_superposition_and_scaling():
+    st = ti.stack_c1()
+    nx, ny = 12, 9
+    p1 = ti.power_cells(st, nx, ny, [ti.density_uniform_hotspots(nx, ny, 3)], np.float64)
+    p2 = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, 4)], np.float64)
+    th = lambda p: solve.steady(nx, ny, st, p) - st.t_amb
+    np.testing.assert_allclose(th(p1 + p2), th(p1) + th(p2), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(th(2.5 * p1), 2.5 * th(p1), rtol=1e-10, atol=1e-12)
+
+
+def test_direct_paths_agree():
+    """Dense Cholesky, sparse LU and Algorithm 1 (Jacobi, 1e-13) give the same solution."""
+    st = ti.stack_c1()
+    nx, ny = 16, 16
+    A = disc.assemble(nx, ny, st)
+    b = disc.rhs_steady(nx, ny, st, ti.power_cells(st, nx, ny, [ti.density_uniform_hotspots(nx, ny, 5)]))
+    x_ch = solve.cholesky_solve(A, b)
+    x_lu = __import__("scipy.sparse.linalg", fromlist=["spsolve"]).spsolve(A.tocsc(), b)
+    x_cg, it, _, _ = krylov.pcg(krylov.CountingOp(A), b, krylov.jacobi(A), tol_rel=1e-14)
+    np.testing.assert_allclose(x_lu, x_ch, rtol=1e-12)
+    np.testing.assert_allclose(x_cg, x_ch, rtol=1e-11)
+
+
+# ----------------------------------------------------------------- Algorithm 1
+
+def test_pcg_finite_termination():
+    """CG on a matrix with m distinct eigenvalues terminates in m iterations (exact-arithmetic theory)."""
+    import scipy.sparse as sp
+    vals = np.repeat([1.0, 2.0, 5.0, 11.0, 30.0], 20)
+    A = sp.diags(vals).tocsr()
+    b = ti.random_vector(vals.size, 11)
+    x, it, hist, true_res = krylov.pcg(krylov.CountingOp(A), b, krylov.identity(), tol_rel=1e-12)
+    assert it == 5
+    np.testing.assert_allclose(x, b / vals, rtol=1e-10)
+
+
+def test_pcg_residual_history_monotone_energy():
+    """PCG error in the A-norm decreases monotonically (a defining property of CG)."""
+    st = ti.stack_c1()
+    nx, ny = 10, 10
+    A = disc.assemble(nx, ny, st)
+    b = ti.random_vector(A.shape[0], 3, lo=0.0, hi=1e-4)
+    xs = solve.cholesky_solve(A, b)
+    errs = []
+    for m in range(1, 25):
+        x, _, _, _ = krylov.pcg(krylov.CountingOp(A), b, krylov.jacobi(A), tol_rel=0.0, maxit=m)
+        e = x - xs
+        errs.append(e @ (A @ e))
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-9) for i in range(len(errs) - 1))
+
+
+def test_nspmv_convention_golden_and_oracle():
+    """The paper's N_SpMV equals (N_ite+1) k + N_ite + 2 for CUTh1-3, and the oracle counts the same way."""
+    for bench, n_ite, n_spmv, k in read_golden("nspmv_counts.txt"):
+        n_ite, n_spmv, k = int(n_ite), int(n_spmv), int(k)
+        assert (n_ite + 1) * k + n_ite + 2 == n_spmv, bench
+    st = ti.stack_c1()
+    nx, ny = 12, 12
+    A = disc.assemble(nx, ny, st)
+    b = disc.rhs_steady(nx, ny, st, uniform_power(st, nx, ny))
+    ev = np.linalg.eigvalsh(A.toarray())
+    op = krylov.CountingOp(A)
+    k = 30
+    prec = lambda r: krylov.chebyshev(op, r, ev[0], 1.05 * ev[-1], k)
+    x, n_ite, _, _ = krylov.pcg(op, b, prec, tol_rel=1e-12)
+    assert n_ite > 0
+    assert op.count == (n_ite + 1) * k + n_ite + 2
+
+
+# ----------------------------------------------------------------- Chebyshev
+
+def _cheb_closed(k, x):
+    """Textbook first-kind Chebyshev polynomial via numpy's Chebyshev series (coefficient e_k)."""
+    c = np.zeros(k + 1)
+    c[k] = 1.0
+    return npcheb.chebval(x, c)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 30])
+def test_chebyshev_spectral_closed_form(k):
+    """z = V diag((1 - P_k(l))/l) V^T r with P_k(l) = C_k((theta-l)/delta)/C_k(theta/delta) (Sec. 4.3)."""
+    st = ti.stack_c1()
+    nx, ny = 5, 4
+    A = disc.assemble(nx, ny, st)
+    lam, V = np.linalg.eigh(A.toarray())
+    lo, hi = lam[0] * 1.5, lam[-1] * 1.02
+    r = ti.random_vector(A.shape[0], 13)
+    z = krylov.chebyshev(krylov.CountingOp(A), r, lo, hi, k)
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    Pk = _cheb_closed(k, (theta - lam) / delta) / _cheb_closed(k, theta / delta)
+    z_ref = V @ (((1.0 - Pk) / lam) * (V.T @ r))
+    np.testing.assert_allclose(z, z_ref, rtol=1e-9, atol=1e-12 * np.abs(z_ref).max())
+    np.testing.assert_allclose(krylov.chebyshev_residual_poly(lam, lo, hi, k), Pk, rtol=1e-10, atol=1e-300)
+
+
+def test_chebyshev_minimax_level_and_spd():
+    """max_{[a,b]} |P_k| = 1/C_k(theta/delta); M^{-1} is SPD when lmax is over-estimated."""
+    a, b, k = 0.01, 2.0, 7
+    grid = np.linspace(a, b, 20001)
+    Pk = krylov.chebyshev_residual_poly(grid, a, b, k)
+    theta, delta = (a + b) / 2, (b - a) / 2
+    assert abs(np.abs(Pk).max() - 1.0 / np.cosh(k * np.arccosh(theta / delta))) < 1e-10
+    st = ti.stack_c1()
+    A = disc.assemble(4, 4, st)
+    lam = np.linalg.eigvalsh(A.toarray())
+    n = A.shape[0]
+    M = np.column_stack([krylov.chebyshev(krylov.CountingOp(A), e, lam[0] * 3, lam[-1] * 1.05, 6)
+                         for e in np.eye(n)])
+    np.testing.assert_allclose(M, M.T, atol=1e-8 * np.abs(M).max())
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+# ----------------------------------------------------------------- Lanczos
+
+def test_splitmix64_published_vector():
+    """SplitMix64 from state 0 gives 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F."""
+    outs = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    u = krylov.splitmix64_uniform(3, 0)
+    want = np.array([2.0 * ((o >> 11) / 2.0 ** 53) - 1.0 for o in outs])
+    np.testing.assert_array_equal(u, want)
+
+
+def test_lanczos_extremes_vs_eigvalsh():
+    st = ti.stack_c2()
+    nx, ny = 6, 6
+    A = disc.assemble(nx, ny, st, dt=1e-4)
+    lam = np.linalg.eigvalsh(A.toarray())
+    a, b = krylov.lanczos(krylov.CountingOp(A), krylov.splitmix64_uniform(A.shape[0], 1), 60)
+    lo, hi = krylov.ritz_extremes(a, b)
+    assert abs(hi - lam[-1]) / lam[-1] < 0.01
+    assert lo >= lam[0] * (1 - 1e-9)         # Ritz values lie inside the spectrum
+    # a full-length run (m = N) recovers the smallest eigenvalue as well
+    a, b = krylov.lanczos(krylov.CountingOp(A), krylov.splitmix64_uniform(A.shape[0], 1), A.shape[0])
+    lo_full, _ = krylov.ritz_extremes(a, b)
+    assert abs(lo_full - lam[0]) / lam[0] < 1e-6
+    # the Jacobi-scaled operator: its Ritz interval lies inside the spectrum of D^-1/2 A D^-1/2
+    opj, s = krylov.jacobi_scaled(A)
+    lamj = np.linalg.eigvalsh((s[:, None] * A.toarray()) * s[None, :])
+    a, b = krylov.lanczos(opj, krylov.splitmix64_uniform(A.shape[0], 1), 60)
+    lo, hi = krylov.ritz_extremes(a, b)
+    assert lamj[0] * (1 - 1e-9) <= lo and hi <= lamj[-1] * (1 + 1e-9)
+    assert abs(hi - lamj[-1]) / lamj[-1] < 0.01
+
+
+# ----------------------------------------------------------------- transient
+
+def test_transient_single_cell_closed_form():
+    """1x1x1 grid: T_{n+1} = (C V T_n/dt + P + h S T_amb) / (C V/dt + h S) (Eq. transient)."""
+    st = ti.Stack((ti.Layer("si", 100e-6, 150.0, 1.63e6, True),), h=1e4)
+    p, dt = 3e-4, 1e-3
+    sched = [np.array([p])] * 6
+    Ts = solve.transient(1, 1, st, sched, dt, np.array([st.t_amb]))
+    CV = 1.63e6 * st.dx * st.dy * 100e-6
+    hS = st.h * st.dx * st.dy
+    T = st.t_amb
+    for Tn in Ts:
+        T = (CV * T / dt + p + hS * st.t_amb) / (CV / dt + hS)
+        assert abs(Tn[0] - T) < 1e-12
+
+
+def test_transient_energy_balance_and_steady_limit():
+    st = ti.stack_c2()
+    nx, ny = 8, 6
+    dt = 1e-4
+    P = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (1, 2)], np.float64)
+         for _ in range(3)]
+    T0 = np.full(nx * ny * st.L, st.t_amb)
+    Ts = solve.transient(nx, ny, st, P, dt, T0)
+    cdt = disc.capacity_over_dt(nx, ny, st, dt)
+    sink = disc.top_sink(nx, ny, st)
+    prev = T0
+    for T, p in zip(Ts, P):
+        lhs = np.sum(cdt * (T - prev)) + np.sum(sink * (T - st.t_amb))
+        assert abs(lhs - p.sum()) / p.sum() < 1e-10
+        prev = T
+    # dt -> infinity reduces Eq. (transient) to Eq. (steady-state)
+    Tinf = solve.transient(nx, ny, st, P[:1], 1e12, T0)[0]
+    np.testing.assert_allclose(Tinf, solve.steady(nx, ny, st, P[0]), rtol=1e-9)
+
+
+# ----------------------------------------------------------------- adjoint
+
+def _small_case():
+    st = ti.stack_c1()
+    nx, ny = 10, 8
+    p = ti.power_cells(st, nx, ny, [ti.density_uniform_hotspots(nx, ny, 9, dx=st.dx, dy=st.dy)], np.float64)
+    mask = adjoint.silicon_mask(nx, ny, st, st.power_layers())
+    return st, nx, ny, p, mask
+
+
+def test_adjoint_vs_central_differences():
+    st, nx, ny, p, mask = _small_case()
+    beta = 2.0
+    J, dJdP, dJdk, dJdh, lam = adjoint.gradient(nx, ny, st, p, mask, beta)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(p.size, 8, replace=False):
+        h = 1e-3 * max(abs(p[i]), 1e-4)
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (adjoint.objective(nx, ny, st, pp, mask, beta) - adjoint.objective(nx, ny, st, pm, mask, beta)) / (2 * h)
+        assert abs(fd - dJdP[i]) <= 1e-4 * abs(dJdP[i]) + 1e-9
+    k = st.k()
+    for l in range(st.L):
+        h = 1e-3 * k[l]
+        kp, km = k.copy(), k.copy()
+        kp[l] += h
+        km[l] -= h
+        fd = (adjoint.objective(nx, ny, st.with_k(kp), p, mask, beta)
+              - adjoint.objective(nx, ny, st.with_k(km), p, mask, beta)) / (2 * h)
+        assert abs(fd - dJdk[l]) <= 1e-4 * abs(dJdk[l]) + 1e-12, (l, fd, dJdk[l])
+
+
+def test_adjoint_invariants():
+    """sum_top h S lambda = sum w = 1 (since A^T 1 = h S e_top); Euler homogeneity in (k, h)."""
+    st, nx, ny, p, mask = _small_case()
+    beta = 2.0
+    J, dJdP, dJdk, dJdh, lam = adjoint.gradient(nx, ny, st, p, mask, beta)
+    sink = disc.top_sink(nx, ny, st)
+    assert abs(np.sum(sink * lam) - 1.0) < 1e-10
+    T = solve.steady(nx, ny, st, p)
+    _, w = adjoint.lse(T, mask, beta)
+    # theta(s k, s h) = theta / s  =>  sum_l k_l dJ/dk_l + h dJ/dh = -sum_i w_i theta_i
+    lhs = np.sum(st.k() * dJdk) + st.h * dJdh
+    rhs = -np.sum(w * (T - st.t_amb))
+    assert abs(lhs - rhs) < 1e-9 * abs(rhs)
+
+
+def test_lse_properties():
+    T = np.array([1.0, 3.0, 2.0, 100.0])
+    mask = np.array([True, True, True, False])
+    J, w = adjoint.lse(T, mask, 2.0)
+    assert 3.0 < J < 3.0 + np.log(3) / 2.0
+    assert w[3] == 0.0 and abs(w.sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(J, np.log(np.sum(np.exp(2.0 * T[:3]))) / 2.0, rtol=1e-15)
