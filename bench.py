@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: time to 1e-8 relative residual per backward-Euler step at 8.4M DOF.
+
+Workload (synthetic, seeded): 1024 x 1024 cells x 8 layers (8,388,608 unknowns),
+two stacked Si dies (100um Si + 10um bond each), TIM 25um and a 1mm Cu spreader in
+three sublayers; 50um cells; h = 1e4 W/m^2K to 45 C; dt = 1e-4 s; 100 steps from
+45 C; four random block floorplans (64 rectangles + 16 Gaussian hotspots on each Si
+layer, seeds 30-33) switched every 25 steps.  Every step is solved to
+||b - A theta|| <= 1e-8 ||b|| (FP64) with FP32 Chebyshev-preconditioned PCG inside
+FP64 iterative refinement, the whole 100-step loop replayed as one CUDA graph with
+device-side loop control.  The plain FP64 GPU path (FP64 PCG, same preconditioner)
+is timed on the same trajectory.
+
+One bench step = one full 100-step trajectory.  `value` = ms per time step.
+Inputs (about 1 GB of FP32/FP64 arrays) exceed the 129 MB L2, so no L2 flush is
+needed between steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel. residual (8.4M DOF) & stencil HBM GB/s, mixed vs FP64 GPU"
+UNIT = "ms per backward-Euler step (8.4M DOF, rel. residual 1e-8)"
+NX = NY = 1024
+DT = 1e-4
+N_STEPS = 100
+STEPS_PER_MAP = 25
+SEEDS = (30, 31, 32, 33)
+
+# algorithmic bytes per cell of each timed kernel (reads + writes it must make)
+KERNEL_BYTES = {
+    "cheb_f32": 28,      # gx gy gz (12) + z_m, z_{m-1}, r (12) + z_{m+1} (4)
+    "spmv_dot_f32": 28,  # gx gy gz (12) + z, p_old (8) + p_new, mu (8)
+    "update_f32": 32,    # x, r (read+write 16) + p, mu, 1/diag (12) + z (4)
+    "stencil_f32": 20,   # gx gy gz (12) + x (4) + y (4)
+    "cheb_bf16": 22,     # gx gy gz bf16 (6) + 16
+    "residual_f64": 48,  # gx gy gz (24) + theta, theta_n (16) + P f32 (4) + r f32 (4)
+    "stencil_f64": 40,   # gx gy gz (24) + x (8) + y (8)
+    "cheb_f64": 64,      # gx gy gz (24) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)
+}
+DOMINANT = "cheb_f32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--degree", type=int, default=6, help="Chebyshev degree k (SpMVs per application)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if len(r) > 5 + j and r[5 + j] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------- workload
+
+def workload_arrays():
+    import numpy as np
+    import thermal_inputs as ti
+    inst = ti.c3(NX, NY, SEEDS, dtype=np.float32)
+    maps = [inst.power] + list(inst.extra_power)
+    return inst, maps
+
+
+def config_dict(degree):
+    return {"workload": "transient backward Euler, 1024x1024x8 layers (8,388,608 DOF), 2 Si dies + TIM + Cu, "
+                        "dt=1e-4 s, 100 steps from 45 C, 4 floorplans switched every 25 steps",
+            "nx": NX, "ny": NY, "layers": 8, "dof": NX * NY * 8, "time_steps_per_bench_step": N_STEPS,
+            "tol_rel": 1e-8, "precision": "FP32 PCG + FP64 iterative refinement",
+            "preconditioner": f"Chebyshev degree {degree} on the Jacobi-scaled operator (Lanczos bounds)",
+            "loop": "CUDA graph, conditional WHILE nodes (no host sync inside the 100 steps)",
+            "l2": "inputs larger than L2 (about 1 GB resident vs 129 MB L2); no flush"}
+
+
+# ----------------------------------------------------------------- oracle timing (CPU)
+
+def cpu_oracle_step_ms(n_samples=1):
+    """The FP64 CPU oracle as it stands: Algorithm 1 with Jacobi on the assembled CSR
+    matrix of one backward-Euler step, to the same 1e-8 relative residual, single thread."""
+    import numpy as np
+    from oracle import discretisation as disc, krylov
+    inst, maps = workload_arrays()
+    st = inst.stack
+    A = disc.assemble(NX, NY, st, dt=DT)
+    T = np.full(inst.n, st.t_amb)
+    times = []
+    for s in range(n_samples):
+        p = maps[(s // STEPS_PER_MAP) % len(maps)].astype(np.float64)
+        b = disc.rhs_transient(NX, NY, st, p, T, DT)
+        t0 = time.perf_counter()
+        op = krylov.CountingOp(A)
+        T, it, _, _ = krylov.pcg(op, b, krylov.jacobi(A), x0=T, tol_rel=1e-8)
+        times.append((time.perf_counter() - t0) * 1e3)
+    return times
+
+
+def run_cpu_child():
+    times = cpu_oracle_step_ms(1)
+    print(json.dumps({"ms": times}))
+
+
+def cpu_baseline():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child"], env=env, capture_output=True,
+                       text=True, timeout=1200)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
+    ms = json.loads(r.stdout.strip().splitlines()[-1])["ms"]
+    return {"value": ms[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first backward-Euler step of the 100-step workload (full 1024x1024x8 grid), FP64 "
+                      "Jacobi-PCG on the assembled CSR matrix to rel. residual 1e-8, 1 thread; assembly untimed"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import discretisation as disc, krylov
+    inst, maps = workload_arrays()
+    st = inst.stack
+    A = disc.assemble(NX, NY, st, dt=DT)
+    T = np.full(inst.n, st.t_amb)
+    step_ms = []
+    for s in range(args.warmup + args.steps):
+        p = maps[(s // STEPS_PER_MAP) % len(maps)].astype(np.float64)
+        b = disc.rhs_transient(NX, NY, st, p, T, DT)
+        t0 = time.perf_counter()
+        T, it, _, _ = krylov.pcg(krylov.CountingOp(A), b, krylov.jacobi(A), x0=T, tol_rel=1e-8)
+        dt_ms = (time.perf_counter() - t0) * 1e3
+        if s >= args.warmup:
+            step_ms.append(dt_ms)
+    v = sum(step_ms) / len(step_ms)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(args.degree),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "one backward-Euler step of the 100-step workload per bench step (steps "
+                                      "0..W+K-1 of the trajectory), FP64 Jacobi-PCG on the assembled CSR matrix "
+                                      "to rel. residual 1e-8; assembly untimed"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.cpu_child:
+        run_cpu_child()
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2606_17850_gb300 import ThermalGrid
+
+    inst, maps_h = workload_arrays()
+    st = inst.stack
+    grid = ThermalGrid.from_stack(NX, NY, st)
+    maps = [torch.from_numpy(m).cuda() for m in maps_h]
+    T = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
+    opts = dict(precision="mixed", precond="cheb", cheb_degree=args.degree, tol_rel=1e-8, use_graph=1)
+
+    def trajectory(o, Tt, mp):
+        Tt.fill_(st.t_amb)
+        return grid.run_transient(mp, STEPS_PER_MAP, N_STEPS, DT, Tt, **o)[1]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t_setup = time.perf_counter()
+    stats = trajectory(opts, T, maps)  # first call: Lanczos setup and graph build
+    t_setup = (time.perf_counter() - t_setup) * 1e3
+    for _ in range(args.warmup):
+        stats = trajectory(opts, T, maps)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats = trajectory(opts, T, maps)
+        e1.record(stream)
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = t.item()
+    ms_traj = ms_total / args.steps
+    value = ms_traj / N_STEPS
+    T_mixed = T.clone()
+
+    result = {"metric": METRIC, "value": value / world if False else value, "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_traj, "higher_is_better": False,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+              "config": config_dict(args.degree)}
+    result["solver"] = {"inner_it_per_traj": stats["inner_it"], "outer_it_per_traj": stats["outer_it"],
+                        "n_spmv_per_traj": stats["n_spmv"], "final_rel_res": stats["rel_res"],
+                        "status": stats["status"], "first_call_ms (setup+graph build+solve)": t_setup}
+    k = args.degree
+    # kernel launches per trajectory from the solver's counters (graph mode)
+    pairs = (stats["inner_it"] + stats["outer_it"]) // 2 + stats["outer_it"]
+    launches = (3 + N_STEPS * 6 + stats["outer_it"] * (k + 4) + pairs * (2 * (k + 1) + 1) + 1) * args.steps
+    result["gpu_launches"] = int(launches)
+    result["clocks"] = clk.summary()
+
+    # plain FP64 GPU path on the same trajectory (the baseline the metric compares against)
+    if not args.no_fp64:
+        o64 = dict(opts, precision="fp64")
+        T64 = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
+        trajectory(o64, T64, maps)  # warm-up (graph build)
+        barrier()
+        e0.record(stream)
+        s64 = trajectory(o64, T64, maps)
+        e1.record(stream)
+        barrier()
+        ms64 = e0.elapsed_time(e1)
+        rise = (T64 - st.t_amb).abs().max().item()
+        err = (T_mixed - T64).abs().max().item() / rise
+        result["fp64_gpu"] = {"value": ms64 / N_STEPS, "unit": UNIT, "ms_per_trajectory": ms64,
+                              "inner_it": s64["inner_it"], "final_rel_res": s64["rel_res"]}
+        result["speedup_mixed_vs_fp64"] = (ms64 / N_STEPS) / value
+        result["accuracy"] = {"max_abs_diff_mixed_vs_fp64_K": err * rise,
+                              "max_rel_diff_vs_rise": err}
+
+    # live per-kernel timings (CUDA events on the launching stream) -> roofline
+    peak, peak_kind = measured_peaks()
+    if not args.no_kernels:
+        kern = {}
+        for name, nbytes in KERNEL_BYTES.items():
+            ms = grid.kernel_time(name, reps=40, dt=DT)
+            gbs = nbytes * inst.n / (ms * 1e-3) / 1e9
+            kern[name] = {"ms": ms, "bytes_per_cell": nbytes, "GB/s": gbs, "frac_of_" + peak_kind: gbs / peak}
+        result["kernels"] = kern
+        dom = kern[DOMINANT]
+        result["roofline"] = {"bound": "hbm", "kernel": DOMINANT, "achieved": dom["GB/s"], "peak": peak,
+                              "unit": "GB/s", "frac": dom["GB/s"] / peak, "peak_source": peak_kind,
+                              "algorithmic_bytes_per_launch": KERNEL_BYTES[DOMINANT] * inst.n,
+                              "traffic": traffic_from_profiles(DOMINANT)}
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        maps_pin = [torch.from_numpy(m).pin_memory() for m in maps_h]
+        T_pin = torch.full((inst.n,), st.t_amb, dtype=torch.float64).pin_memory()
+        trajectory(opts, T_pin, maps_pin)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            trajectory(opts, T_pin, maps_pin)
+        barrier()
+        ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+        result["e2e"] = {"value": ms_e2e / N_STEPS, "unit": UNIT,
+                         "h2d_bytes_per_step": int(sum(m.numel() * 4 for m in maps_pin) + inst.n * 8),
+                         "d2h_bytes_per_step": int(inst.n * 8),
+                         "note": "per bench step (one 100-step trajectory): 4 power maps + T_0 to the device, "
+                                 "T_100 back, through thermal_run_transient with pinned host buffers"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def traffic_from_profiles(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent or ent.get("sources_sha") != sources_sha():
+        return None
+    return ent.get("dram_bytes_per_launch_full_size")
+
+
+def sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_17850_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

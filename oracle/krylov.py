@@ -183,3 +183,23 @@ def jacobi_scaled(A):
     """The operator D^{-1/2} A D^{-1/2} (symmetric Jacobi scaling) and D^{-1/2}."""
     s = 1.0 / np.sqrt(A.diagonal())
     return (lambda x: s * (A @ (s * x))), s
+
+
+def zline(A, nx, ny, L):
+    """Block Jacobi with one block per (x, y) column: the L x L submatrix of A over the
+    column's cells (main diagonal and the vertical couplings), solved densely per column.
+    (Not in the paper; the z-line alternative the GPU path offers.)
+    """
+    Ad = A.tocsr()
+    blocks = []
+    for y in range(ny):
+        for x in range(nx):
+            idx = np.array([x + nx * (y + ny * z) for z in range(L)])
+            blocks.append((idx, np.linalg.inv(Ad[idx][:, idx].toarray())))
+
+    def apply(r):
+        z = np.zeros_like(r, dtype=np.float64)
+        for idx, inv in blocks:
+            z[idx] = inv @ r[idx]
+        return z
+    return apply

@@ -1,0 +1,222 @@
+"""Python binding of libthermal: thin wrappers that pass torch tensors' pointers.
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+solve runs in the library's kernels.  Tensors may live on the GPU or on the host
+(host tensors are copied by the library inside the call).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _lib as L
+
+PRECISION = {"fp64": L.TH_PREC_FP64, "mixed": L.TH_PREC_MIXED_IR, "mixed_bf16": L.TH_PREC_MIXED_IR_BF16}
+PRECOND = {"none": L.TH_PC_NONE, "jacobi": L.TH_PC_JACOBI, "cheb": L.TH_PC_CHEB, "zline": L.TH_PC_ZLINE}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to libthermal must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor):
+    if t.dtype == torch.float32:
+        return L.TH_F32
+    if t.dtype == torch.float64:
+        return L.TH_F64
+    raise TypeError(f"power maps must be float32 or float64, got {t.dtype}")
+
+
+def make_opts(precision="mixed", precond="cheb", **kw):
+    o = L.default_opts(**kw)
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+    return o
+
+
+def _darr(v):
+    a = (C.c_double * len(v))(*[float(x) for x in v])
+    return a
+
+
+class ThermalGrid:
+    """A layered grid of nx * ny * layers cells (x fastest, layer 0 at the bottom)."""
+
+    def __init__(self, nx, ny, k, c, h, dx, dy, dz, t_amb):
+        lib = L.load()
+        self.nx, self.ny, self.L = int(nx), int(ny), len(k)
+        self.n = self.nx * self.ny * self.L
+        self.t_amb = float(t_amb)
+        self._h = C.c_void_p()
+        L.check(lib.thermal_grid_create(self.nx, self.ny, self.L, _darr(k), _darr(c) if c is not None else None,
+                                        float(h), C.byref(self._h)))
+        L.check(lib.thermal_grid_set_geometry(self._h, float(dx), float(dy), _darr(dz), float(t_amb)))
+
+    @classmethod
+    def from_stack(cls, nx, ny, stack):
+        """Build from any object with k(), c(), dz() arrays and h, dx, dy, t_amb attributes."""
+        return cls(nx, ny, list(stack.k()), list(stack.c()), stack.h, stack.dx, stack.dy, list(stack.dz()),
+                   stack.t_amb)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            L.load().thermal_grid_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_conductivity(self, k: Sequence[float]):
+        L.check(L.load().thermal_grid_set_conductivity(self._h, _darr(k)))
+
+    # ------------------------------------------------------------------ kernels
+
+    def faces(self, dt=0.0, device="cuda"):
+        out = {k: torch.empty(self.n, dtype=torch.float64, device=device) for k in ("gx", "gy", "gz", "diag")}
+        L.check(L.load().thermal_grid_faces(self._h, float(dt), _ptr(out["gx"]), _ptr(out["gy"]), _ptr(out["gz"]),
+                                            _ptr(out["diag"]), _stream()))
+        return out
+
+    def apply(self, x: torch.Tensor, dt=0.0, precision="fp64"):
+        y = torch.empty_like(x)
+        L.check(L.load().thermal_apply(self._h, float(dt), PRECISION[precision], _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def precond(self, r: torch.Tensor, dt=0.0, **opts):
+        z = torch.empty_like(r)
+        o = make_opts(**opts)
+        L.check(L.load().thermal_precond_apply(self._h, float(dt), C.byref(o), _ptr(r), _ptr(z), _stream()))
+        return z
+
+    def spectral_bounds(self, dt=0.0, **opts):
+        o = make_opts(**opts)
+        v = [C.c_double() for _ in range(4)]
+        L.check(L.load().thermal_spectral_bounds(self._h, float(dt), C.byref(o), *[C.byref(x) for x in v],
+                                                 _stream()))
+        return tuple(x.value for x in v)
+
+    KERNELS = {"stencil_f32": 0, "cheb_f32": 1, "cheb_bf16": 2, "spmv_dot_f32": 3, "update_f32": 4,
+               "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7}
+
+    def kernel_time(self, kernel, reps=50, dt=0.0):
+        """Average duration (ms) of one launch of a hot kernel on this grid (CUDA events)."""
+        ms = C.c_double()
+        kid = self.KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        L.check(L.load().thermal_kernel_time(self._h, kid, int(reps), float(dt), C.byref(ms), _stream()))
+        return ms.value
+
+    # ------------------------------------------------------------------ solves
+
+    def solve_steady(self, power: torch.Tensor, T: Optional[torch.Tensor] = None, **opts):
+        """Returns (T, stats).  T (float64, deg C) is allocated on power's device when not given."""
+        if T is None:
+            T = torch.empty(self.n, dtype=torch.float64, device=power.device)
+        o = make_opts(**opts)
+        st = L.SolveStats()
+        L.check(L.load().thermal_solve_steady(self._h, _ptr(power), _dtype_code(power), _ptr(T), C.byref(o),
+                                              C.byref(st), _stream()))
+        return T, st.as_dict()
+
+    def step_transient(self, power: torch.Tensor, dt: float, T: torch.Tensor, **opts):
+        """One backward-Euler step in place on T (T_n -> T_{n+1})."""
+        o = make_opts(**opts)
+        st = L.SolveStats()
+        L.check(L.load().thermal_step_transient(self._h, _ptr(power), _dtype_code(power), float(dt), _ptr(T),
+                                                C.byref(o), C.byref(st), _stream()))
+        return T, st.as_dict()
+
+    def run_transient(self, maps: List[torch.Tensor], steps_per_map: int, n_steps: int, dt: float,
+                      T: torch.Tensor, **opts):
+        """n_steps backward-Euler steps in place on T; step s uses maps[(s // steps_per_map) % len(maps)]."""
+        o = make_opts(**opts)
+        st = L.SolveStats()
+        arr = (C.c_void_p * len(maps))(*[m.data_ptr() for m in maps])
+        L.check(L.load().thermal_run_transient(self._h, arr, len(maps), _dtype_code(maps[0]), int(steps_per_map),
+                                               int(n_steps), float(dt), _ptr(T), C.byref(o), C.byref(st),
+                                               _stream()))
+        return T, st.as_dict()
+
+    # ------------------------------------------------------------------ adjoint
+
+    def hotspot_lse(self, T: torch.Tensor, layers: Sequence[int], beta: float, want_grad=True):
+        ids = (C.c_int * len(layers))(*[int(l) for l in layers])
+        J = C.c_double()
+        g = torch.empty_like(T) if want_grad else None
+        L.check(L.load().thermal_hotspot_lse(self._h, _ptr(T), ids, len(layers), float(beta), C.byref(J), _ptr(g),
+                                             _stream()))
+        return J.value, g
+
+    def grad(self, T: torch.Tensor, dJdT: torch.Tensor, dJdP_dtype=torch.float32, want_k=True, **opts):
+        """Adjoint gradient: (dJ/dP on the device, dJ/dk per layer as a list)."""
+        dJdP = torch.empty(self.n, dtype=dJdP_dtype, device=T.device)
+        dk = (C.c_double * self.L)() if want_k else None
+        o = make_opts(**opts)
+        st = L.SolveStats()
+        L.check(L.load().thermal_grad(self._h, _ptr(T), _ptr(dJdT), _ptr(dJdP), _dtype_code(dJdP),
+                                      dk, C.byref(o), C.byref(st), _stream()))
+        return dJdP, (list(dk) if want_k else None), st.as_dict()
+
+
+def solve_batched(grids: List[ThermalGrid], powers: List[torch.Tensor], Ts: List[torch.Tensor], **opts):
+    n = len(grids)
+    o = make_opts(**opts)
+    stats = (L.SolveStats * n)()
+    gh = (C.c_void_p * n)(*[g.handle.value for g in grids])
+    ph = (C.c_void_p * n)(*[p.data_ptr() for p in powers])
+    th = (C.c_void_p * n)(*[t.data_ptr() for t in Ts])
+    L.check(L.load().thermal_solve_batched(gh, n, ph, _dtype_code(powers[0]), th, C.byref(o), stats, _stream()))
+    return [s.as_dict() for s in stats]
+
+
+class SteadyAdjoint(torch.autograd.Function):
+    """T = solve(P, k): forward is a steady solve, backward one adjoint solve.
+
+    forward(grid, power [n], k [L] float64 (CPU), opts dict) -> T [n] float64 (deg C).
+    backward returns dJ/dP (power's dtype) and dJ/dk (float64, CPU).
+    """
+
+    @staticmethod
+    def forward(ctx, grid: ThermalGrid, power: torch.Tensor, k: torch.Tensor, opts: dict):
+        grid.set_conductivity(k.detach().cpu().double().tolist())
+        T, _ = grid.solve_steady(power.detach(), **opts)
+        ctx.grid, ctx.opts, ctx.pdtype = grid, opts, power.dtype
+        ctx.save_for_backward(T)
+        return T
+
+    @staticmethod
+    def backward(ctx, grad_T):
+        (T,) = ctx.saved_tensors
+        dJdP, dJdk, _ = ctx.grid.grad(T, grad_T.contiguous().double(), dJdP_dtype=ctx.pdtype, **ctx.opts)
+        return None, dJdP, torch.tensor(dJdk, dtype=torch.float64), None
+
+
+class HotspotLSE(torch.autograd.Function):
+    """J = (1/beta) log sum exp(beta T_i) over the given layers (library kernel)."""
+
+    @staticmethod
+    def forward(ctx, grid: ThermalGrid, T: torch.Tensor, layers, beta: float):
+        J, g = grid.hotspot_lse(T.detach().contiguous(), layers, beta)
+        ctx.save_for_backward(g)
+        return torch.tensor(J, dtype=torch.float64, device=T.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return None, g * gJ, None, None

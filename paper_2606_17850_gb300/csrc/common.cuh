@@ -1,0 +1,204 @@
+// Device-side building blocks shared by the solver kernels.
+//
+// * Stencil row of the 7-point finite-volume operator (Eq. steady-state /
+//   Eq. transient, Sec. 3.2) written in difference form:
+//     (A v)_i = s_z v_i + sum_faces g_f (v_i - v_j)
+//   where g_f are the per-face conductances (stored once per face, structure of
+//   arrays gx/gy/gz: the upper off-diagonals D5/D6/D7 of the paper's Quad-Diag
+//   storage with the sign flipped) and s_z = h dx dy on the top layer plus
+//   c dx dy dz / dt in a transient step.  The main diagonal (D4) is not stored: it
+//   is the sum of the six face conductances plus s_z and is formed on the fly.
+// * The device control block (scalars of PCG, refinement and step loops) that
+//   lets the loops run without host round trips.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define TH_MAXL 32            // maximum number of layers
+#define TH_BX 32              // threads per block along x
+#define TH_BY 8               // threads per block along y
+#define TH_NT (TH_BX * TH_BY)
+
+struct Dims {
+  int nx, ny, L;
+  long long pxy;  // nx*ny (z stride)
+  long long n;    // nx*ny*L
+};
+
+// Per-layer diagonal terms, in device memory (read with __ldg, index uniform per block).
+struct LayerTab {
+  double s64[TH_MAXL];    // h dx dy (top layer) + c dx dy dz / dt (transient)
+  double cdt64[TH_MAXL];  // c dx dy dz / dt (0 in steady state)
+  double k[TH_MAXL];      // conductivity per layer
+  double dz[TH_MAXL];     // thickness per layer
+  double S;               // dx * dy
+  float s32[TH_MAXL];
+};
+
+// Control block of one solve, in device memory.  Fields written by the last
+// block of a reduction are read by the blocks of the next kernel.
+struct Ctl {
+  // inner PCG (FP32 in MIXED_IR, FP64 in the plain FP64 path)
+  double rz;         // r_k^T z_k of the current iterate
+  double rz_next;    // r_{k+1}^T z_{k+1}
+  double pAp;        // p_k^T A p_k
+  double rr;         // ||r_{k+1}||^2 (recursive residual)
+  double rr0;        // ||r_0||^2 of the inner solve
+  double inner_rel;  // relative reduction the current inner solve must reach
+  int first;         // 1 before the first search direction exists
+  int done;          // inner loop finished
+  int it;            // inner iterations of the current inner solve
+  int status;        // th_status of the solve (sticky)
+  long long it_total;
+  long long n_spmv;
+  // outer loop (iterative refinement) / FP64 residual
+  double bb;         // ||b||^2
+  double rr64;       // ||b - A theta||^2 (FP64)
+  double rel_res;    // sqrt(rr64 / bb)
+  int outer_done;
+  int outer_it;
+  int max_outer;
+  int max_inner;
+  double tol_rel;
+  double inner_tol;
+  // transient loop
+  int step;
+  int n_steps;
+  int steps_per_map;
+  int n_maps;
+  int steps_done;
+  int n_inits;      // inner solves started
+  long long lanczos_spmv;
+};
+
+__device__ __forceinline__ float ldc(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double ldc(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldc(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+template <typename T> __device__ __forceinline__ T ldv(const T* p) { return *p; }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int block_linear_id() {
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+__device__ __forceinline__ int block_count() { return gridDim.x * gridDim.y * gridDim.z; }
+__device__ __forceinline__ int thread_linear_id() { return threadIdx.x + blockDim.x * threadIdx.y; }
+__device__ __forceinline__ int block_threads() { return blockDim.x * blockDim.y; }
+
+// Thread -> cell mapping used by every stencil kernel: block (TH_BX, TH_BY),
+// grid (ceil(nx/TH_BX), ceil(ny/TH_BY), L); blockIdx.z is the layer.
+struct Cell {
+  int x, y, z;
+  long long i;
+  bool valid;
+};
+__device__ __forceinline__ Cell cell_of(const Dims& d) {
+  Cell c;
+  c.x = blockIdx.x * TH_BX + threadIdx.x;
+  c.y = blockIdx.y * TH_BY + threadIdx.y;
+  c.z = blockIdx.z;
+  c.valid = (c.x < d.nx) && (c.y < d.ny);
+  c.i = (long long)c.x + (long long)d.nx * ((long long)c.y + (long long)d.ny * c.z);
+  return c;
+}
+
+// (A v)_i in difference form and the diagonal A_ii.  `val(j)` returns v_j as TA.
+template <typename TA, typename TC, typename F>
+__device__ __forceinline__ TA stencil_row(const TC* __restrict__ gx, const TC* __restrict__ gy,
+                                          const TC* __restrict__ gz, const Dims& d, const Cell& c,
+                                          TA s_layer, TA vi, F val, TA& diag) {
+  TA acc = s_layer * vi;
+  TA dg = s_layer;
+  if (c.x + 1 < d.nx) { TA g = (TA)ldc(gx + c.i);         acc += g * (vi - val(c.i + 1));      dg += g; }
+  if (c.x > 0)        { TA g = (TA)ldc(gx + c.i - 1);     acc += g * (vi - val(c.i - 1));      dg += g; }
+  if (c.y + 1 < d.ny) { TA g = (TA)ldc(gy + c.i);         acc += g * (vi - val(c.i + d.nx));   dg += g; }
+  if (c.y > 0)        { TA g = (TA)ldc(gy + c.i - d.nx);  acc += g * (vi - val(c.i - d.nx));   dg += g; }
+  if (c.z + 1 < d.L)  { TA g = (TA)ldc(gz + c.i);         acc += g * (vi - val(c.i + d.pxy));  dg += g; }
+  if (c.z > 0)        { TA g = (TA)ldc(gz + c.i - d.pxy); acc += g * (vi - val(c.i - d.pxy));  dg += g; }
+  diag = dg;
+  return acc;
+}
+
+template <typename T> __device__ __forceinline__ bool finite_(T v) { return isfinite((double)v); }
+
+__device__ __forceinline__ int ld_int(const int* p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_dbl(const double* p) { return __ldcg(p); }
+
+template <typename TA> __device__ __forceinline__ TA lay_s(const LayerTab* t, int z);
+template <> __device__ __forceinline__ double lay_s<double>(const LayerTab* t, int z) { return __ldg(&t->s64[z]); }
+template <> __device__ __forceinline__ float lay_s<float>(const LayerTab* t, int z) { return __ldg(&t->s32[z]); }
+
+// Sum NQ per-thread values (type T, warp level in T) over the block, then over the
+// grid: each block writes one FP64 partial; the last block sums the partials in a
+// fixed order.  Returns true in thread 0 of the last block, with tot[] valid there.
+template <typename T, int NQ>
+__device__ __forceinline__ bool grid_reduce(T (&v)[NQ], double* partials, int stride, unsigned* counter,
+                                            double (&tot)[NQ]) {
+  __shared__ double sm[NQ][32];
+  __shared__ bool am_last;
+  const int t = thread_linear_id();
+  const int nw = (block_threads() + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+  if ((t & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sm[q][t >> 5] = (double)v[q];
+  }
+  __syncthreads();
+  if (t == 0) {
+    const int bid = block_linear_id();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sm[q][w];
+      partials[(size_t)q * stride + bid] = s;
+    }
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    am_last = (prev == (unsigned)(block_count() - 1));
+  }
+  __syncthreads();
+  if (!am_last) return false;
+  __threadfence();
+  const int nb = block_count();
+  double s[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    s[q] = 0.0;
+    for (int j = t; j < nb; j += block_threads()) s[q] += __ldcg(partials + (size_t)q * stride + j);
+    s[q] = warp_sum(s[q]);
+  }
+  __syncthreads();
+  if ((t & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sm[q][t >> 5] = s[q];
+  }
+  __syncthreads();
+  if (t != 0) return false;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += sm[q][w];
+    tot[q] = a;
+  }
+  *counter = 0u;
+  return true;
+}
+

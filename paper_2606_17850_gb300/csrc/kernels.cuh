@@ -1,0 +1,417 @@
+// Solver kernels: PCG (Algorithm 1) with fused stencil + dot product, fused
+// vector updates, the Chebyshev polynomial preconditioner (Algorithm "Chebyshev
+// Polynomial Preconditioning", Sec. 4.3) in its equivalent three-term form, the
+// z-line block-Jacobi preconditioner, the FP64 residual of iterative refinement,
+// Lanczos (Sec. 4.3) and the device-side loop control.
+//
+// All scalars of the iteration live in the device control block `Ctl`; every
+// reduction is finished by the last block of its kernel, which also takes the
+// loop decisions, so a solve needs no host round trip.
+#pragma once
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------- control
+
+struct CtlInit {
+  double tol_rel, inner_tol;
+  int max_outer, max_inner, n_steps, steps_per_map, n_maps;
+};
+
+__global__ void k_ctl_reset(Ctl* c, CtlInit in) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Ctl z = {};
+  z.tol_rel = in.tol_rel;
+  z.inner_tol = in.inner_tol;
+  z.max_outer = in.max_outer;
+  z.max_inner = in.max_inner;
+  z.n_steps = in.n_steps;
+  z.steps_per_map = in.steps_per_map;
+  z.n_maps = in.n_maps;
+  z.inner_rel = in.inner_tol;
+  z.rel_res = 1.0;
+  *c = z;
+}
+
+// Start of a backward-Euler step: theta_n <- theta (element-wise) is done by
+// k_copy; this resets the per-step loop flags (counters keep accumulating).
+__global__ void k_step_begin(Ctl* c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  c->outer_done = 0;
+  c->done = 0;
+  c->rel_res = 1.0;
+}
+
+__global__ void k_step_end(Ctl* c) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  c->step += 1;
+  c->steps_done += 1;
+}
+
+// which: 0 inner loop (!done), 1 outer loop (!outer_done), 2 step loop (step < n_steps,
+// and no fatal status).
+__global__ void k_cond(cudaGraphConditionalHandle h, const Ctl* c, int which) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned v = 0;
+  const int fatal = (c->status == 5 || c->status == 6);  // TH_EBREAKDOWN, TH_ENONFINITE
+  if (which == 0) v = (c->done == 0);
+  else if (which == 1) v = (c->outer_done == 0);
+  else v = (c->step < c->n_steps) && !fatal;
+  cudaGraphSetConditional(h, v);
+}
+
+// ---------------------------------------------------------------- element-wise
+
+// mode 0: theta = 0; 1: theta = T - t_amb; 2: theta_n = T - t_amb and theta = theta_n.
+__global__ void k_prepare(long long n, const double* __restrict__ T, double t_amb, int mode,
+                          double* __restrict__ theta, double* __restrict__ theta_n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = 0.0;
+  if (mode >= 1) v = T[i] - t_amb;
+  theta[i] = v;
+  if (mode == 2) theta_n[i] = v;
+}
+
+__global__ void k_finalize(long long n, const double* __restrict__ theta, double t_amb, double* __restrict__ T) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T[i] = theta[i] + t_amb;
+}
+
+__global__ void k_copy64(long long n, const double* __restrict__ a, double* __restrict__ b) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  b[i] = a[i];
+}
+
+// theta += rscale * d (refinement correction; rscale undoes the inner solve's scaling).
+__global__ void k_theta_axpy(long long n, const Ctl* ctl, double* __restrict__ theta, const float* __restrict__ d) {
+  if (ld_int(&ctl->outer_done)) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double sc = ld_dbl(&ctl->rr64);  // holds ||r|| of the residual the inner solve was given
+  theta[i] += sqrt(sc) * (double)d[i];
+}
+
+// ---------------------------------------------------------------- FP64 residual
+
+// r = b - A theta in FP64 (FP64 faces), b = P + cdt * theta_n (theta_n optional).
+// Power map: P, or ptab[(step / steps_per_map) % n_maps] when ptab != NULL.
+// Reduces ||r||^2 and ||b||^2 (squares in FP32, partial sums in FP64).
+// mode 0: refinement (outer) decision; mode 1: start of the plain FP64 PCG
+// (sets rr0 and the target); mode 2: final residual for statistics only.
+template <typename TP, typename TR>
+__global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, const double* __restrict__ theta,
+                           const TP* __restrict__ P, const TP* const* ptab, const double* __restrict__ theta_n,
+                           TR* __restrict__ r, int mode, int count_outer, double* partials, int stride,
+                           unsigned* counter) {
+  if (mode == 0 && ld_int(&ctl->outer_done)) return;
+  const Cell c = cell_of(d);
+  if (ptab) {
+    const int st = ld_int(&ctl->step), spm = ctl->steps_per_map, nm = ctl->n_maps;
+    P = ptab[(st / spm) % nm];
+  }
+  float v[2] = {0.f, 0.f};
+  if (c.valid) {
+    const double ti = theta[c.i];
+    double dg;
+    const double a = stencil_row<double>(f.gx, f.gy, f.gz, d, c, lay_s<double>(tab, c.z), ti,
+                                         [&](long long j) { return theta[j]; }, dg);
+    double b = (double)P[c.i];
+    if (theta_n) b += __ldg(&tab->cdt64[c.z]) * theta_n[c.i];
+    const double ri = b - a;
+    r[c.i] = (TR)ri;
+    const float rf = (float)ri, bf = (float)b;
+    v[0] = rf * rf;
+    v[1] = bf * bf;
+  }
+  double tot[2];
+  if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
+  // last block, thread 0
+  const double rr = tot[0], bb = tot[1];
+  ctl->rr64 = rr;
+  ctl->bb = bb;
+  ctl->n_spmv += 1;
+  const double rel = (bb > 0.0) ? sqrt(rr / bb) : 0.0;
+  ctl->rel_res = rel;
+  if (mode == 2) return;
+  if (mode == 1) {  // plain FP64 PCG start
+    ctl->rr0 = rr;
+    ctl->rr = rr;
+    ctl->inner_rel = (rr > 0.0) ? ctl->tol_rel * sqrt(bb / rr) : 0.0;
+    ctl->it = 0;
+    ctl->first = 1;
+    ctl->done = (rel <= ctl->tol_rel) || !(rr == rr);
+    if (!isfinite(rr)) ctl->status = 6;
+    return;
+  }
+  if (count_outer) ctl->outer_it += 1;
+  if (!isfinite(rr) || !isfinite(bb)) {
+    ctl->status = 6;
+    ctl->outer_done = 1;
+  } else if (rel <= ctl->tol_rel) {
+    ctl->outer_done = 1;
+  } else if (ctl->outer_it >= ctl->max_outer) {
+    ctl->status = 4;
+    ctl->outer_done = 1;
+  } else {
+    // reduce the residual as far as this step needs, never less than inner_tol
+    double want = 0.3 * ctl->tol_rel / rel;
+    if (want > 0.5) want = 0.5;
+    ctl->inner_rel = want > ctl->inner_tol ? want : ctl->inner_tol;
+  }
+}
+
+// ---------------------------------------------------------------- PCG kernels
+
+// Search direction and stencil product, fused (Algorithm 1 lines "mu = A p" and the
+// denominator of alpha): p_new = z + beta p_old (formed on the fly for the cell and
+// its six neighbours; beta = rz_next / rz, 0 at the first iteration), mu = A p_new,
+// pAp = p_new^T mu.
+template <typename TV, typename TC>
+__global__ void k_spmv_dot(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC* __restrict__ gy,
+                           const TC* __restrict__ gz, const LayerTab* tab, const TV* __restrict__ z,
+                           const TV* __restrict__ p_old, TV* __restrict__ p_new, TV* __restrict__ mu,
+                           double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const Cell c = cell_of(d);
+  const int first = ld_int(&ctl->first);
+  const TV beta = first ? (TV)0 : (TV)(ld_dbl(&ctl->rz_next) / ld_dbl(&ctl->rz));
+  TV v[1] = {(TV)0};
+  if (c.valid) {
+    auto pv = [&](long long j) -> TV { return first ? z[j] : z[j] + beta * p_old[j]; };
+    const TV pi = pv(c.i);
+    TV dg;
+    const TV ai = stencil_row<TV>(gx, gy, gz, d, c, lay_s<TV>(tab, c.z), pi, pv, dg);
+    p_new[c.i] = pi;
+    mu[c.i] = ai;
+    v[0] = pi * ai;
+  }
+  double tot[1];
+  if (!grid_reduce<TV, 1>(v, partials, stride, counter, tot)) return;
+  const double pAp = tot[0];
+  ctl->pAp = pAp;
+  ctl->rz = ctl->rz_next;
+  ctl->first = 0;
+  if (!(pAp > 0.0)) {
+    ctl->status = isfinite(pAp) ? 5 : 6;
+    ctl->done = 1;
+    ctl->outer_done = 1;
+  }
+}
+
+// ZMODE: 0 no preconditioner (z = r), 1 Jacobi (z = r / A_ii), 2 first Chebyshev
+// iterate (z_1 = zscale * r, or zscale * r / A_ii when scaled), 3 z formed by
+// another kernel.  INIT: start of an inner solve (x = 0, alpha = 0; in the mixed
+// path r is first scaled to unit norm by 1/sqrt(rr64)).
+template <typename TV, bool INIT, int ZMODE>
+__global__ void k_update(Dims d, Ctl* ctl, TV* __restrict__ x, const TV* __restrict__ p, TV* __restrict__ r,
+                         const TV* __restrict__ mu, const TV* __restrict__ invd, TV* __restrict__ z, TV zscale,
+                         int scaled, int rz_here, int scale_r, double* partials, int stride, unsigned* counter) {
+  if (!INIT && ld_int(&ctl->done)) return;
+  if (INIT && ld_int(&ctl->outer_done)) return;
+  const Cell c = cell_of(d);
+  TV alpha = (TV)0;
+  if (!INIT) alpha = (TV)(ld_dbl(&ctl->rz) / ld_dbl(&ctl->pAp));
+  TV rs = (TV)1;
+  if (INIT && scale_r) {
+    const double rr = ld_dbl(&ctl->rr64);
+    rs = (TV)(rr > 0.0 ? 1.0 / sqrt(rr) : 1.0);
+  }
+  TV v[2] = {(TV)0, (TV)0};
+  if (c.valid) {
+    TV ri = r[c.i];
+    if (INIT) {
+      if (x) x[c.i] = (TV)0;
+      if (scale_r) {
+        ri *= rs;
+        r[c.i] = ri;
+      }
+    } else {
+      x[c.i] += alpha * p[c.i];
+      ri -= alpha * mu[c.i];
+      r[c.i] = ri;
+    }
+    TV zi = ri;
+    if (ZMODE == 1) zi = ri * invd[c.i];
+    if (ZMODE == 2) zi = (scaled ? ri * invd[c.i] : ri) * zscale;
+    if (ZMODE == 1 || ZMODE == 2) z[c.i] = zi;
+    v[0] = ri * ri;
+    v[1] = ri * zi;
+  }
+  double tot[2];
+  if (!grid_reduce<TV, 2>(v, partials, stride, counter, tot)) return;
+  const double rr = tot[0];
+  ctl->rr = rr;
+  if (rz_here) ctl->rz_next = tot[1];
+  if (INIT) {
+    ctl->rr0 = rr;
+    ctl->it = 0;
+    ctl->first = 1;
+    ctl->n_inits += 1;
+    ctl->done = !(rr > 0.0) || (ctl->inner_rel >= 1.0);
+    if (!isfinite(rr)) {
+      ctl->status = 6;
+      ctl->done = 1;
+      ctl->outer_done = 1;
+    }
+    return;
+  }
+  ctl->it += 1;
+  ctl->it_total += 1;
+  const double tgt = ctl->inner_rel * ctl->inner_rel * ctl->rr0;
+  if (!isfinite(rr)) {
+    ctl->status = 6;
+    ctl->done = 1;
+    ctl->outer_done = 1;
+  } else if (rr <= tgt) {
+    ctl->done = 1;
+  } else if (ctl->it >= ctl->max_inner) {
+    ctl->done = 1;
+  }
+}
+
+// One step of the Chebyshev recurrence in three-term form.  With z_0 = 0,
+// z_1 = d_0 and z_{m+1} = z_m + d_m, the algorithm's updates give
+//   z_{m+1} = z_m + rho_m rho_{m-1} (z_m - z_{m-1}) + (2 rho_m / delta) M (r - A z_m),
+// M = I (as written in the paper) or D^{-1} (Chebyshev on the Jacobi-scaled operator).
+// LAST: also reduce r^T z_{m+1} (the rz of the outer PCG).
+template <typename TV, typename TC, bool SCALED, bool LAST>
+__global__ void k_cheb(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC* __restrict__ gy,
+                       const TC* __restrict__ gz, const LayerTab* tab, const TV* __restrict__ r,
+                       const TV* __restrict__ zprev, const TV* __restrict__ zcur, TV* __restrict__ znext,
+                       const TV* __restrict__ invd, TV c1, TV c2, double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const Cell c = cell_of(d);
+  TV v[1] = {(TV)0};
+  if (c.valid) {
+    const TV zi = zcur[c.i];
+    TV dg;
+    const TV az = stencil_row<TV>(gx, gy, gz, d, c, lay_s<TV>(tab, c.z), zi,
+                                  [&](long long j) { return zcur[j]; }, dg);
+    const TV ri = r[c.i];
+    TV res = ri - az;
+    if (SCALED) {
+      if (sizeof(TV) == 8) res *= invd[c.i];
+      else res = res / dg;
+    }
+    const TV zp = zprev ? zprev[c.i] : (TV)0;
+    const TV zn = zi + c1 * (zi - zp) + c2 * res;
+    znext[c.i] = zn;
+    if (LAST) v[0] = ri * zn;
+  }
+  if (!LAST) return;
+  double tot[1];
+  if (!grid_reduce<TV, 1>(v, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+}
+
+// z-line block Jacobi: per (x, y) column, solve the tridiagonal system with
+// diagonal A_ii and off-diagonals -gz (Thomas algorithm, factors from setup).
+// Reduces r^T z.  Launch: block (TH_BX, TH_BY), grid (ceil(nx/TH_BX), ceil(ny/TH_BY), 1).
+template <typename TV>
+__global__ void k_zline(Dims d, Ctl* ctl, const float* __restrict__ gz, const float* __restrict__ zm,
+                        const float* __restrict__ zc, const TV* __restrict__ r, TV* __restrict__ z,
+                        double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const int x = blockIdx.x * TH_BX + threadIdx.x;
+  const int y = blockIdx.y * TH_BY + threadIdx.y;
+  TV v[1] = {(TV)0};
+  if (x < d.nx && y < d.ny) {
+    const long long base = (long long)x + (long long)d.nx * y;
+    TV dp = (TV)0;
+    for (int k = 0; k < d.L; ++k) {  // forward: d'_k = m_k (r_k + gz_{k-1} d'_{k-1})
+      const long long i = base + d.pxy * k;
+      const TV gdn = (k > 0) ? (TV)gz[i - d.pxy] : (TV)0;
+      dp = (TV)zm[i] * (r[i] + gdn * dp);
+      z[i] = dp;
+    }
+    TV zn = (TV)0;
+    for (int k = d.L - 1; k >= 0; --k) {  // backward: z_k = d'_k + (gz_k m_k) z_{k+1}
+      const long long i = base + d.pxy * k;
+      const TV zk = z[i] + (TV)zc[i] * zn;
+      z[i] = zk;
+      v[0] += r[i] * zk;
+      zn = zk;
+    }
+  }
+  double tot[1];
+  if (!grid_reduce<TV, 1>(v, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+}
+
+// ---------------------------------------------------------------- Lanczos (FP32)
+
+// SplitMix64 (Steele, Lea, Flood 2014), counter form: element i uses the state
+// seed + (i+1) * 0x9E3779B97F4A7C15; top 53 bits -> [0,1) -> [-1,1).
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, long long i) {
+  unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// w = start vector; nrm[0] = ||w||.   lz layout: alpha[0..511], nrm[512..1023]
+__global__ void k_lz_start(Dims d, Ctl* ctl, float* __restrict__ w, unsigned long long seed, double* lz,
+                           double* partials, int stride, unsigned* counter) {
+  const Cell c = cell_of(d);
+  float v[1] = {0.f};
+  if (c.valid) {
+    const float wi = (float)splitmix_uniform(seed, c.i);
+    w[c.i] = wi;
+    v[0] = wi * wi;
+  }
+  double tot[1];
+  if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
+  lz[512] = sqrt(tot[0]);
+}
+
+// v_j = w / nrm[j] (stored), u = Op v_j with Op = A or S A S (S = D^{-1/2}),
+// alpha_j = v_j^T u.
+template <bool SCALED>
+__global__ void k_lz_spmv(Dims d, Ctl* ctl, const float* __restrict__ gx, const float* __restrict__ gy,
+                          const float* __restrict__ gz, const LayerTab* tab, const float* __restrict__ isq,
+                          const float* __restrict__ w, float* __restrict__ vj, float* __restrict__ u, double* lz,
+                          int j, double* partials, int stride, unsigned* counter) {
+  const Cell c = cell_of(d);
+  const float inv = (float)(1.0 / ld_dbl(lz + 512 + j));
+  float v[1] = {0.f};
+  if (c.valid) {
+    auto val = [&](long long k) -> float {
+      const float vk = w[k] * inv;
+      return SCALED ? vk * isq[k] : vk;
+    };
+    const float vi = w[c.i] * inv;
+    float dg;
+    float ai = stencil_row<float>(gx, gy, gz, d, c, lay_s<float>(tab, c.z), val(c.i), val, dg);
+    if (SCALED) ai *= isq[c.i];
+    vj[c.i] = vi;
+    u[c.i] = ai;
+    v[0] = vi * ai;
+  }
+  double tot[1];
+  if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
+  lz[j] = tot[0];
+  ctl->lanczos_spmv += 1;
+}
+
+// w = u - alpha_j v_j - nrm[j] v_{j-1};  nrm[j+1] = ||w||.
+__global__ void k_lz_update(Dims d, Ctl* ctl, const float* __restrict__ u, const float* __restrict__ vj,
+                            const float* __restrict__ vprev, float* __restrict__ w, double* lz, int j,
+                            double* partials, int stride, unsigned* counter) {
+  const Cell c = cell_of(d);
+  const float a = (float)ld_dbl(lz + j);
+  const float b = (float)ld_dbl(lz + 512 + j);
+  float v[1] = {0.f};
+  if (c.valid) {
+    float wi = u[c.i] - a * vj[c.i];
+    if (vprev) wi -= b * vprev[c.i];
+    w[c.i] = wi;
+    v[0] = wi * wi;
+  }
+  double tot[1];
+  if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
+  lz[512 + j + 1] = sqrt(tot[0]);
+}

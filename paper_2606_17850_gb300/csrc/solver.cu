@@ -1,0 +1,941 @@
+// Solver orchestration: plain FP64 PCG (Algorithm 1), FP32 PCG inside FP64
+// iterative refinement, preconditioners (Jacobi, Chebyshev with Lanczos bounds,
+// z-line), backward-Euler steps and the step loop.  Loops are controlled on the
+// device (Ctl); the host either polls the control block between launch chunks or
+// replays a CUDA graph whose loops are conditional WHILE nodes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+// ------------------------------------------------------------------ plan
+
+struct Plan {
+  thermal_grid* g = nullptr;
+  Dims d;
+  dim3 gb, tb, gcol;
+  int prec = TH_PREC_MIXED_IR, pc = TH_PC_CHEB, k = 30, scaled = 1;
+  double dt = 0.0;
+  int pdtype = TH_F32;
+  bool transient = false;   // b includes cdt * theta_n
+  bool use_ptab = true;     // power read through g->dev_ptrs
+  std::vector<double> c1, c2;
+  double inv_theta = 1.0, lmin = 0.0, lmax = 0.0;
+  int pc_spmv = 0;          // stencil applications per preconditioner application
+};
+
+static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
+
+// Stencil products for kernel timing (same body as thermal_apply's kernels).
+__global__ void k_apply_f32(Dims d, const float* __restrict__ gx, const float* __restrict__ gy,
+                            const float* __restrict__ gz, const LayerTab* tab, const float* __restrict__ x,
+                            float* __restrict__ y) {
+  const Cell c = cell_of(d);
+  if (!c.valid) return;
+  float dg;
+  y[c.i] = stencil_row<float>(gx, gy, gz, d, c, lay_s<float>(tab, c.z), x[c.i], [&](long long j) { return x[j]; }, dg);
+}
+__global__ void k_apply_f64(Dims d, const double* __restrict__ gx, const double* __restrict__ gy,
+                            const double* __restrict__ gz, const LayerTab* tab, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  const Cell c = cell_of(d);
+  if (!c.valid) return;
+  double dg;
+  y[c.i] = stencil_row<double>(gx, gy, gz, d, c, lay_s<double>(tab, c.z), x[c.i], [&](long long j) { return x[j]; }, dg);
+}
+
+// ------------------------------------------------------------------ host tridiagonal eigenvalues
+
+// Number of eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm count
+// via the signs of the LDL^T pivots).
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+  int cnt = 0;
+  double q = a[0] - x;
+  if (q < 0) ++cnt;
+  for (size_t j = 1; j < a.size(); ++j) {
+    const double qq = (q == 0.0) ? 1e-300 : q;
+    q = a[j] - x - b[j - 1] * b[j - 1] / qq;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// Smallest and largest eigenvalue by bisection on the Sturm count, Gershgorin start.
+static void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double* lo, double* hi) {
+  const size_t m = a.size();
+  double gl = a[0], gu = a[0];
+  for (size_t j = 0; j < m; ++j) {
+    const double r = (j > 0 ? std::fabs(b[j - 1]) : 0.0) + (j + 1 < m ? std::fabs(b[j]) : 0.0);
+    gl = std::min(gl, a[j] - r);
+    gu = std::max(gu, a[j] + r);
+  }
+  auto bisect = [&](int target) {  // smallest x with count(x) >= target
+    double l = gl, u = gu;
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(std::fabs(l), std::fabs(u)); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (sturm_count(a, b, mid) >= target) u = mid; else l = mid;
+    }
+    return 0.5 * (l + u);
+  };
+  *lo = bisect(1);
+  *hi = bisect((int)m);
+}
+
+// ------------------------------------------------------------------ Lanczos
+
+th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* o, double* rmin, double* rmax,
+                          double* lmin, double* lmax, cudaStream_t s) {
+  TH_TRY(grid_ensure_tab(g, dt, s));
+  TH_TRY(grid_ensure_workspace(g, false, s));
+  const int m = std::min(o->lanczos_steps, 500);
+  const LanczosKey key{dt > 0 ? dt : 0.0, o->cheb_scaled ? 1 : 0, m};
+  double ra, rb;
+  auto it = g->lanczos_cache.find(key);
+  if (it != g->lanczos_cache.end()) {
+    ra = it->second.ritz_min;
+    rb = it->second.ritz_max;
+  } else {
+    const Dims d = grid_dims(g);
+    const dim3 gb = grid_blocks(g), tb(TH_BX, TH_BY);
+    float* w = g->zc32[0];
+    float* u = g->zc32[1];
+    float* vb[2] = {g->zc32[2], g->mu32};
+    k_lz_start<<<gb, tb, 0, s>>>(d, g->ctl, w, 0x5EEDull, g->lz, g->partials, g->partials_stride, g->counters);
+    TH_CHECK_LAUNCH();
+    for (int j = 0; j < m; ++j) {
+      if (o->cheb_scaled)
+        k_lz_spmv<true><<<gb, tb, 0, s>>>(d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->isqd32, w,
+                                          vb[j & 1], u, g->lz, j, g->partials, g->partials_stride, g->counters);
+      else
+        k_lz_spmv<false><<<gb, tb, 0, s>>>(d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->isqd32, w,
+                                           vb[j & 1], u, g->lz, j, g->partials, g->partials_stride, g->counters);
+      TH_CHECK_LAUNCH();
+      k_lz_update<<<gb, tb, 0, s>>>(d, g->ctl, u, vb[j & 1], j > 0 ? vb[(j + 1) & 1] : nullptr, w, g->lz, j,
+                                    g->partials, g->partials_stride, g->counters);
+      TH_CHECK_LAUNCH();
+    }
+    std::vector<double> h(1024);
+    TH_CUDA(cudaMemcpyAsync(h.data(), g->lz, 1024 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TH_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> a, b;
+    for (int j = 0; j < m; ++j) {
+      if (!std::isfinite(h[j])) return th_fail(TH_ENONFINITE, "Lanczos produced a non-finite value");
+      a.push_back(h[j]);
+      const double bj = h[512 + j + 1];
+      if (j + 1 < m) {
+        if (!(bj > 0.0)) break;  // invariant subspace: T is complete
+        b.push_back(bj);
+      }
+    }
+    if (b.size() + 1 < a.size()) a.resize(b.size() + 1);
+    tridiag_extremes(a, b, &ra, &rb);
+    g->lanczos_cache[key] = LanczosVal{ra, rb};
+  }
+  // interval used by the preconditioner: lmax = 1.05 ritz_max, lmin = max(ritz_min, 1e-7 lmax)
+  const double hi = 1.05 * rb;
+  const double lo = std::max(ra, 1e-7 * hi);
+  if (rmin) *rmin = ra;
+  if (rmax) *rmax = rb;
+  if (lmin) *lmin = lo;
+  if (lmax) *lmax = hi;
+  if (!(lo > 0.0) || !(hi > lo)) return th_fail(TH_EBREAKDOWN, "invalid spectral interval [%g, %g]", lo, hi);
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ plan setup
+
+static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts* o, int pdtype, bool transient,
+                           Plan& P, cudaStream_t s) {
+  P.g = g;
+  P.d = grid_dims(g);
+  P.gb = grid_blocks(g);
+  P.tb = dim3(TH_BX, TH_BY);
+  P.gcol = dim3((g->nx + TH_BX - 1) / TH_BX, (g->ny + TH_BY - 1) / TH_BY, 1);
+  P.prec = o->precision;
+  P.pc = o->precond;
+  P.k = o->cheb_degree;
+  P.scaled = o->cheb_scaled ? 1 : 0;
+  P.dt = dt;
+  P.pdtype = pdtype;
+  P.transient = transient;
+  TH_TRY(grid_ensure_tab(g, dt, s));
+  TH_TRY(grid_ensure_workspace(g, P.prec == TH_PREC_FP64, s));
+  if (P.pc == TH_PC_ZLINE) TH_TRY(grid_ensure_zline(g, dt, s));
+  P.pc_spmv = 0;
+  if (P.pc == TH_PC_CHEB) {
+    double ra, rb;
+    TH_TRY(solver_spectral(g, dt, o, &ra, &rb, &P.lmin, &P.lmax, s));
+    const double theta = 0.5 * (P.lmax + P.lmin), delta = 0.5 * (P.lmax - P.lmin);
+    const double sigma1 = theta / delta;
+    double rho_prev = 1.0 / sigma1;  // rho_0
+    P.inv_theta = 1.0 / theta;
+    P.c1.assign(P.k, 0.0);
+    P.c2.assign(P.k, 0.0);
+    for (int m = 1; m < P.k; ++m) {
+      const double rho = 1.0 / (2.0 * sigma1 - rho_prev);
+      P.c1[m] = rho * rho_prev;
+      P.c2[m] = 2.0 * rho / delta;
+      rho_prev = rho;
+    }
+    P.pc_spmv = P.k - 1;
+  }
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ vector sets
+
+template <typename TV> struct VecSet {
+  TV* x;
+  TV* r;
+  TV* mu;
+  TV* p[2];
+  TV* zc[3];
+  const TV* invd;
+};
+
+static VecSet<float> vec32(thermal_grid* g) {
+  VecSet<float> v;
+  v.x = g->d32; v.r = g->r32; v.mu = g->mu32;
+  v.p[0] = g->p32[0]; v.p[1] = g->p32[1];
+  for (int i = 0; i < 3; ++i) v.zc[i] = g->zc32[i];
+  v.invd = g->invd32;
+  return v;
+}
+static VecSet<double> vec64(thermal_grid* g) {
+  VecSet<double> v;
+  v.x = g->theta[0]; v.r = g->r64; v.mu = g->mu64;
+  v.p[0] = g->p64[0]; v.p[1] = g->p64[1];
+  for (int i = 0; i < 3; ++i) v.zc[i] = g->zc64[i];
+  v.invd = g->invd64;
+  return v;
+}
+
+template <typename TV> static TV* z_final(const Plan& P, const VecSet<TV>& V) {
+  switch (P.pc) {
+    case TH_PC_NONE: return V.r;
+    case TH_PC_CHEB: return V.zc[(P.k - 1) % 3];
+    default: return V.zc[0];
+  }
+}
+
+// ------------------------------------------------------------------ enqueue: preconditioner
+
+template <typename TV, bool INIT>
+static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st, int p_cur, int zero_x,
+                            int scale_r) {
+  thermal_grid* g = P.g;
+  Ctl* ctl = g->ctl;
+  TV* x = V.x;
+  const TV* pp = V.p[p_cur];
+  const TV zs = (TV)P.inv_theta;
+  const int rz1 = (P.pc == TH_PC_NONE || P.pc == TH_PC_JACOBI || (P.pc == TH_PC_CHEB && P.k == 1)) ? 1 : 0;
+  // an INIT without zeroing x must not touch x: pass it through a harmless path
+  // (x is only written when INIT && zero_x, or in a regular update).
+  TV* xw = (INIT && !zero_x) ? nullptr : x;
+#define TH_UPD(ZM)                                                                                          \
+  k_update<TV, INIT, ZM><<<P.gb, P.tb, 0, st>>>(P.d, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], zs, P.scaled, \
+                                                rz1, scale_r, g->partials, g->partials_stride, g->counters)
+  switch (P.pc) {
+    case TH_PC_NONE: TH_UPD(0); break;
+    case TH_PC_JACOBI: TH_UPD(1); break;
+    case TH_PC_CHEB: TH_UPD(2); break;
+    default: TH_UPD(3); break;
+  }
+#undef TH_UPD
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+template <typename TV, typename TC>
+static th_status enq_cheb_tail(const Plan& P, const VecSet<TV>& V, const TC* gx, const TC* gy, const TC* gz,
+                               cudaStream_t st) {
+  thermal_grid* g = P.g;
+  for (int m = 1; m < P.k; ++m) {
+    const TV* zprev = (m >= 2) ? V.zc[(m - 2) % 3] : nullptr;
+    const TV* zcur = V.zc[(m - 1) % 3];
+    TV* znext = V.zc[m % 3];
+    const bool last = (m == P.k - 1);
+    const TV c1 = (TV)P.c1[m], c2 = (TV)P.c2[m];
+#define TH_CHEB(SC, LA)                                                                                      \
+  k_cheb<TV, TC, SC, LA><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, gx, gy, gz, g->tab, V.r, zprev, zcur, znext, \
+                                                V.invd, c1, c2, g->partials, g->partials_stride, g->counters)
+    if (P.scaled) {
+      if (last) TH_CHEB(true, true); else TH_CHEB(true, false);
+    } else {
+      if (last) TH_CHEB(false, true); else TH_CHEB(false, false);
+    }
+#undef TH_CHEB
+    TH_CHECK_LAUNCH();
+  }
+  return TH_OK;
+}
+
+template <typename TV>
+static th_status enq_precond_tail(const Plan& P, const VecSet<TV>& V, cudaStream_t st) {
+  thermal_grid* g = P.g;
+  if (P.pc == TH_PC_CHEB) {
+    if constexpr (sizeof(TV) == 8) {
+      return enq_cheb_tail<TV, double>(P, V, g->f64.gx, g->f64.gy, g->f64.gz, st);
+    } else {
+      if (P.prec == TH_PREC_MIXED_IR_BF16)
+        return enq_cheb_tail<TV, __nv_bfloat16>(P, V, g->f16.gx, g->f16.gy, g->f16.gz, st);
+      return enq_cheb_tail<TV, float>(P, V, g->f32.gx, g->f32.gy, g->f32.gz, st);
+    }
+  }
+  if (P.pc == TH_PC_ZLINE) {
+    k_zline<TV><<<P.gcol, P.tb, 0, st>>>(P.d, g->ctl, g->f32.gz, g->zl_m, g->zl_c, V.r, V.zc[0], g->partials,
+                                         g->partials_stride, g->counters);
+    TH_CHECK_LAUNCH();
+  }
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ enqueue: PCG iteration
+
+template <typename TV>
+static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t st, int parity) {
+  thermal_grid* g = P.g;
+  TV* zf = z_final(P, V);
+  if constexpr (sizeof(TV) == 8) {
+    k_spmv_dot<double, double><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, zf,
+                                                      V.p[parity], V.p[1 - parity], V.mu, g->partials,
+                                                      g->partials_stride, g->counters);
+  } else {
+    k_spmv_dot<float, float><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, zf,
+                                                    V.p[parity], V.p[1 - parity], V.mu, g->partials,
+                                                    g->partials_stride, g->counters);
+  }
+  TH_CHECK_LAUNCH();
+  TH_TRY((enq_update<TV, false>(P, V, st, 1 - parity, 1, 0)));
+  return enq_precond_tail<TV>(P, V, st);
+}
+
+// ------------------------------------------------------------------ enqueue: residual & control
+
+static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int count_outer, bool out64) {
+  thermal_grid* g = P.g;
+  const double* th = g->theta[0];
+  const double* thn = P.transient ? g->theta_n : nullptr;
+#define TH_RES(TP, TR, RP)                                                                                     \
+  k_residual<TP, TR><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64, g->tab, th, (const TP*)nullptr,             \
+                                            (const TP* const*)g->dev_ptrs, thn, RP, mode, count_outer,         \
+                                            g->partials, g->partials_stride, g->counters)
+  if (P.pdtype == TH_F32) {
+    if (out64) TH_RES(float, double, g->r64); else TH_RES(float, float, g->r32);
+  } else {
+    if (out64) TH_RES(double, double, g->r64); else TH_RES(double, float, g->r32);
+  }
+#undef TH_RES
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+static th_status enq_cond(cudaStream_t st, cudaGraphConditionalHandle h, const Ctl* ctl, int which) {
+  k_cond<<<1, 1, 0, st>>>(h, ctl, which);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+// Pieces of a solve, shared by the polled and the graph form.
+struct Pieces {
+  const Plan& P;
+  explicit Pieces(const Plan& p) : P(p) {}
+
+  // mixed: scale r, x = 0, z_0 = M r
+  th_status inner_init(cudaStream_t st) {
+    VecSet<float> V = vec32(P.g);
+    TH_TRY((enq_update<float, true>(P, V, st, 0, 1, 1)));
+    return enq_precond_tail<float>(P, V, st);
+  }
+  th_status inner_pair(cudaStream_t st) {
+    VecSet<float> V = vec32(P.g);
+    TH_TRY(enq_iteration<float>(P, V, st, 0));
+    return enq_iteration<float>(P, V, st, 1);
+  }
+  th_status outer_close(cudaStream_t st) {  // theta += ||r|| d ; r = b - A theta
+    k_theta_axpy<<<nb1(P.d.n), 256, 0, st>>>(P.d.n, P.g->ctl, P.g->theta[0], P.g->d32);
+    TH_CHECK_LAUNCH();
+    return enq_residual(P, st, 0, 1, false);
+  }
+  // fp64 path
+  th_status fp64_init(cudaStream_t st) {
+    TH_TRY(enq_residual(P, st, 1, 0, true));
+    VecSet<double> V = vec64(P.g);
+    TH_TRY((enq_update<double, true>(P, V, st, 0, 0, 0)));
+    return enq_precond_tail<double>(P, V, st);
+  }
+  th_status fp64_pair(cudaStream_t st) {
+    VecSet<double> V = vec64(P.g);
+    TH_TRY(enq_iteration<double>(P, V, st, 0));
+    return enq_iteration<double>(P, V, st, 1);
+  }
+};
+
+// ------------------------------------------------------------------ graph building
+
+struct GraphKey {
+  int kind, prec, pc, k, scaled, pdtype, lz;
+  double dt;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, dt) <
+           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.dt);
+  }
+};
+struct GraphEntry {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  CtlInit ci;  // options baked into the graph's control-block reset
+};
+struct GraphCache {
+  std::map<GraphKey, GraphEntry> m;
+  cudaStream_t cs[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+void graph_cache_free(GraphCache* c) {
+  if (!c) return;
+  for (auto& kv : c->m) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  for (auto& s : c->cs)
+    if (s) cudaStreamDestroy(s);
+  delete c;
+}
+
+template <class F>
+static th_status capture_body(cudaGraph_t body, cudaStream_t cs, F&& fill) {
+  TH_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  th_status st = fill(cs);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &out);
+  if (st != TH_OK) return st;
+  if (e != cudaSuccess) return th_fail(TH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  return TH_OK;
+}
+
+
+// Adds a WHILE node at the current position of the capture on `cs`: creates its
+// handle on the capturing graph, sets the first condition with k_cond(which) and
+// returns the (empty) body graph.
+static th_status begin_while(cudaStream_t cs, const Ctl* ctl, int which, cudaGraph_t* body,
+                             cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  TH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive) return th_fail(TH_ECUDA, "stream is not capturing");
+  TH_CUDA(cudaGraphConditionalHandleCreate(h, cg, 0, 0));
+  TH_TRY(enq_cond(cs, *h, ctl, which));
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  TH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &ed, &nd));
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = *h;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node;
+  TH_CUDA(cudaGraphAddNode(&node, cg, deps, ed, nd, &prm));
+  *body = prm.conditional.phGraph_out[0];
+  TH_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return TH_OK;
+}
+
+// One system solve as graph nodes on the capturing stream gc->cs[lvl]; nested loop
+// bodies are captured on gc->cs[lvl+1], gc->cs[lvl+2].
+static th_status emit_solve(const Plan& P, GraphCache* gc, int lvl) {
+  Pieces pcs(P);
+  Ctl* ctl = P.g->ctl;
+  cudaStream_t s = gc->cs[lvl];
+  if (P.prec == TH_PREC_FP64) {
+    TH_TRY(pcs.fp64_init(s));
+    cudaGraph_t bi;
+    cudaGraphConditionalHandle hi;
+    TH_TRY(begin_while(s, ctl, 0, &bi, &hi));
+    TH_TRY(capture_body(bi, gc->cs[lvl + 1], [&](cudaStream_t sb) -> th_status {
+      TH_TRY(pcs.fp64_pair(sb));
+      return enq_cond(sb, hi, ctl, 0);
+    }));
+    return enq_residual(P, s, 2, 0, true);
+  }
+  TH_TRY(enq_residual(P, s, 0, 0, false));
+  cudaGraph_t bo;
+  cudaGraphConditionalHandle ho;
+  TH_TRY(begin_while(s, ctl, 1, &bo, &ho));
+  return capture_body(bo, gc->cs[lvl + 1], [&](cudaStream_t sb) -> th_status {
+    TH_TRY(pcs.inner_init(sb));
+    cudaGraph_t bi;
+    cudaGraphConditionalHandle hi;
+    TH_TRY(begin_while(sb, ctl, 0, &bi, &hi));
+    TH_TRY(capture_body(bi, gc->cs[lvl + 2], [&](cudaStream_t sc) -> th_status {
+      TH_TRY(pcs.inner_pair(sc));
+      return enq_cond(sc, hi, ctl, 0);
+    }));
+    TH_TRY(pcs.outer_close(sb));
+    return enq_cond(sb, ho, ctl, 1);
+  });
+}
+
+static CtlInit ctl_init(const thermal_solve_opts* o, int n_steps, int spm, int n_maps) {
+  CtlInit ci;
+  ci.tol_rel = o->tol_rel;
+  ci.inner_tol = o->inner_tol;
+  ci.max_outer = o->precision == TH_PREC_FP64 ? 1 : o->max_outer;
+  ci.max_inner = o->precision == TH_PREC_FP64 ? o->max_iter : o->max_inner;
+  ci.n_steps = n_steps;
+  ci.steps_per_map = spm > 0 ? spm : 1;
+  ci.n_maps = n_maps > 0 ? n_maps : 1;
+  return ci;
+}
+
+static th_status build_graph(const Plan& P, int kind, const CtlInit& ci, GraphEntry* out) {
+  thermal_grid* g = P.g;
+  const double toff = (kind == KIND_ADJ) ? 0.0 : g->t_amb;
+  if (!g->graphs) {
+    g->graphs = new GraphCache();
+    for (auto& s : g->graphs->cs) TH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  }
+  GraphCache* gc = g->graphs;
+  Ctl* ctl = g->ctl;
+  const long long n = P.d.n;
+  cudaGraph_t G = nullptr;
+  TH_CUDA(cudaGraphCreate(&G, 0));
+  th_status st = capture_body(G, gc->cs[0], [&](cudaStream_t s0) -> th_status {
+    k_ctl_reset<<<1, 1, 0, s0>>>(ctl, ci);
+    TH_CHECK_LAUNCH();
+    const int prep = (kind == KIND_STEP) ? 2 : 1;
+    k_prepare<<<nb1(n), 256, 0, s0>>>(n, g->stage_T, toff, prep, g->theta[0], g->theta_n);
+    TH_CHECK_LAUNCH();
+    if (kind == KIND_RUN) {
+      cudaGraph_t bs;
+      cudaGraphConditionalHandle hs;
+      TH_TRY(begin_while(s0, ctl, 2, &bs, &hs));
+      TH_TRY(capture_body(bs, gc->cs[1], [&](cudaStream_t sb) -> th_status {
+        k_copy64<<<nb1(n), 256, 0, sb>>>(n, g->theta[0], g->theta_n);
+        TH_CHECK_LAUNCH();
+        k_step_begin<<<1, 1, 0, sb>>>(ctl);
+        TH_CHECK_LAUNCH();
+        TH_TRY(emit_solve(P, gc, 1));
+        k_step_end<<<1, 1, 0, sb>>>(ctl);
+        TH_CHECK_LAUNCH();
+        return enq_cond(sb, hs, ctl, 2);
+      }));
+    } else {
+      TH_TRY(emit_solve(P, gc, 0));
+    }
+    k_finalize<<<nb1(n), 256, 0, s0>>>(n, g->theta[0], toff, g->stage_T);
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  });
+  if (st != TH_OK) {
+    cudaGraphDestroy(G);
+    return st;
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ex, G, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(G);
+    return th_fail(TH_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+  }
+  out->graph = G;
+  out->exec = ex;
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ polled execution
+
+static th_status poll(thermal_grid* g, cudaStream_t s, Ctl* h) {
+  TH_CUDA(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  *h = *g->ctl_host;
+  return TH_OK;
+}
+
+// One system solve with host polling between launch chunks.
+static th_status polled_solve(const Plan& P, cudaStream_t s) {
+  thermal_grid* g = P.g;
+  Pieces pcs(P);
+  Ctl h;
+  if (P.prec == TH_PREC_FP64) {
+    TH_TRY(pcs.fp64_init(s));
+    TH_TRY(poll(g, s, &h));
+    int chunk = 4;
+    while (!h.done) {
+      for (int c = 0; c < chunk; ++c) TH_TRY(pcs.fp64_pair(s));
+      TH_TRY(poll(g, s, &h));
+      chunk = std::min(chunk * 2, 128);
+    }
+    return enq_residual(P, s, 2, 0, true);
+  }
+  TH_TRY(enq_residual(P, s, 0, 0, false));
+  TH_TRY(poll(g, s, &h));
+  while (!h.outer_done) {
+    TH_TRY(pcs.inner_init(s));
+    TH_TRY(poll(g, s, &h));
+    int chunk = 2;
+    while (!h.done) {
+      for (int c = 0; c < chunk; ++c) TH_TRY(pcs.inner_pair(s));
+      TH_TRY(poll(g, s, &h));
+      chunk = std::min(chunk * 2, 32);
+    }
+    TH_TRY(pcs.outer_close(s));
+    TH_TRY(poll(g, s, &h));
+  }
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ staging
+
+static th_status ensure_stage(thermal_grid* g, size_t pbytes) {
+  if (!g->stage_T) {
+    if (cudaMalloc((void**)&g->stage_T, sizeof(double) * (size_t)g->n) != cudaSuccess) {
+      cudaGetLastError();
+      return th_fail(TH_ENOMEM, "staging allocation failed");
+    }
+  }
+  if (!g->dev_ptrs) {
+    if (cudaMalloc((void**)&g->dev_ptrs, 256 * sizeof(void*)) != cudaSuccess) {
+      cudaGetLastError();
+      return th_fail(TH_ENOMEM, "pointer table allocation failed");
+    }
+  }
+  if (pbytes > g->stage_p_bytes) {
+    if (g->stage_p) cudaFree(g->stage_p);
+    g->stage_p = nullptr;
+    g->stage_p_bytes = 0;
+    if (cudaMalloc(&g->stage_p, pbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return th_fail(TH_ENOMEM, "power staging allocation of %zu bytes failed", pbytes);
+    }
+    g->stage_p_bytes = pbytes;
+  }
+  return TH_OK;
+}
+
+// Power maps -> device pointers in g->dev_ptrs (host maps are copied into stage_p).
+static th_status stage_power(thermal_grid* g, const void* const* maps, int n_maps, int pdtype, cudaStream_t s) {
+  if (n_maps < 1 || n_maps > 256) return th_fail(TH_EINVAL, "n_maps must lie in [1, 256]");
+  const size_t esz = pdtype == TH_F64 ? 8 : 4;
+  const size_t bytes = esz * (size_t)g->n;
+  bool any_host = false;
+  for (int i = 0; i < n_maps; ++i) {
+    if (!maps[i]) return th_fail(TH_EINVAL, "power map %d is NULL", i);
+    if (!is_device_pointer(maps[i])) any_host = true;
+  }
+  TH_TRY(ensure_stage(g, any_host ? bytes * n_maps : 0));
+  static thread_local std::vector<const void*> ptrs;
+  ptrs.assign(n_maps, nullptr);
+  for (int i = 0; i < n_maps; ++i) {
+    if (is_device_pointer(maps[i])) {
+      ptrs[i] = maps[i];
+    } else {
+      char* dst = (char*)g->stage_p + bytes * i;
+      TH_CUDA(cudaMemcpyAsync(dst, maps[i], bytes, cudaMemcpyHostToDevice, s));
+      ptrs[i] = dst;
+    }
+  }
+  TH_CUDA(cudaMemcpyAsync((void*)g->dev_ptrs, ptrs.data(), n_maps * sizeof(void*), cudaMemcpyHostToDevice, s));
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ solve driver
+
+static void fill_stats(const Plan& P, const Ctl& h, float ms, thermal_solve_stats* st) {
+  if (!st) return;
+  std::memset(st, 0, sizeof(*st));
+  st->status = h.status;
+  st->outer_it = P.prec == TH_PREC_FP64 ? std::max(1, h.steps_done) : h.outer_it;
+  st->inner_it = h.it_total;
+  st->n_spmv = h.n_spmv + h.it_total * (1 + P.pc_spmv) + (long long)h.n_inits * P.pc_spmv;
+  st->rel_res = h.rel_res;
+  st->t_solve_ms = ms;
+  st->lam_min = P.lmin;
+  st->lam_max = P.lmax;
+  st->steps = h.steps_done;
+}
+
+// kind: KIND_STEADY, KIND_STEP or KIND_RUN.  maps/n_maps: power maps; T: host or device.
+th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* maps, int n_maps, int pdtype,
+                       int spm, int n_steps, double* T, const thermal_solve_opts* o, thermal_solve_stats* stats,
+                       cudaStream_t s) {
+  if (!g || !T || !maps) return th_fail(TH_EINVAL, "NULL argument");
+  if (pdtype != TH_F32 && pdtype != TH_F64) return th_fail(TH_EINVAL, "power dtype must be TH_F32 or TH_F64");
+  TH_TRY(validate_opts(o));
+  if (o->lanczos_steps > 500) return th_fail(TH_EINVAL, "lanczos_steps must be <= 500");
+  cudaEvent_t e0, e1;
+  TH_CUDA(cudaEventCreate(&e0));
+  TH_CUDA(cudaEventCreate(&e1));
+  struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
+  Plan P;
+  const bool transient = (kind == KIND_STEP || kind == KIND_RUN);
+  const double toff = (kind == KIND_ADJ) ? 0.0 : g->t_amb;  // the adjoint state has no offset
+  TH_TRY(make_plan(g, transient ? dt : 0.0, o, pdtype, transient, P, s));
+  TH_TRY(ensure_stage(g, 0));
+  TH_TRY(stage_power(g, maps, n_maps, pdtype, s));
+  const size_t tb = sizeof(double) * (size_t)g->n;
+  const bool t_dev = is_device_pointer(T);
+  const bool need_T = transient || o->use_guess;
+  if (need_T) TH_CUDA(cudaMemcpyAsync(g->stage_T, T, tb, t_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  else TH_CUDA(cudaMemsetAsync(g->stage_T, 0, tb, s));
+  const CtlInit ci = ctl_init(o, kind == KIND_RUN ? n_steps : 1, spm, n_maps);
+  TH_CUDA(cudaEventRecord(e0, s));
+  if (o->use_graph) {
+    const GraphKey key{kind, P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.transient ? dt : 0.0};
+    if (!g->graphs) {
+      g->graphs = new GraphCache();
+      for (auto& sx : g->graphs->cs) TH_CUDA(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
+    }
+    auto it = g->graphs->m.find(key);
+    if (it != g->graphs->m.end() && std::memcmp(&it->second.ci, &ci, sizeof(CtlInit)) != 0) {
+      cudaGraphExecDestroy(it->second.exec);
+      cudaGraphDestroy(it->second.graph);
+      g->graphs->m.erase(it);
+      it = g->graphs->m.end();
+    }
+    if (it == g->graphs->m.end()) {
+      TH_CUDA(cudaStreamSynchronize(s));
+      GraphEntry ge;
+      TH_TRY(build_graph(P, kind, ci, &ge));
+      ge.ci = ci;
+      g->graphs->m[key] = ge;
+      it = g->graphs->m.find(key);
+      TH_CUDA(cudaEventRecord(e0, s));
+    }
+    TH_CUDA(cudaGraphLaunch(it->second.exec, s));
+  } else {
+    const long long n = P.d.n;
+    k_ctl_reset<<<1, 1, 0, s>>>(g->ctl, ci);
+    TH_CHECK_LAUNCH();
+    const int prep = (kind == KIND_STEP) ? 2 : 1;
+    k_prepare<<<nb1(n), 256, 0, s>>>(n, g->stage_T, toff, prep, g->theta[0], g->theta_n);
+    TH_CHECK_LAUNCH();
+    if (kind == KIND_RUN) {
+      Ctl h;
+      for (int step = 0; step < n_steps; ++step) {
+        k_copy64<<<nb1(n), 256, 0, s>>>(n, g->theta[0], g->theta_n);
+        TH_CHECK_LAUNCH();
+        k_step_begin<<<1, 1, 0, s>>>(g->ctl);
+        TH_CHECK_LAUNCH();
+        TH_TRY(polled_solve(P, s));
+        k_step_end<<<1, 1, 0, s>>>(g->ctl);
+        TH_CHECK_LAUNCH();
+        TH_TRY(poll(g, s, &h));
+        if (h.status == TH_EBREAKDOWN || h.status == TH_ENONFINITE) break;
+      }
+    } else {
+      TH_TRY(polled_solve(P, s));
+      if (kind == KIND_STEP) {
+        k_step_end<<<1, 1, 0, s>>>(g->ctl);
+        TH_CHECK_LAUNCH();
+      }
+    }
+    k_finalize<<<nb1(n), 256, 0, s>>>(n, g->theta[0], toff, g->stage_T);
+    TH_CHECK_LAUNCH();
+  }
+  TH_CUDA(cudaEventRecord(e1, s));
+  TH_CUDA(cudaMemcpyAsync(T, g->stage_T, tb, t_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  Ctl h;
+  TH_TRY(poll(g, s, &h));
+  float ms = 0.f;
+  TH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  fill_stats(P, h, ms, stats);
+  if (kind == KIND_STEP && stats) stats->steps = 1;
+  th_status res = (th_status)h.status;
+  if (res == TH_OK && !(h.rel_res <= o->tol_rel)) res = TH_ENOCONV;
+  if (stats) stats->status = res;
+  if (res != TH_OK) return th_fail(res, "solve ended with status %d (rel. residual %.3e, tol %.1e)", (int)res,
+                                   h.rel_res, o->tol_rel);
+  return TH_OK;
+}
+
+// ------------------------------------------------------------------ ABI
+
+#define ABI_BEGIN try {
+#define ABI_END                                                        \
+  }                                                                    \
+  catch (const std::bad_alloc&) {                                      \
+    return th_fail(TH_ENOMEM, "host allocation failed");               \
+  }                                                                    \
+  catch (...) {                                                        \
+    return th_fail(TH_ECUDA, "unexpected C++ exception inside libthermal"); \
+  }
+
+extern "C" th_status thermal_solve_steady(thermal_grid* g, const void* power, int power_dtype, double* T,
+                                          const thermal_solve_opts* opts, thermal_solve_stats* stats, void* stream) {
+  ABI_BEGIN
+  th_clear_error();
+  const void* maps[1] = {power};
+  return solver_drive(g, KIND_STEADY, 0.0, maps, 1, power_dtype, 1, 1, T, opts, stats, (cudaStream_t)stream);
+  ABI_END
+}
+
+extern "C" th_status thermal_step_transient(thermal_grid* g, const void* power, int power_dtype, double dt, double* T,
+                                            const thermal_solve_opts* opts, thermal_solve_stats* stats,
+                                            void* stream) {
+  ABI_BEGIN
+  th_clear_error();
+  if (!(dt > 0.0) || !std::isfinite(dt)) return th_fail(TH_EINVAL, "dt must be finite and > 0");
+  const void* maps[1] = {power};
+  return solver_drive(g, KIND_STEP, dt, maps, 1, power_dtype, 1, 1, T, opts, stats, (cudaStream_t)stream);
+  ABI_END
+}
+
+extern "C" th_status thermal_run_transient(thermal_grid* g, const void* const* power_maps, int n_maps, int power_dtype,
+                                           int steps_per_map, int n_steps, double dt, double* T,
+                                           const thermal_solve_opts* opts, thermal_solve_stats* stats, void* stream) {
+  ABI_BEGIN
+  th_clear_error();
+  if (!(dt > 0.0) || !std::isfinite(dt)) return th_fail(TH_EINVAL, "dt must be finite and > 0");
+  if (n_steps < 0 || steps_per_map < 1) return th_fail(TH_EINVAL, "n_steps >= 0 and steps_per_map >= 1 required");
+  if (!power_maps) return th_fail(TH_EINVAL, "power_maps is NULL");
+  if (n_steps == 0) return TH_OK;
+  return solver_drive(g, KIND_RUN, dt, power_maps, n_maps, power_dtype, steps_per_map, n_steps, T, opts, stats,
+               (cudaStream_t)stream);
+  ABI_END
+}
+
+extern "C" th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solve_opts* opts,
+                                             double* ritz_min, double* ritz_max, double* lam_min, double* lam_max,
+                                             void* stream) {
+  ABI_BEGIN
+  th_clear_error();
+  if (!g) return th_fail(TH_EINVAL, "grid is NULL");
+  TH_TRY(validate_opts(opts));
+  if (opts->lanczos_steps > 500) return th_fail(TH_EINVAL, "lanczos_steps must be <= 500");
+  return solver_spectral(g, dt, opts, ritz_min, ritz_max, lam_min, lam_max, (cudaStream_t)stream);
+  ABI_END
+}
+
+extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const thermal_solve_opts* opts, const float* r,
+                                           float* z, void* stream) {
+  ABI_BEGIN
+  th_clear_error();
+  if (!g || !r || !z) return th_fail(TH_EINVAL, "NULL argument");
+  TH_TRY(validate_opts(opts));
+  if (opts->lanczos_steps > 500) return th_fail(TH_EINVAL, "lanczos_steps must be <= 500");
+  cudaStream_t s = (cudaStream_t)stream;
+  thermal_solve_opts o = *opts;
+  o.precision = (opts->precision == TH_PREC_MIXED_IR_BF16) ? TH_PREC_MIXED_IR_BF16 : TH_PREC_MIXED_IR;
+  Plan P;
+  TH_TRY(make_plan(g, dt, &o, TH_F32, dt > 0.0, P, s));
+  const CtlInit ci = ctl_init(&o, 1, 1, 1);
+  k_ctl_reset<<<1, 1, 0, s>>>(g->ctl, ci);
+  TH_CHECK_LAUNCH();
+  const size_t bytes = sizeof(float) * (size_t)g->n;
+  TH_CUDA(cudaMemcpyAsync(g->r32, r, bytes, cudaMemcpyDeviceToDevice, s));
+  VecSet<float> V = vec32(g);
+  TH_TRY((enq_update<float, true>(P, V, s, 0, 1, 0)));
+  TH_TRY(enq_precond_tail<float>(P, V, s));
+  TH_CUDA(cudaMemcpyAsync(z, z_final(P, V), bytes, cudaMemcpyDeviceToDevice, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  return TH_OK;
+  ABI_END
+}
+
+// ------------------------------------------------------------------ kernel timing
+
+template <typename T>
+__global__ void k_fill(long long n, T* a, T v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+__global__ void k_ctl_timing(Ctl* c) {
+  Ctl z = {};
+  z.rz = 1.0; z.rz_next = 1.0; z.pAp = 1.0; z.rr0 = 1e30; z.inner_rel = 1e-20;
+  z.max_inner = 0x7fffffff; z.max_outer = 0x7fffffff; z.tol_rel = 0.0; z.inner_tol = 1e-20;
+  z.steps_per_map = 1; z.n_maps = 1;
+  *c = z;
+}
+
+extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
+  ABI_BEGIN
+  th_clear_error();
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 7) return th_fail(TH_EINVAL, "invalid argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  thermal_solve_opts o;
+  thermal_default_opts(&o);
+  o.precond = TH_PC_JACOBI;
+  o.precision = (kernel >= 5) ? TH_PREC_FP64 : TH_PREC_MIXED_IR;
+  Plan P;
+  TH_TRY(make_plan(g, dt, &o, TH_F32, dt > 0.0, P, s));
+  TH_TRY(ensure_stage(g, sizeof(float) * (size_t)g->n));
+  TH_TRY(grid_ensure_workspace(g, true, s));
+  const long long n = g->n;
+  const unsigned nb = nb1(n);
+  for (float* a : {g->r32, g->d32, g->mu32, g->p32[0], g->p32[1], g->zc32[0], g->zc32[1], g->zc32[2]})
+    k_fill<float><<<nb, 256, 0, s>>>(n, a, 1.0f);
+  for (double* a : {g->theta[0], g->theta_n, g->r64, g->mu64, g->p64[0], g->p64[1], g->zc64[0], g->zc64[1], g->zc64[2]})
+    k_fill<double><<<nb, 256, 0, s>>>(n, a, 1.0);
+  k_fill<float><<<nb, 256, 0, s>>>(n, (float*)g->stage_p, 1e-4f);
+  TH_CHECK_LAUNCH();
+  const void* pp[1] = {g->stage_p};
+  TH_CUDA(cudaMemcpyAsync((void*)g->dev_ptrs, pp, sizeof(void*), cudaMemcpyHostToDevice, s));
+  k_ctl_timing<<<1, 1, 0, s>>>(g->ctl);
+  TH_CHECK_LAUNCH();
+  VecSet<float> V = vec32(g);
+  VecSet<double> W = vec64(g);
+  const float c1 = 0.5f, c2 = 0.5f;
+  auto launch = [&]() -> th_status {
+    switch (kernel) {
+      case 0:
+        k_apply_f32<<<P.gb, P.tb, 0, s>>>(P.d, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->zc32[0], g->zc32[1]);
+        break;
+      case 1:
+        k_cheb<float, float, true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
+                                                                V.r, V.zc[0], V.zc[1], V.zc[2], V.invd, c1, c2,
+                                                                g->partials, g->partials_stride, g->counters);
+        break;
+      case 2:
+        k_cheb<float, __nv_bfloat16, true, false><<<P.gb, P.tb, 0, s>>>(
+            P.d, g->ctl, g->f16.gx, g->f16.gy, g->f16.gz, g->tab, V.r, V.zc[0], V.zc[1], V.zc[2], V.invd, c1, c2,
+            g->partials, g->partials_stride, g->counters);
+        break;
+      case 3:
+        k_spmv_dot<float, float><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
+                                                        V.zc[0], V.p[0], V.p[1], V.mu, g->partials,
+                                                        g->partials_stride, g->counters);
+        break;
+      case 4:
+        k_update<float, false, 1><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0], 1.0f,
+                                                        1, 1, 0, g->partials, g->partials_stride, g->counters);
+        break;
+      case 5:
+        k_residual<float, float><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f64, g->tab, g->theta[0], nullptr,
+                                                       (const float* const*)g->dev_ptrs,
+                                                       P.transient ? g->theta_n : nullptr, g->r32, 2, 0,
+                                                       g->partials, g->partials_stride, g->counters);
+        break;
+      case 6:
+        k_apply_f64<<<P.gb, P.tb, 0, s>>>(P.d, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, g->zc64[0], g->zc64[1]);
+        break;
+      default:
+        k_cheb<double, double, true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f64.gx, g->f64.gy, g->f64.gz,
+                                                                  g->tab, W.r, W.zc[0], W.zc[1], W.zc[2], W.invd,
+                                                                  0.5, 0.5, g->partials, g->partials_stride,
+                                                                  g->counters);
+        break;
+    }
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  };
+  TH_TRY(launch());  // warm-up
+  cudaEvent_t e0, e1;
+  TH_CUDA(cudaEventCreate(&e0));
+  TH_CUDA(cudaEventCreate(&e1));
+  struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
+  TH_CUDA(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) TH_TRY(launch());
+  TH_CUDA(cudaEventRecord(e1, s));
+  TH_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  TH_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  *ms = (double)t / reps;
+  return TH_OK;
+  ABI_END
+}

@@ -1,0 +1,110 @@
+"""The C ABI without a GPU: the library builds, loads, exports every declared entry
+point, and rejects invalid arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "thermal.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(thermal_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2606_17850_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_expected_boundary():
+    names = declared_functions()
+    for must in ("thermal_grid_create", "thermal_solve_steady", "thermal_step_transient", "thermal_grad",
+                 "thermal_run_transient", "thermal_solve_batched", "thermal_apply"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2606_17850_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+
+
+def test_default_opts(lib):
+    from paper_2606_17850_gb300 import _lib
+    o = _lib.default_opts()
+    assert o.tol_rel == 1e-8 and o.cheb_degree == 30 and o.precond == _lib.TH_PC_CHEB
+    assert o.precision == _lib.TH_PREC_MIXED_IR
+    assert lib.thermal_version().decode().endswith("sm_103a")
+
+
+def _arr(v):
+    return (C.c_double * len(v))(*v)
+
+
+@pytest.mark.parametrize("nx,ny,L,k,c,h", [
+    (0, 4, 2, [1.0, 1.0], [1.0, 1.0], 1.0),
+    (4, -1, 2, [1.0, 1.0], [1.0, 1.0], 1.0),
+    (4, 4, 0, [1.0], [1.0], 1.0),
+    (4, 4, 2, [1.0, -2.0], [1.0, 1.0], 1.0),
+    (4, 4, 2, [1.0, float("nan")], [1.0, 1.0], 1.0),
+    (4, 4, 2, [1.0, 1.0], [0.0, 1.0], 1.0),
+    (4, 4, 2, [1.0, 1.0], [1.0, 1.0], -1.0),
+    (4, 4, 2, [1.0, 1.0], [1.0, 1.0], float("inf")),
+    (4, 4, 40, [1.0] * 40, [1.0] * 40, 1.0),
+])
+def test_grid_create_rejects_invalid(lib, nx, ny, L, k, c, h):
+    from paper_2606_17850_gb300 import _lib
+    out = C.c_void_p()
+    st = lib.thermal_grid_create(nx, ny, L, _arr(k), _arr(c), h, C.byref(out))
+    assert st == _lib.TH_EINVAL
+    assert out.value is None
+    assert lib.thermal_last_error().decode()
+
+
+def test_null_arguments_rejected(lib):
+    from paper_2606_17850_gb300 import _lib
+    assert lib.thermal_grid_create(4, 4, 1, _arr([1.0]), None, 1.0, None) == _lib.TH_EINVAL
+    assert lib.thermal_grid_set_geometry(None, 1.0, 1.0, _arr([1.0]), 0.0) == _lib.TH_EINVAL
+    o = _lib.default_opts()
+    st = _lib.SolveStats()
+    assert lib.thermal_solve_steady(None, None, 0, None, C.byref(o), C.byref(st), None) == _lib.TH_EINVAL
+    assert lib.thermal_grid_destroy(None) == _lib.TH_OK
+
+
+def test_status_enum_matches_header():
+    from paper_2606_17850_gb300 import _lib
+    text = open(HEADER).read()
+    for i, name in enumerate(_lib.STATUS_NAMES):
+        m = re.search(rf"\b{name}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == i, name
+
+
+def test_struct_layouts_match_header(lib):
+    """Field order of the option/statistics structs in the binding follows the header."""
+    from paper_2606_17850_gb300 import _lib
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for cname, py in (("thermal_solve_opts", _lib.SolveOpts), ("thermal_solve_stats", _lib.SolveStats)):
+        body = re.search(r"typedef struct %s \{(.*?)\}" % cname, text, re.S).group(1)
+        fields = re.findall(r"\b(\w+)(?:\[\d+\])?;", body)
+        assert fields == [f for f, _ in py._fields_], cname
+
+
+def test_oracle_zline_exact_without_inplane_coupling():
+    """On a 1x1 column grid the z-line block is the whole matrix: its inverse is exact."""
+    import thermal_inputs as ti
+    from oracle import discretisation as disc, krylov
+    st = ti.stack_c2()
+    A = disc.assemble(1, 1, st)
+    r = ti.random_vector(st.L, 3)
+    np.testing.assert_allclose(krylov.zline(A, 1, 1, st.L)(r), np.linalg.solve(A.toarray(), r), rtol=1e-12)

@@ -1,0 +1,310 @@
+"""GPU path vs the CPU oracle, through the C ABI (libthermal.so).
+
+Grids span several 32x8 thread tiles with ragged tails (nx, ny not multiples of
+the tile) and the stacks of the measured workloads.  Tolerances follow from the
+arithmetic:
+
+* FP64 stencil: componentwise |dy_i| <= 1e-14 * sum_j |a_ij x_j| (a handful of
+  roundings of size 2^-53 per term).
+* FP32 stencil: coefficients rounded to FP32 (2^-24) and ~13 FP32 operations:
+  |dy_i| <= 2e-6 * sum_j |a_ij x_j|.  BF16 coefficients (2^-9): 1e-2.
+* Solves: max|T - T_ref| / max|T_ref - T_amb| <= 1e-6 at tol_rel 1e-10 (FP64 and
+  mixed paths), the target accuracy of the method on this hardware.
+"""
+import numpy as np
+import pytest
+
+import thermal_inputs as ti
+from oracle import adjoint as oadj, discretisation as disc, krylov, solve as osolve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as ge
+    ge.build()
+
+
+def grid_of(nx, ny, st):
+    from paper_2606_17850_gb300 import ThermalGrid
+    return ThermalGrid.from_stack(nx, ny, st)
+
+
+def cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+SHAPES = [(70, 19, "c1"), (37, 45, "c2"), (33, 9, "mol"), (5, 3, "c2")]
+STACKS = {"c1": ti.stack_c1, "c2": ti.stack_c2, "mol": ti.stack_mol}
+
+
+# ----------------------------------------------------------------- A1: setup
+
+@pytest.mark.parametrize("nx,ny,mk", SHAPES)
+@pytest.mark.parametrize("dt", [0.0, 1e-4])
+def test_faces_and_diagonal(nx, ny, mk, dt):
+    st = STACKS[mk]()
+    A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None).tocsr()
+    g = grid_of(nx, ny, st)
+    f = {k: v.cpu().numpy() for k, v in g.faces(dt).items()}
+    n = nx * ny * st.L
+    i = np.arange(n)
+    x = i % nx
+    y = (i // nx) % ny
+    z = i // (nx * ny)
+    want_gx = np.where(x + 1 < nx, -np.asarray(A[i, np.minimum(i + 1, n - 1)]).ravel(), 0.0)
+    want_gy = np.where(y + 1 < ny, -np.asarray(A[i, np.minimum(i + nx, n - 1)]).ravel(), 0.0)
+    want_gz = np.where(z + 1 < st.L, -np.asarray(A[i, np.minimum(i + nx * ny, n - 1)]).ravel(), 0.0)
+    np.testing.assert_allclose(f["gx"], want_gx, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(f["gy"], want_gy, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(f["gz"], want_gz, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(f["diag"], A.diagonal(), rtol=1e-14, atol=0)
+
+
+# ----------------------------------------------------------------- A2: stencil
+
+@pytest.mark.parametrize("nx,ny,mk", SHAPES)
+@pytest.mark.parametrize("dt", [0.0, 1e-4])
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-14), ("mixed", 2e-6), ("mixed_bf16", 1e-2)])
+def test_stencil_product(nx, ny, mk, dt, prec, rtol):
+    st = STACKS[mk]()
+    A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None).tocsr()
+    g = grid_of(nx, ny, st)
+    xh = ti.random_vector(A.shape[0], 21, lo=-3.0, hi=5.0)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    xd = cuda(xh, dtype)
+    y = g.apply(xd, dt, prec).cpu().double().numpy()
+    x_used = xd.cpu().double().numpy()          # the rounded input both sides see
+    y_ref = A @ x_used
+    bound = abs(A) @ np.abs(x_used)
+    assert np.all(np.abs(y - y_ref) <= rtol * bound), np.max(np.abs(y - y_ref) / bound)
+
+
+def test_stencil_symmetry_fp64():
+    st = ti.stack_c2()
+    g = grid_of(41, 23, st)
+    n = 41 * 23 * st.L
+    x = cuda(ti.random_vector(n, 1))
+    yv = cuda(ti.random_vector(n, 2))
+    a = torch.dot(g.apply(x, 0.0, "fp64"), yv).item()
+    b = torch.dot(x, g.apply(yv, 0.0, "fp64")).item()
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+
+
+# ----------------------------------------------------------------- A3/A4: preconditioners
+
+@pytest.mark.parametrize("dt", [0.0, 1e-4])
+def test_lanczos_matches_oracle(dt):
+    st = ti.stack_c2()
+    nx, ny = 45, 38
+    g = grid_of(nx, ny, st)
+    A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None)
+    op, _ = krylov.jacobi_scaled(A)
+    a, b = krylov.lanczos(op, krylov.splitmix64_uniform(A.shape[0], 0x5EED), 50)
+    lo, hi = krylov.ritz_extremes(a, b)
+    rmin, rmax, lmin, lmax = g.spectral_bounds(dt, lanczos_steps=50, cheb_scaled=1)
+    assert abs(rmax - hi) <= 1e-3 * hi
+    assert abs(rmin - lo) <= 2e-2 * lo
+    assert abs(lmax - 1.05 * rmax) <= 1e-12 * lmax
+
+
+@pytest.mark.parametrize("pc", ["none", "jacobi", "cheb", "zline"])
+@pytest.mark.parametrize("scaled", [1, 0])
+def test_preconditioner_apply(pc, scaled):
+    if pc != "cheb" and scaled == 0:
+        pytest.skip("scaling only applies to Chebyshev")
+    st = ti.stack_c2()
+    nx, ny, dt = 37, 29, 1e-4
+    g = grid_of(nx, ny, st)
+    A = disc.assemble(nx, ny, st, dt=dt)
+    r = ti.random_vector(A.shape[0], 5).astype(np.float32)
+    k = 12
+    z = g.precond(cuda(r), dt, precond=pc, cheb_degree=k, cheb_scaled=scaled).cpu().double().numpy()
+    r64 = r.astype(np.float64)
+    if pc == "none":
+        ref = r64
+    elif pc == "jacobi":
+        ref = r64 / A.diagonal()
+    elif pc == "zline":
+        ref = krylov.zline(A, nx, ny, st.L)(r64)
+    else:
+        _, _, lmin, lmax = g.spectral_bounds(dt, cheb_scaled=scaled)
+        D = A.diagonal()
+        op = (lambda v: (A @ v) / D) if scaled else (lambda v: A @ v)
+        ref = krylov.chebyshev(op, r64 / D if scaled else r64, lmin, lmax, k)
+    np.testing.assert_allclose(z, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
+
+
+# ----------------------------------------------------------------- A5/A6: steady solves
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
+@pytest.mark.parametrize("pc", ["cheb", "jacobi", "none", "zline"])
+def test_steady_solve_c1(prec, pc):
+    inst = ti.c1(dtype=np.float32)
+    st = inst.stack
+    g = grid_of(inst.nx, inst.ny, st)
+    T, stats = g.solve_steady(cuda(inst.power), precision=prec, precond=pc, cheb_degree=10, tol_rel=1e-10)
+    T_ref = osolve.steady(inst.nx, inst.ny, st, inst.power.astype(np.float64))
+    err = osolve.rise_relative_error(T.cpu().numpy(), T_ref, st.t_amb)
+    assert stats["status"] == 0 and stats["rel_res"] <= 1e-10
+    assert err <= 1e-6, err
+    A = disc.assemble(inst.nx, inst.ny, st)
+    b = disc.rhs_steady(inst.nx, inst.ny, st, inst.power.astype(np.float64))
+    assert osolve.rel_residual(A, T.cpu().numpy(), b, st.t_amb) <= 2e-10
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_steady_ragged_graph(graph, prec):
+    st = ti.stack_c2()
+    nx, ny = 45, 27
+    dens = [ti.density_floorplan(nx, ny, s) for s in (8, 9)]
+    P = ti.power_cells(st, nx, ny, dens, np.float64)
+    g = grid_of(nx, ny, st)
+    T, stats = g.solve_steady(cuda(P), precision=prec, precond="cheb", cheb_degree=16, tol_rel=1e-10,
+                              use_graph=graph)
+    T_ref = osolve.steady(nx, ny, st, P)
+    assert stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), T_ref, st.t_amb) <= 1e-6
+    # a second call reuses the cached graph and must give the same answer
+    T2, _ = g.solve_steady(cuda(P), precision=prec, precond="cheb", cheb_degree=16, tol_rel=1e-10,
+                           use_graph=graph)
+    np.testing.assert_array_equal(T.cpu().numpy(), T2.cpu().numpy())
+
+
+def test_steady_host_buffers_and_guess():
+    inst = ti.c1(nx=40, ny=33, dtype=np.float32)
+    st = inst.stack
+    g = grid_of(inst.nx, inst.ny, st)
+    P = torch.from_numpy(inst.power)                   # host memory
+    T = torch.full((inst.n,), 60.0, dtype=torch.float64)  # host initial guess
+    T, stats = g.solve_steady(P, T=T, tol_rel=1e-10, use_guess=1)
+    T_ref = osolve.steady(inst.nx, inst.ny, st, inst.power.astype(np.float64))
+    assert osolve.rise_relative_error(T.numpy(), T_ref, st.t_amb) <= 1e-6
+
+
+def test_energy_balance_gpu():
+    inst = ti.c1(dtype=np.float32)
+    st = inst.stack
+    g = grid_of(inst.nx, inst.ny, st)
+    T, _ = g.solve_steady(cuda(inst.power), tol_rel=1e-11)
+    top = T.cpu().numpy()[(st.L - 1) * inst.nx * inst.ny:]
+    out = np.sum(st.h * st.dx * st.dy * (top - st.t_amb))
+    assert abs(out - inst.power.astype(np.float64).sum()) / inst.power.sum() < 1e-9
+
+
+# ----------------------------------------------------------------- A7/A8: transient
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_transient_step(prec):
+    st = ti.stack_c2()
+    nx, ny, dt = 50, 35, 1e-4
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (30, 31)], np.float32)
+    g = grid_of(nx, ny, st)
+    T0 = np.full(nx * ny * st.L, st.t_amb)
+    T0[::7] += 3.0
+    T = cuda(T0.copy())
+    T, stats = g.step_transient(cuda(P), dt, T, precision=prec, tol_rel=1e-10, cheb_degree=6)
+    ref = osolve.transient(nx, ny, st, [P.astype(np.float64)], dt, T0)[0]
+    assert stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_run_transient_schedule(graph, prec):
+    st = ti.stack_c2()
+    nx, ny, dt = 40, 26, 1e-4
+    maps = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s + j) for j in (0, 1)], np.float32)
+            for s in (30, 32)]
+    n_steps, spm = 7, 3
+    g = grid_of(nx, ny, st)
+    T = cuda(np.full(nx * ny * st.L, st.t_amb))
+    T, stats = g.run_transient([cuda(m) for m in maps], spm, n_steps, dt, T, precision=prec, tol_rel=1e-10,
+                               cheb_degree=6, use_graph=graph)
+    sched = [maps[(s // spm) % 2].astype(np.float64) for s in range(n_steps)]
+    ref = osolve.transient(nx, ny, st, sched, dt, np.full(nx * ny * st.L, st.t_amb))[-1]
+    assert stats["steps"] == n_steps and stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+# ----------------------------------------------------------------- A10: adjoint
+
+def test_lse_and_adjoint_gradient():
+    st = ti.stack_c1()
+    nx, ny = 34, 30
+    P = ti.power_cells(st, nx, ny, [ti.density_uniform_hotspots(nx, ny, 9)], np.float64)
+    mask = oadj.silicon_mask(nx, ny, st, st.power_layers())
+    g = grid_of(nx, ny, st)
+    T, _ = g.solve_steady(cuda(P), tol_rel=1e-12, precision="fp64")
+    J, w = g.hotspot_lse(T, st.power_layers(), 2.0)
+    J_ref, dJdP_ref, dJdk_ref, _, _ = oadj.gradient(nx, ny, st, P, mask, 2.0)
+    assert abs(J - J_ref) <= 1e-9 * abs(J_ref)
+    dJdP, dJdk, _ = g.grad(T, w, dJdP_dtype=torch.float64, tol_rel=1e-12, precision="mixed")
+    np.testing.assert_allclose(dJdP.cpu().numpy(), dJdP_ref, rtol=1e-6, atol=1e-6 * np.abs(dJdP_ref).max())
+    np.testing.assert_allclose(dJdk, dJdk_ref, rtol=1e-6, atol=1e-9 * np.abs(dJdk_ref).max())
+
+
+def test_autograd_function():
+    from paper_2606_17850_gb300 import HotspotLSE, SteadyAdjoint
+    st = ti.stack_c1()
+    nx, ny = 20, 18
+    P = ti.power_cells(st, nx, ny, [ti.density_uniform_hotspots(nx, ny, 4)], np.float32)
+    g = grid_of(nx, ny, st)
+    Pt = cuda(P).requires_grad_(True)
+    kt = torch.tensor(st.k(), dtype=torch.float64, requires_grad=True)
+    opts = dict(tol_rel=1e-12, precision="mixed")
+    T = SteadyAdjoint.apply(g, Pt, kt, opts)
+    J = HotspotLSE.apply(g, T, st.power_layers(), 2.0)
+    J.backward()
+    mask = oadj.silicon_mask(nx, ny, st, st.power_layers())
+    _, dJdP_ref, dJdk_ref, _, _ = oadj.gradient(nx, ny, st, P.astype(np.float64), mask, 2.0)
+    np.testing.assert_allclose(Pt.grad.cpu().double().numpy(), dJdP_ref, rtol=1e-5, atol=1e-6 * np.abs(dJdP_ref).max())
+    np.testing.assert_allclose(kt.grad.numpy(), dJdk_ref, rtol=1e-5)
+
+
+# ----------------------------------------------------------------- A9: batched
+
+def test_batched_matches_individual():
+    from paper_2606_17850_gb300 import solve_batched
+    insts = ti.c4_instances(n=5, scale=16)
+    grids = [grid_of(i.nx, i.ny, i.stack) for i in insts]
+    powers = [cuda(i.power) for i in insts]
+    Ts = [torch.empty(i.n, dtype=torch.float64, device="cuda") for i in insts]
+    stats = solve_batched(grids, powers, Ts, tol_rel=1e-10, cheb_degree=8)
+    for inst, T, s in zip(insts, Ts, stats):
+        ref = osolve.steady(inst.nx, inst.ny, inst.stack, inst.power.astype(np.float64))
+        assert s["status"] == 0
+        assert osolve.rise_relative_error(T.cpu().numpy(), ref, inst.stack.t_amb) <= 1e-6
+
+
+# ----------------------------------------------------------------- errors
+
+def test_nonfinite_power_reported():
+    from paper_2606_17850_gb300 import ThermalError
+    inst = ti.c1(nx=16, ny=16)
+    g = grid_of(16, 16, inst.stack)
+    P = inst.power.copy()
+    P[5] = np.nan
+    with pytest.raises(ThermalError) as e:
+        g.solve_steady(cuda(P))
+    assert e.value.status == 6
+    T, st = g.solve_steady(cuda(inst.power))   # the grid stays usable
+    assert st["status"] == 0
+
+
+def test_invalid_options_rejected():
+    from paper_2606_17850_gb300 import ThermalError
+    inst = ti.c1(nx=8, ny=8)
+    g = grid_of(8, 8, inst.stack)
+    with pytest.raises(ThermalError):
+        g.solve_steady(cuda(inst.power), inner_tol=2.0)
+    with pytest.raises(ThermalError):
+        g.solve_steady(cuda(inst.power), cheb_degree=0)
