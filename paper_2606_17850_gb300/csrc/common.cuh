@@ -58,7 +58,8 @@ struct Ctl {
   double rr64;       // ||b - A theta||^2 (FP64)
   double rel_res;    // sqrt(rr64 / bb)
   int outer_done;
-  int outer_it;
+  int outer_it;       // refinement steps, summed over time steps
+  int outer_it_step;  // refinement steps of the current system
   int max_outer;
   int max_inner;
   double tol_rel;
@@ -71,7 +72,28 @@ struct Ctl {
   int steps_done;
   int n_inits;      // inner solves started
   long long lanczos_spmv;
+  // scalars precomputed once by the last block of the kernel that produces them,
+  // so no thread of the next kernel does FP64 arithmetic (FP64 is ~1/64 of FP32 on GB300)
+  double alpha_d, beta_d;  // alpha = rz/pAp, beta = rz_next/rz
+  float alpha_f, beta_f;
+  double rnorm;            // ||r|| of the last FP64 residual
+  float rscale_f;          // 1/||r||
+  float pad_f;
 };
+
+template <typename T> __device__ __forceinline__ T ctl_alpha(const Ctl* c);
+template <> __device__ __forceinline__ float ctl_alpha<float>(const Ctl* c) { return __ldcg(&c->alpha_f); }
+template <> __device__ __forceinline__ double ctl_alpha<double>(const Ctl* c) { return __ldcg(&c->alpha_d); }
+template <typename T> __device__ __forceinline__ T ctl_beta(const Ctl* c);
+template <> __device__ __forceinline__ float ctl_beta<float>(const Ctl* c) { return __ldcg(&c->beta_f); }
+template <> __device__ __forceinline__ double ctl_beta<double>(const Ctl* c) { return __ldcg(&c->beta_d); }
+
+// last-block helper: beta for the next search direction once rz_next is known
+__device__ __forceinline__ void ctl_set_beta(Ctl* c) {
+  const double b = (c->first || !(c->rz != 0.0)) ? 0.0 : c->rz_next / c->rz;
+  c->beta_d = b;
+  c->beta_f = (float)b;
+}
 
 __device__ __forceinline__ float ldc(const float* p) { return __ldg(p); }
 __device__ __forceinline__ double ldc(const double* p) { return __ldg(p); }

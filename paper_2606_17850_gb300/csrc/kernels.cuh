@@ -38,6 +38,7 @@ __global__ void k_ctl_reset(Ctl* c, CtlInit in) {
 __global__ void k_step_begin(Ctl* c) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   c->outer_done = 0;
+  c->outer_it_step = 0;
   c->done = 0;
   c->rel_res = 1.0;
 }
@@ -90,8 +91,8 @@ __global__ void k_theta_axpy(long long n, const Ctl* ctl, double* __restrict__ t
   if (ld_int(&ctl->outer_done)) return;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double sc = ld_dbl(&ctl->rr64);  // holds ||r|| of the residual the inner solve was given
-  theta[i] += sqrt(sc) * (double)d[i];
+  const double sc = ld_dbl(&ctl->rnorm);  // ||r|| of the residual the inner solve was given
+  theta[i] += sc * (double)d[i];
 }
 
 // ---------------------------------------------------------------- FP64 residual
@@ -99,14 +100,16 @@ __global__ void k_theta_axpy(long long n, const Ctl* ctl, double* __restrict__ t
 // r = b - A theta in FP64 (FP64 faces), b = P + cdt * theta_n (theta_n optional).
 // Power map: P, or ptab[(step / steps_per_map) % n_maps] when ptab != NULL.
 // Reduces ||r||^2 and ||b||^2 (squares in FP32, partial sums in FP64).
-// mode 0: refinement (outer) decision; mode 1: start of the plain FP64 PCG
-// (sets rr0 and the target); mode 2: final residual for statistics only.
+// The last block takes the outer-loop decision on the true FP64 residual:
+// mode 0: iterative refinement (the FP32 inner solve must reduce r by inner_rel);
+// mode 1: plain FP64 PCG restarted from the true residual (reduce to 0.5 tol);
+// mode 2: statistics only.
 template <typename TP, typename TR>
 __global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, const double* __restrict__ theta,
                            const TP* __restrict__ P, const TP* const* ptab, const double* __restrict__ theta_n,
                            TR* __restrict__ r, int mode, int count_outer, double* partials, int stride,
                            unsigned* counter) {
-  if (mode == 0 && ld_int(&ctl->outer_done)) return;
+  if (mode != 2 && ld_int(&ctl->outer_done)) return;
   const Cell c = cell_of(d);
   if (ptab) {
     const int st = ld_int(&ctl->step), spm = ctl->steps_per_map, nm = ctl->n_maps;
@@ -132,34 +135,31 @@ __global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, con
   const double rr = tot[0], bb = tot[1];
   ctl->rr64 = rr;
   ctl->bb = bb;
+  ctl->rnorm = sqrt(rr);
+  ctl->rscale_f = (rr > 0.0) ? (float)(1.0 / sqrt(rr)) : 1.0f;
   ctl->n_spmv += 1;
   const double rel = (bb > 0.0) ? sqrt(rr / bb) : 0.0;
   ctl->rel_res = rel;
   if (mode == 2) return;
-  if (mode == 1) {  // plain FP64 PCG start
-    ctl->rr0 = rr;
-    ctl->rr = rr;
-    ctl->inner_rel = (rr > 0.0) ? ctl->tol_rel * sqrt(bb / rr) : 0.0;
-    ctl->it = 0;
-    ctl->first = 1;
-    ctl->done = (rel <= ctl->tol_rel) || !(rr == rr);
-    if (!isfinite(rr)) ctl->status = 6;
-    return;
+  if (count_outer) {
+    ctl->outer_it += 1;
+    ctl->outer_it_step += 1;
   }
-  if (count_outer) ctl->outer_it += 1;
   if (!isfinite(rr) || !isfinite(bb)) {
     ctl->status = 6;
     ctl->outer_done = 1;
   } else if (rel <= ctl->tol_rel) {
     ctl->outer_done = 1;
-  } else if (ctl->outer_it >= ctl->max_outer) {
+  } else if (ctl->outer_it_step >= ctl->max_outer) {
     ctl->status = 4;
     ctl->outer_done = 1;
-  } else {
-    // reduce the residual as far as this step needs, never less than inner_tol
+  } else if (mode == 0) {
+    // reduce the residual as far as this system needs, never less than inner_tol
     double want = 0.3 * ctl->tol_rel / rel;
     if (want > 0.5) want = 0.5;
     ctl->inner_rel = want > ctl->inner_tol ? want : ctl->inner_tol;
+  } else {
+    ctl->inner_rel = 0.5 * ctl->tol_rel / rel;
   }
 }
 
@@ -177,7 +177,7 @@ __global__ void k_spmv_dot(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC
   if (ld_int(&ctl->done)) return;
   const Cell c = cell_of(d);
   const int first = ld_int(&ctl->first);
-  const TV beta = first ? (TV)0 : (TV)(ld_dbl(&ctl->rz_next) / ld_dbl(&ctl->rz));
+  const TV beta = first ? (TV)0 : ctl_beta<TV>(ctl);
   TV v[1] = {(TV)0};
   if (c.valid) {
     auto pv = [&](long long j) -> TV { return first ? z[j] : z[j] + beta * p_old[j]; };
@@ -194,6 +194,9 @@ __global__ void k_spmv_dot(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC
   ctl->pAp = pAp;
   ctl->rz = ctl->rz_next;
   ctl->first = 0;
+  const double al = (pAp > 0.0) ? ctl->rz / pAp : 0.0;
+  ctl->alpha_d = al;
+  ctl->alpha_f = (float)al;
   if (!(pAp > 0.0)) {
     ctl->status = isfinite(pAp) ? 5 : 6;
     ctl->done = 1;
@@ -213,12 +216,9 @@ __global__ void k_update(Dims d, Ctl* ctl, TV* __restrict__ x, const TV* __restr
   if (INIT && ld_int(&ctl->outer_done)) return;
   const Cell c = cell_of(d);
   TV alpha = (TV)0;
-  if (!INIT) alpha = (TV)(ld_dbl(&ctl->rz) / ld_dbl(&ctl->pAp));
+  if (!INIT) alpha = ctl_alpha<TV>(ctl);
   TV rs = (TV)1;
-  if (INIT && scale_r) {
-    const double rr = ld_dbl(&ctl->rr64);
-    rs = (TV)(rr > 0.0 ? 1.0 / sqrt(rr) : 1.0);
-  }
+  if (INIT && scale_r) rs = (TV)__ldcg(&ctl->rscale_f);
   TV v[2] = {(TV)0, (TV)0};
   if (c.valid) {
     TV ri = r[c.i];
@@ -244,7 +244,10 @@ __global__ void k_update(Dims d, Ctl* ctl, TV* __restrict__ x, const TV* __restr
   if (!grid_reduce<TV, 2>(v, partials, stride, counter, tot)) return;
   const double rr = tot[0];
   ctl->rr = rr;
-  if (rz_here) ctl->rz_next = tot[1];
+  if (rz_here) {
+    ctl->rz_next = tot[1];
+    if (!INIT) ctl_set_beta(ctl);
+  }
   if (INIT) {
     ctl->rr0 = rr;
     ctl->it = 0;
@@ -305,6 +308,7 @@ __global__ void k_cheb(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC* __
   double tot[1];
   if (!grid_reduce<TV, 1>(v, partials, stride, counter, tot)) return;
   ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
 }
 
 // z-line block Jacobi: per (x, y) column, solve the tridiagonal system with
@@ -339,6 +343,7 @@ __global__ void k_zline(Dims d, Ctl* ctl, const float* __restrict__ gz, const fl
   double tot[1];
   if (!grid_reduce<TV, 1>(v, partials, stride, counter, tot)) return;
   ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
 }
 
 // ---------------------------------------------------------------- Lanczos (FP32)
@@ -365,7 +370,11 @@ __global__ void k_lz_start(Dims d, Ctl* ctl, float* __restrict__ w, unsigned lon
   }
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
-  lz[512] = sqrt(tot[0]);
+  const double nr = sqrt(tot[0]);
+  float* lzf = (float*)(lz + 3072);
+  lz[512] = nr;
+  lzf[512] = (float)(1.0 / nr);
+  lzf[1024] = (float)nr;
 }
 
 // v_j = w / nrm[j] (stored), u = Op v_j with Op = A or S A S (S = D^{-1/2}),
@@ -376,7 +385,7 @@ __global__ void k_lz_spmv(Dims d, Ctl* ctl, const float* __restrict__ gx, const 
                           const float* __restrict__ w, float* __restrict__ vj, float* __restrict__ u, double* lz,
                           int j, double* partials, int stride, unsigned* counter) {
   const Cell c = cell_of(d);
-  const float inv = (float)(1.0 / ld_dbl(lz + 512 + j));
+  const float inv = __ldcg((const float*)(lz + 3072) + 512 + j);
   float v[1] = {0.f};
   if (c.valid) {
     auto val = [&](long long k) -> float {
@@ -394,6 +403,7 @@ __global__ void k_lz_spmv(Dims d, Ctl* ctl, const float* __restrict__ gx, const 
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
   lz[j] = tot[0];
+  ((float*)(lz + 3072))[j] = (float)tot[0];
   ctl->lanczos_spmv += 1;
 }
 
@@ -402,8 +412,9 @@ __global__ void k_lz_update(Dims d, Ctl* ctl, const float* __restrict__ u, const
                             const float* __restrict__ vprev, float* __restrict__ w, double* lz, int j,
                             double* partials, int stride, unsigned* counter) {
   const Cell c = cell_of(d);
-  const float a = (float)ld_dbl(lz + j);
-  const float b = (float)ld_dbl(lz + 512 + j);
+  const float* lzf = (const float*)(lz + 3072);
+  const float a = __ldcg(lzf + j);
+  const float b = __ldcg(lzf + 1024 + j);
   float v[1] = {0.f};
   if (c.valid) {
     float wi = u[c.i] - a * vj[c.i];
@@ -413,5 +424,9 @@ __global__ void k_lz_update(Dims d, Ctl* ctl, const float* __restrict__ u, const
   }
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
-  lz[512 + j + 1] = sqrt(tot[0]);
+  const double nr = sqrt(tot[0]);
+  float* lzw = (float*)(lz + 3072);
+  lz[512 + j + 1] = nr;
+  lzw[512 + j + 1] = nr > 0.0 ? (float)(1.0 / nr) : 0.0f;
+  lzw[1024 + j + 1] = (float)nr;
 }

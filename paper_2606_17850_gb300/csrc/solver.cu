@@ -362,13 +362,14 @@ struct Pieces {
     TH_CHECK_LAUNCH();
     return enq_residual(P, st, 0, 1, false);
   }
-  // fp64 path
+  // fp64 path: PCG on theta itself, restarted from the true FP64 residual
+  th_status fp64_begin(cudaStream_t st) { return enq_residual(P, st, 1, 0, true); }
   th_status fp64_init(cudaStream_t st) {
-    TH_TRY(enq_residual(P, st, 1, 0, true));
     VecSet<double> V = vec64(P.g);
     TH_TRY((enq_update<double, true>(P, V, st, 0, 0, 0)));
     return enq_precond_tail<double>(P, V, st);
   }
+  th_status fp64_close(cudaStream_t st) { return enq_residual(P, st, 1, 1, true); }
   th_status fp64_pair(cudaStream_t st) {
     VecSet<double> V = vec64(P.g);
     TH_TRY(enq_iteration<double>(P, V, st, 0));
@@ -453,15 +454,22 @@ static th_status emit_solve(const Plan& P, GraphCache* gc, int lvl) {
   Ctl* ctl = P.g->ctl;
   cudaStream_t s = gc->cs[lvl];
   if (P.prec == TH_PREC_FP64) {
-    TH_TRY(pcs.fp64_init(s));
-    cudaGraph_t bi;
-    cudaGraphConditionalHandle hi;
-    TH_TRY(begin_while(s, ctl, 0, &bi, &hi));
-    TH_TRY(capture_body(bi, gc->cs[lvl + 1], [&](cudaStream_t sb) -> th_status {
-      TH_TRY(pcs.fp64_pair(sb));
-      return enq_cond(sb, hi, ctl, 0);
-    }));
-    return enq_residual(P, s, 2, 0, true);
+    TH_TRY(pcs.fp64_begin(s));
+    cudaGraph_t bo;
+    cudaGraphConditionalHandle ho;
+    TH_TRY(begin_while(s, ctl, 1, &bo, &ho));
+    return capture_body(bo, gc->cs[lvl + 1], [&](cudaStream_t sb) -> th_status {
+      TH_TRY(pcs.fp64_init(sb));
+      cudaGraph_t bi;
+      cudaGraphConditionalHandle hi;
+      TH_TRY(begin_while(sb, ctl, 0, &bi, &hi));
+      TH_TRY(capture_body(bi, gc->cs[lvl + 2], [&](cudaStream_t sc) -> th_status {
+        TH_TRY(pcs.fp64_pair(sc));
+        return enq_cond(sc, hi, ctl, 0);
+      }));
+      TH_TRY(pcs.fp64_close(sb));
+      return enq_cond(sb, ho, ctl, 1);
+    });
   }
   TH_TRY(enq_residual(P, s, 0, 0, false));
   cudaGraph_t bo;
@@ -485,7 +493,7 @@ static CtlInit ctl_init(const thermal_solve_opts* o, int n_steps, int spm, int n
   CtlInit ci;
   ci.tol_rel = o->tol_rel;
   ci.inner_tol = o->inner_tol;
-  ci.max_outer = o->precision == TH_PREC_FP64 ? 1 : o->max_outer;
+  ci.max_outer = o->max_outer;
   ci.max_inner = o->precision == TH_PREC_FP64 ? o->max_iter : o->max_inner;
   ci.n_steps = n_steps;
   ci.steps_per_map = spm > 0 ? spm : 1;
@@ -562,15 +570,21 @@ static th_status polled_solve(const Plan& P, cudaStream_t s) {
   Pieces pcs(P);
   Ctl h;
   if (P.prec == TH_PREC_FP64) {
-    TH_TRY(pcs.fp64_init(s));
+    TH_TRY(pcs.fp64_begin(s));
     TH_TRY(poll(g, s, &h));
-    int chunk = 4;
-    while (!h.done) {
-      for (int c = 0; c < chunk; ++c) TH_TRY(pcs.fp64_pair(s));
+    while (!h.outer_done) {
+      TH_TRY(pcs.fp64_init(s));
       TH_TRY(poll(g, s, &h));
-      chunk = std::min(chunk * 2, 128);
+      int chunk = 4;
+      while (!h.done) {
+        for (int c = 0; c < chunk; ++c) TH_TRY(pcs.fp64_pair(s));
+        TH_TRY(poll(g, s, &h));
+        chunk = std::min(chunk * 2, 128);
+      }
+      TH_TRY(pcs.fp64_close(s));
+      TH_TRY(poll(g, s, &h));
     }
-    return enq_residual(P, s, 2, 0, true);
+    return TH_OK;
   }
   TH_TRY(enq_residual(P, s, 0, 0, false));
   TH_TRY(poll(g, s, &h));
@@ -649,7 +663,7 @@ static void fill_stats(const Plan& P, const Ctl& h, float ms, thermal_solve_stat
   if (!st) return;
   std::memset(st, 0, sizeof(*st));
   st->status = h.status;
-  st->outer_it = P.prec == TH_PREC_FP64 ? std::max(1, h.steps_done) : h.outer_it;
+  st->outer_it = h.outer_it;
   st->inner_it = h.it_total;
   st->n_spmv = h.n_spmv + h.it_total * (1 + P.pc_spmv) + (long long)h.n_inits * P.pc_spmv;
   st->rel_res = h.rel_res;
@@ -848,6 +862,7 @@ __global__ void k_fill(long long n, T* a, T v) {
 __global__ void k_ctl_timing(Ctl* c) {
   Ctl z = {};
   z.rz = 1.0; z.rz_next = 1.0; z.pAp = 1.0; z.rr0 = 1e30; z.inner_rel = 1e-20;
+  z.alpha_d = 1.0; z.beta_d = 1.0; z.alpha_f = 1.0f; z.beta_f = 1.0f; z.rnorm = 1.0; z.rscale_f = 1.0f;
   z.max_inner = 0x7fffffff; z.max_outer = 0x7fffffff; z.tol_rel = 0.0; z.inner_tol = 1e-20;
   z.steps_per_map = 1; z.n_maps = 1;
   *c = z;
