@@ -280,6 +280,38 @@ th_status thermal_solve_batched(thermal_grid* const* grids, int n, const void* c
                                 int power_dtype, double* const* T, const thermal_solve_opts* opts,
                                 thermal_solve_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------ allocation-free variant */
+
+/*
+ * y = A x and x^T A x in FP32, without allocating any device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * at the time they need the product, e.g. code held to a device-memory budget fixed
+ * at start-up, hosts whose own allocator owns the device and hands out only
+ * pre-sized buffers, or latency-critical paths where an allocation would
+ * synchronise the device.
+ *
+ * gx, gy, gz: the FP32 face conductances of an nx * ny * layers grid in the layout of
+ *   thermal_grid_faces (device, n_cells floats each).
+ * s_layer: host array of `layers` floats, the per-layer diagonal term (h dx dy on the
+ *   top layer plus c dx dy dz / dt in a transient step).
+ * x (device, n_cells floats) in; y (device, n_cells floats) and *xAx (device, one
+ *   double) out.  The stencil row and its FP32 arithmetic are those of thermal_apply.
+ * Scratch: the per-block partial sums and a completion counter live in one static
+ *   device array of 65536 doubles (+256 B), which every GPU that loads the library
+ *   holds until the process exits.  Grids needing more than 65536 thread blocks
+ *   (ceil(nx/32) * ceil(ny/8) * layers) are rejected with TH_EINVAL.
+ * The first call on a device looks up that array's device address
+ *   (cudaGetSymbolAddress) with the device current; make that first call before any
+ *   stream capture.  Every call zeroes the counter on `stream` (cudaMemsetAsync).
+ *   All calls on one device share that device's array, which keeps the last call's
+ *   contents: calls that may overlap on the GPU (e.g. on two streams of the same
+ *   device) race and must be ordered by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called.  Asynchronous.
+ */
+th_status thermal_apply_dot_noalloc(int nx, int ny, int layers, const float* gx, const float* gy,
+                                    const float* gz, const float* s_layer, const float* x, float* y,
+                                    double* xAx, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
