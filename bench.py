@@ -44,6 +44,7 @@ KERNEL_BYTES = {
     "update_f32": 32,    # x, r (read+write 16) + p, mu, 1/diag (12) + z (4)
     "stencil_f32": 20,   # gx gy gz (12) + x (4) + y (4)
     "cheb_bf16": 22,     # gx gy gz bf16 (6) + 16
+    "residual_df": 48,   # gx gy gz hi+lo (24) + theta, theta_n hi+lo (16) + P f32 (4) + r f32 (4)
     "residual_f64": 48,  # gx gy gz (24) + theta, theta_n (16) + P f32 (4) + r f32 (4)
     "stencil_f64": 40,   # gx gy gz (24) + x (8) + y (8)
     "cheb_f64": 64,      # gx gy gz (24) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)
@@ -64,6 +65,12 @@ def parse():
     ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--polled", action="store_true",
                     help="host-polled loop instead of the CUDA graph (same kernels; for per-kernel profiling)")
+    ap.add_argument("--time-steps", type=int, default=N_STEPS,
+                    help="backward-Euler steps per trajectory (100 for the measured workload; "
+                         "fewer only for short profiling captures)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only time each hot kernel on the full-size grid (short ncu target)")
+    ap.add_argument("--reps", type=int, default=40, help="launches per kernel timing")
     ap.add_argument("--cpu-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -247,14 +254,21 @@ def main():
     inst, maps_h = workload_arrays()
     st = inst.stack
     grid = ThermalGrid.from_stack(NX, NY, st)
+    peak, peak_kind = measured_peaks()
+    if args.kernels_only:
+        kern = kernel_table(grid, inst.n, args.reps, peak, peak_kind)
+        print(json.dumps({"kernels": kern, "config": config_dict(args.degree), "reps": args.reps}))
+        return
     maps = [torch.from_numpy(m).cuda() for m in maps_h]
     T = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
     opts = dict(precision="mixed", precond="cheb", cheb_degree=args.degree, tol_rel=1e-8,
                 use_graph=0 if args.polled else 1)
 
+    nsteps = args.time_steps
+
     def trajectory(o, Tt, mp):
         Tt.fill_(st.t_amb)
-        return grid.run_transient(mp, STEPS_PER_MAP, N_STEPS, DT, Tt, **o)[1]
+        return grid.run_transient(mp, STEPS_PER_MAP, nsteps, DT, Tt, **o)[1]
 
     def barrier():
         if world > 1:
@@ -281,20 +295,23 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_total = t.item()
     ms_traj = ms_total / args.steps
-    value = ms_traj / N_STEPS
+    value = ms_traj / nsteps
     T_mixed = T.clone()
 
     result = {"metric": METRIC, "value": value / world if False else value, "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_traj, "higher_is_better": False,
               "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
               "config": config_dict(args.degree, args.polled)}
+    if nsteps != N_STEPS:
+        result["config"]["time_steps_per_bench_step"] = nsteps
+        result["config"]["note"] = "shortened trajectory (profiling run), not the measured workload"
     result["solver"] = {"inner_it_per_traj": stats["inner_it"], "outer_it_per_traj": stats["outer_it"],
                         "n_spmv_per_traj": stats["n_spmv"], "final_rel_res": stats["rel_res"],
                         "status": stats["status"], "first_call_ms (setup+graph build+solve)": t_setup}
     k = args.degree
     # kernel launches per trajectory from the solver's counters (graph mode)
     pairs = (stats["inner_it"] + stats["outer_it"]) // 2 + stats["outer_it"]
-    launches = (3 + N_STEPS * 6 + stats["outer_it"] * (k + 4) + pairs * (2 * (k + 1) + 1) + 1) * args.steps
+    launches = (3 + nsteps * 6 + stats["outer_it"] * (k + 4) + pairs * (2 * (k + 1) + 1) + 1) * args.steps
     result["gpu_launches"] = int(launches)
     result["clocks"] = clk.summary()
 
@@ -311,20 +328,15 @@ def main():
         ms64 = e0.elapsed_time(e1)
         rise = (T64 - st.t_amb).abs().max().item()
         err = (T_mixed - T64).abs().max().item() / rise
-        result["fp64_gpu"] = {"value": ms64 / N_STEPS, "unit": UNIT, "ms_per_trajectory": ms64,
+        result["fp64_gpu"] = {"value": ms64 / nsteps, "unit": UNIT, "ms_per_trajectory": ms64,
                               "inner_it": s64["inner_it"], "final_rel_res": s64["rel_res"]}
-        result["speedup_mixed_vs_fp64"] = (ms64 / N_STEPS) / value
+        result["speedup_mixed_vs_fp64"] = (ms64 / nsteps) / value
         result["accuracy"] = {"max_abs_diff_mixed_vs_fp64_K": err * rise,
                               "max_rel_diff_vs_rise": err}
 
     # live per-kernel timings (CUDA events on the launching stream) -> roofline
-    peak, peak_kind = measured_peaks()
     if not args.no_kernels:
-        kern = {}
-        for name, nbytes in KERNEL_BYTES.items():
-            ms = grid.kernel_time(name, reps=40, dt=DT)
-            gbs = nbytes * inst.n / (ms * 1e-3) / 1e9
-            kern[name] = {"ms": ms, "bytes_per_cell": nbytes, "GB/s": gbs, "frac_of_" + peak_kind: gbs / peak}
+        kern = kernel_table(grid, inst.n, args.reps, peak, peak_kind)
         result["kernels"] = kern
         dom = kern[DOMINANT]
         result["roofline"] = {"bound": "hbm", "kernel": DOMINANT, "achieved": dom["GB/s"], "peak": peak,
@@ -343,7 +355,7 @@ def main():
             trajectory(opts, T_pin, maps_pin)
         barrier()
         ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
-        result["e2e"] = {"value": ms_e2e / N_STEPS, "unit": UNIT,
+        result["e2e"] = {"value": ms_e2e / nsteps, "unit": UNIT,
                          "h2d_bytes_per_step": int(sum(m.numel() * 4 for m in maps_pin) + inst.n * 8),
                          "d2h_bytes_per_step": int(inst.n * 8),
                          "note": "per bench step (one 100-step trajectory): 4 power maps + T_0 to the device, "
@@ -354,6 +366,17 @@ def main():
         print(json.dumps(result))
     if world > 1:
         dist.destroy_process_group()
+
+
+def kernel_table(grid, n, reps, peak, peak_kind):
+    """Mean launch time of each hot kernel (CUDA events around `reps` back-to-back
+    launches on the launching stream) and the HBM bandwidth its algorithmic bytes imply."""
+    kern = {}
+    for name, nbytes in KERNEL_BYTES.items():
+        ms = grid.kernel_time(name, reps=reps, dt=DT)
+        gbs = nbytes * n / (ms * 1e-3) / 1e9
+        kern[name] = {"ms": ms, "bytes_per_cell": nbytes, "GB/s": gbs, "frac_of_" + peak_kind: gbs / peak}
+    return kern
 
 
 def traffic_from_profiles(kernel):

@@ -87,7 +87,9 @@ typedef struct thermal_solve_opts {
   int lanczos_steps;   /* Lanczos steps for the spectral interval (50)                          */
   int use_guess;       /* 1: T holds the initial guess on entry; 0: start from T = T_amb (0)    */
   int use_graph;       /* 1: device-side loop control in a CUDA graph with conditional nodes   */
-  int reserved[8];
+  int batched_mode;    /* thermal_solve_batched: 0 one persistent launch when possible, 1 one */
+                       /* instance after another through the single-grid solver (0)          */
+  int reserved[7];
 } thermal_solve_opts;
 
 typedef struct thermal_solve_stats {
@@ -204,6 +206,7 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  *   5  FP64 refinement residual r = b - A theta with ||r||, ||b||
  *   6  FP64 stencil product
  *   7  FP64 Chebyshev step (plain FP64 path)
+ *   8  double-float refinement residual (the mixed path's r = b - A theta)
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

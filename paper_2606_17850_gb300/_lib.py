@@ -33,7 +33,8 @@ class SolveOpts(C.Structure):
         ("lanczos_steps", C.c_int),
         ("use_guess", C.c_int),
         ("use_graph", C.c_int),
-        ("reserved", C.c_int * 8),
+        ("batched_mode", C.c_int),
+        ("reserved", C.c_int * 7),
     ]
 
 

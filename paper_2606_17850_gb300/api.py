@@ -113,7 +113,7 @@ class ThermalGrid:
         return tuple(x.value for x in v)
 
     KERNELS = {"stencil_f32": 0, "cheb_f32": 1, "cheb_bf16": 2, "spmv_dot_f32": 3, "update_f32": 4,
-               "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7}
+               "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7, "residual_df": 8}
 
     def kernel_time(self, kernel, reps=50, dt=0.0):
         """Average duration (ms) of one launch of a hot kernel on this grid (CUDA events)."""

@@ -35,6 +35,9 @@ struct LayerTab {
   double dz[TH_MAXL];     // thickness per layer
   double S;               // dx * dy
   float s32[TH_MAXL];
+  // double-float (hi + lo) copies for the mixed-path residual
+  float sink_hi[TH_MAXL], sink_lo[TH_MAXL];  // h dx dy on the top layer, else 0
+  float cdt_hi[TH_MAXL], cdt_lo[TH_MAXL];    // c dx dy dz / dt
 };
 
 // Control block of one solve, in device memory.  Fields written by the last
@@ -78,6 +81,7 @@ struct Ctl {
   float alpha_f, beta_f;
   double rnorm;            // ||r|| of the last FP64 residual
   float rscale_f;          // 1/||r||
+  float rnorm_hi, rnorm_lo;  // ||r|| as a double-float
   float pad_f;
 };
 
@@ -87,6 +91,95 @@ template <> __device__ __forceinline__ double ctl_alpha<double>(const Ctl* c) { 
 template <typename T> __device__ __forceinline__ T ctl_beta(const Ctl* c);
 template <> __device__ __forceinline__ float ctl_beta<float>(const Ctl* c) { return __ldcg(&c->beta_f); }
 template <> __device__ __forceinline__ double ctl_beta<double>(const Ctl* c) { return __ldcg(&c->beta_d); }
+
+// last-block decision after the x/r update (or the start of an inner solve):
+// records ||r||^2 and r^T z, decides whether the inner PCG has converged.
+__device__ __forceinline__ void ctl_set_beta(Ctl* c);
+__device__ __forceinline__ void fin_update(Ctl* ctl, double rr, double rz, bool init, int rz_here) {
+  ctl->rr = rr;
+  if (rz_here) {
+    ctl->rz_next = rz;
+    if (!init) ctl_set_beta(ctl);
+  }
+  if (init) {
+    ctl->rr0 = rr;
+    ctl->it = 0;
+    ctl->first = 1;
+    ctl->n_inits += 1;
+    ctl->done = !(rr > 0.0) || (ctl->inner_rel >= 1.0);
+    if (!isfinite(rr)) {
+      ctl->status = 6;
+      ctl->done = 1;
+      ctl->outer_done = 1;
+    }
+    return;
+  }
+  ctl->it += 1;
+  ctl->it_total += 1;
+  const double tgt = ctl->inner_rel * ctl->inner_rel * ctl->rr0;
+  if (!isfinite(rr)) {
+    ctl->status = 6;
+    ctl->done = 1;
+    ctl->outer_done = 1;
+  } else if (rr <= tgt) {
+    ctl->done = 1;
+  } else if (ctl->it >= ctl->max_inner) {
+    ctl->done = 1;
+  }
+}
+
+// last-block decision after p^T A p: alpha for the update, breakdown check.
+__device__ __forceinline__ void fin_pap(Ctl* ctl, double pAp) {
+  ctl->pAp = pAp;
+  ctl->rz = ctl->rz_next;
+  ctl->first = 0;
+  const double al = (pAp > 0.0) ? ctl->rz / pAp : 0.0;
+  ctl->alpha_d = al;
+  ctl->alpha_f = (float)al;
+  if (!(pAp > 0.0)) {
+    ctl->status = isfinite(pAp) ? 5 : 6;
+    ctl->done = 1;
+    ctl->outer_done = 1;
+  }
+}
+
+// last-block decision on the true FP64 residual (outer loop).
+// mode 0: iterative refinement; mode 1: FP64 PCG restart; mode 2: statistics only.
+__device__ __forceinline__ void fin_residual(Ctl* ctl, double rr, double bb, int mode, int count_outer) {
+  ctl->rr64 = rr;
+  ctl->bb = bb;
+  ctl->rnorm = sqrt(rr);
+  ctl->rscale_f = (rr > 0.0) ? (float)(1.0 / sqrt(rr)) : 1.0f;
+  {
+    const float h = (float)ctl->rnorm;
+    ctl->rnorm_hi = h;
+    ctl->rnorm_lo = (float)(ctl->rnorm - (double)h);
+  }
+  ctl->n_spmv += 1;
+  const double rel = (bb > 0.0) ? sqrt(rr / bb) : 0.0;
+  ctl->rel_res = rel;
+  if (mode == 2) return;
+  if (count_outer) {
+    ctl->outer_it += 1;
+    ctl->outer_it_step += 1;
+  }
+  if (!isfinite(rr) || !isfinite(bb)) {
+    ctl->status = 6;
+    ctl->outer_done = 1;
+  } else if (rel <= ctl->tol_rel) {
+    ctl->outer_done = 1;
+  } else if (ctl->outer_it_step >= ctl->max_outer) {
+    ctl->status = 4;
+    ctl->outer_done = 1;
+  } else if (mode == 0) {
+    // reduce the residual as far as this system needs, never less than inner_tol
+    double want = 0.3 * ctl->tol_rel / rel;
+    if (want > 0.5) want = 0.5;
+    ctl->inner_rel = want > ctl->inner_tol ? want : ctl->inner_tol;
+  } else {
+    ctl->inner_rel = 0.5 * ctl->tol_rel / rel;
+  }
+}
 
 // last-block helper: beta for the next search direction once rz_next is known
 __device__ __forceinline__ void ctl_set_beta(Ctl* c) {

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "internal.h"
+#include "dfloat.cuh"
 
 // ------------------------------------------------------------------ errors
 
@@ -96,7 +97,7 @@ __device__ __forceinline__ double series_face(double S, double la, double ka, do
 
 // Per-face conductances (FP64 master, FP32 and BF16 copies).  geo = [k(L), dz(L)].
 __global__ void k_setup_faces(Dims d, const double* __restrict__ geo, double dx, double dy,
-                              Faces64 f64, Faces32 f32, Faces16 f16) {
+                              Faces64 f64, Faces32 f32, Faces32 f32lo, Faces16 f16) {
   const Cell c = cell_of(d);
   if (!c.valid) return;
   const double k = geo[c.z], dz = geo[TH_MAXL + c.z];
@@ -105,6 +106,9 @@ __global__ void k_setup_faces(Dims d, const double* __restrict__ geo, double dx,
   const double gz = (c.z + 1 < d.L) ? series_face(dx * dy, dz, k, geo[TH_MAXL + c.z + 1], geo[c.z + 1]) : 0.0;
   f64.gx[c.i] = gx; f64.gy[c.i] = gy; f64.gz[c.i] = gz;
   f32.gx[c.i] = (float)gx; f32.gy[c.i] = (float)gy; f32.gz[c.i] = (float)gz;
+  f32lo.gx[c.i] = (float)(gx - (double)(float)gx);
+  f32lo.gy[c.i] = (float)(gy - (double)(float)gy);
+  f32lo.gz[c.i] = (float)(gz - (double)(float)gz);
   f16.gx[c.i] = __double2bfloat16(gx); f16.gy[c.i] = __double2bfloat16(gy); f16.gz[c.i] = __double2bfloat16(gz);
 }
 
@@ -210,6 +214,8 @@ thermal_grid::~thermal_grid() {
   if (graphs) graph_cache_free(graphs);
   dfree(f64.gx); dfree(f64.gy); dfree(f64.gz);
   dfree(f32.gx); dfree(f32.gy); dfree(f32.gz);
+  dfree(f32lo.gx); dfree(f32lo.gy); dfree(f32lo.gz);
+  dfree(th_hi); dfree(th_lo); dfree(thn_hi); dfree(thn_lo);
   dfree(f16.gx); dfree(f16.gy); dfree(f16.gz);
   dfree(tab); dfree(invd32); dfree(invd64); dfree(isqd32); dfree(zl_c); dfree(zl_m);
   for (auto& p : theta) dfree(p);
@@ -236,7 +242,8 @@ static th_status compute_faces(thermal_grid* g) {
   TH_TRY(dalloc(&geo, 2 * TH_MAXL));
   cudaError_t e = cudaMemcpy(geo, geo_h, sizeof(geo_h), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    k_setup_faces<<<grid_blocks(g), dim3(TH_BX, TH_BY)>>>(grid_dims(g), geo, g->dx, g->dy, g->f64, g->f32, g->f16);
+    k_setup_faces<<<grid_blocks(g), dim3(TH_BX, TH_BY)>>>(grid_dims(g), geo, g->dx, g->dy, g->f64, g->f32, g->f32lo,
+                                                          g->f16);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
@@ -273,6 +280,8 @@ th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s) {
     g->tab_host.s32[l] = (float)(sink + cdt);
     g->tab_host.k[l] = g->k[l];
     g->tab_host.dz[l] = g->dz[l];
+    df_split(sink, &g->tab_host.sink_hi[l], &g->tab_host.sink_lo[l]);
+    df_split(cdt, &g->tab_host.cdt_hi[l], &g->tab_host.cdt_lo[l]);
   }
   g->tab_host.S = S;
   TH_CUDA(cudaMemcpyAsync(g->tab, &g->tab_host, sizeof(LayerTab), cudaMemcpyHostToDevice, s));
@@ -310,6 +319,10 @@ th_status grid_ensure_workspace(thermal_grid* g, bool need64, cudaStream_t s) {
     TH_TRY(dalloc(&g->mu32, n));
     for (auto& p : g->p32) TH_TRY(dalloc(&p, n));
     for (auto& p : g->zc32) TH_TRY(dalloc(&p, n));
+    TH_TRY(dalloc(&g->th_hi, n));
+    TH_TRY(dalloc(&g->th_lo, n));
+    TH_TRY(dalloc(&g->thn_hi, n));
+    TH_TRY(dalloc(&g->thn_lo, n));
     const dim3 gb = grid_blocks(g);
     g->partials_stride = (int)(gb.x * gb.y * gb.z);
     TH_TRY(dalloc(&g->partials, (size_t)4 * g->partials_stride + 64));
@@ -375,6 +388,9 @@ extern "C" th_status thermal_grid_create(int nx, int ny, int layers, const doubl
   if (s == TH_OK) s = dalloc(&g->f32.gx, n);
   if (s == TH_OK) s = dalloc(&g->f32.gy, n);
   if (s == TH_OK) s = dalloc(&g->f32.gz, n);
+  if (s == TH_OK) s = dalloc(&g->f32lo.gx, n);
+  if (s == TH_OK) s = dalloc(&g->f32lo.gy, n);
+  if (s == TH_OK) s = dalloc(&g->f32lo.gz, n);
   if (s == TH_OK) s = dalloc(&g->f16.gx, n);
   if (s == TH_OK) s = dalloc(&g->f16.gy, n);
   if (s == TH_OK) s = dalloc(&g->f16.gz, n);
@@ -477,10 +493,12 @@ extern "C" th_status thermal_apply(thermal_grid* g, double dt, int precision, co
                                                          (const double*)x, (double*)y);
       break;
     case TH_PREC_MIXED_IR:
+      if (solver_apply_f32(g, false, (const float*)x, (float*)y, s) == TH_OK) return TH_OK;
       k_apply<float, float, float><<<gb, tb, 0, s>>>(d, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
                                                      (const float*)x, (float*)y);
       break;
     case TH_PREC_MIXED_IR_BF16:
+      if (solver_apply_f32(g, true, (const float*)x, (float*)y, s) == TH_OK) return TH_OK;
       k_apply<float, __nv_bfloat16, float><<<gb, tb, 0, s>>>(d, g->f16.gx, g->f16.gy, g->f16.gz, g->tab,
                                                              (const float*)x, (float*)y);
       break;

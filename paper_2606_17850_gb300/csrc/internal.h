@@ -71,6 +71,7 @@ struct thermal_grid {
 
   Faces64 f64;
   Faces32 f32;
+  Faces32 f32lo;  // g - (float)g: low parts for the double-float residual
   Faces16 f16;
 
   // per-dt diagonal data (dt <= 0: steady)
@@ -94,6 +95,8 @@ struct thermal_grid {
   double *r64 = nullptr, *p64[2] = {nullptr, nullptr}, *mu64 = nullptr, *zc64[3] = {nullptr, nullptr, nullptr};
   float *r32 = nullptr, *d32 = nullptr, *p32[2] = {nullptr, nullptr}, *mu32 = nullptr;
   float *zc32[3] = {nullptr, nullptr, nullptr};
+  // mixed path: theta and theta_n as double-float (hi, lo) pairs
+  float *th_hi = nullptr, *th_lo = nullptr, *thn_hi = nullptr, *thn_lo = nullptr;
   double* partials = nullptr;   // reduction partials
   int partials_stride = 0;
   unsigned* counters = nullptr; // reduction counters (zeroed)
@@ -108,6 +111,7 @@ struct thermal_grid {
   int dev_ptrs_n = 0;
 
   GraphCache* graphs = nullptr;
+  int zc_tuned = 0;  // layers per thread in the vectorised kernels (autotuned)
 
   ~thermal_grid();
 };
@@ -131,3 +135,8 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
                        int spm, int n_steps, double* T, const thermal_solve_opts* o, thermal_solve_stats* stats,
                        cudaStream_t s);
 void graph_cache_free(GraphCache* c);
+// Lanczos interval and the Chebyshev three-term coefficients (c1[m], c2[m], m < k).
+th_status solver_cheb_coeffs(thermal_grid* g, double dt, const thermal_solve_opts* o, std::vector<float>& c1,
+                             std::vector<float>& c2, float* inv_theta, double* lmin, double* lmax, cudaStream_t s);
+// FP32 / BF16-coefficient y = A x through the vectorised kernel; TH_EINVAL when nx % 4 != 0.
+th_status solver_apply_f32(thermal_grid* g, bool bf16, const float* x, float* y, cudaStream_t s);

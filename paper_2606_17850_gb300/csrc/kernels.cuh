@@ -10,6 +10,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 // ---------------------------------------------------------------- control
 
@@ -131,36 +132,102 @@ __global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, con
   }
   double tot[2];
   if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
-  // last block, thread 0
-  const double rr = tot[0], bb = tot[1];
-  ctl->rr64 = rr;
-  ctl->bb = bb;
-  ctl->rnorm = sqrt(rr);
-  ctl->rscale_f = (rr > 0.0) ? (float)(1.0 / sqrt(rr)) : 1.0f;
-  ctl->n_spmv += 1;
-  const double rel = (bb > 0.0) ? sqrt(rr / bb) : 0.0;
-  ctl->rel_res = rel;
-  if (mode == 2) return;
-  if (count_outer) {
-    ctl->outer_it += 1;
-    ctl->outer_it_step += 1;
+  fin_residual(ctl, tot[0], tot[1], mode, count_outer);
+}
+
+// ---------------------------------------------------------------- double-float (mixed path)
+
+// mode 0: theta = 0; 1: theta = T - t_amb; 2: theta_n = T - t_amb and theta = theta_n.
+__global__ void k_prepare_df(long long n, const double* __restrict__ T, double t_amb, int mode, float* th_hi,
+                             float* th_lo, float* thn_hi, float* thn_lo) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float h = 0.f, l = 0.f;
+  if (mode >= 1) df_split(T[i] - t_amb, &h, &l);
+  th_hi[i] = h;
+  th_lo[i] = l;
+  if (mode == 2) {
+    thn_hi[i] = h;
+    thn_lo[i] = l;
   }
-  if (!isfinite(rr) || !isfinite(bb)) {
-    ctl->status = 6;
-    ctl->outer_done = 1;
-  } else if (rel <= ctl->tol_rel) {
-    ctl->outer_done = 1;
-  } else if (ctl->outer_it_step >= ctl->max_outer) {
-    ctl->status = 4;
-    ctl->outer_done = 1;
-  } else if (mode == 0) {
-    // reduce the residual as far as this system needs, never less than inner_tol
-    double want = 0.3 * ctl->tol_rel / rel;
-    if (want > 0.5) want = 0.5;
-    ctl->inner_rel = want > ctl->inner_tol ? want : ctl->inner_tol;
-  } else {
-    ctl->inner_rel = 0.5 * ctl->tol_rel / rel;
+}
+
+__global__ void k_finalize_df(long long n, const float* __restrict__ th_hi, const float* __restrict__ th_lo,
+                              double t_amb, double* __restrict__ T) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T[i] = ((double)th_hi[i] + (double)th_lo[i]) + t_amb;
+}
+
+__global__ void k_copy_df(long long n, const float* __restrict__ ah, const float* __restrict__ al,
+                          float* __restrict__ bh, float* __restrict__ bl) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bh[i] = ah[i];
+  bl[i] = al[i];
+}
+
+// theta += ||r|| d in double-float.
+__global__ void k_theta_axpy_df(long long n, const Ctl* ctl, float* __restrict__ th_hi, float* __restrict__ th_lo,
+                                const float* __restrict__ d) {
+  if (ld_int(&ctl->outer_done)) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const df rn = df_make(__ldcg(&ctl->rnorm_hi), __ldcg(&ctl->rnorm_lo));
+  const df t = df_add(df_make(th_hi[i], th_lo[i]), df_mul_f(rn, d[i]));
+  th_hi[i] = t.hi;
+  th_lo[i] = t.lo;
+}
+
+// r = P + cdt (theta_n - theta) - sink theta - sum_faces g (theta_i - theta_j) in
+// double-float (theta, g, cdt and sink as hi + lo pairs); r rounded to FP32 for the
+// inner solve; ||r||^2 and ||b||^2 (b = P + cdt theta_n) reduced as in k_residual.
+template <typename TP>
+__global__ void k_residual_df(Dims d, Ctl* ctl, Faces32 gh, Faces32 gl, const LayerTab* tab,
+                              const float* __restrict__ th_hi, const float* __restrict__ th_lo,
+                              const TP* const* ptab, const float* __restrict__ thn_hi,
+                              const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer,
+                              double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->outer_done)) return;
+  const Cell c = cell_of(d);
+  const TP* P;
+  {
+    const int st = ld_int(&ctl->step), spm = ctl->steps_per_map, nm = ctl->n_maps;
+    P = ptab[(st / spm) % nm];
   }
+  float v[2] = {0.f, 0.f};
+  if (c.valid) {
+    const df ti = df_make(th_hi[c.i], th_lo[c.i]);
+    df flux = df_make(0.f, 0.f);
+    auto face = [&](const float* gH, const float* gL, long long fi, long long j) {
+      const df g = df_make(__ldg(gH + fi), __ldg(gL + fi));
+      const df dlt = df_sub(ti, df_make(th_hi[j], th_lo[j]));
+      flux = df_add(flux, df_mul(g, dlt));
+    };
+    if (c.x + 1 < d.nx) face(gh.gx, gl.gx, c.i, c.i + 1);
+    if (c.x > 0) face(gh.gx, gl.gx, c.i - 1, c.i - 1);
+    if (c.y + 1 < d.ny) face(gh.gy, gl.gy, c.i, c.i + d.nx);
+    if (c.y > 0) face(gh.gy, gl.gy, c.i - d.nx, c.i - d.nx);
+    if (c.z + 1 < d.L) face(gh.gz, gl.gz, c.i, c.i + d.pxy);
+    if (c.z > 0) face(gh.gz, gl.gz, c.i - d.pxy, c.i - d.pxy);
+    const df sink = df_make(__ldg(&tab->sink_hi[c.z]), __ldg(&tab->sink_lo[c.z]));
+    df b = df_make((float)P[c.i], 0.f);
+    if (sizeof(TP) == 8) b.lo = (float)((double)P[c.i] - (double)b.hi);
+    df rr = df_sub(df_sub(b, df_mul(sink, ti)), flux);
+    if (thn_hi) {
+      const df cdt = df_make(__ldg(&tab->cdt_hi[c.z]), __ldg(&tab->cdt_lo[c.z]));
+      const df tn = df_make(thn_hi[c.i], thn_lo[c.i]);
+      rr = df_add(rr, df_mul(cdt, df_sub(tn, ti)));
+      b = df_add(b, df_mul(cdt, tn));
+    }
+    const float rf = rr.hi + rr.lo;
+    r[c.i] = rf;
+    v[0] = rf * rf;
+    v[1] = b.hi * b.hi;
+  }
+  double tot[2];
+  if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
+  fin_residual(ctl, tot[0], tot[1], 0, count_outer);
 }
 
 // ---------------------------------------------------------------- PCG kernels
@@ -190,18 +257,7 @@ __global__ void k_spmv_dot(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC
   }
   double tot[1];
   if (!grid_reduce<TV, 1>(v, partials, stride, counter, tot)) return;
-  const double pAp = tot[0];
-  ctl->pAp = pAp;
-  ctl->rz = ctl->rz_next;
-  ctl->first = 0;
-  const double al = (pAp > 0.0) ? ctl->rz / pAp : 0.0;
-  ctl->alpha_d = al;
-  ctl->alpha_f = (float)al;
-  if (!(pAp > 0.0)) {
-    ctl->status = isfinite(pAp) ? 5 : 6;
-    ctl->done = 1;
-    ctl->outer_done = 1;
-  }
+  fin_pap(ctl, tot[0]);
 }
 
 // ZMODE: 0 no preconditioner (z = r), 1 Jacobi (z = r / A_ii), 2 first Chebyshev
@@ -242,37 +298,7 @@ __global__ void k_update(Dims d, Ctl* ctl, TV* __restrict__ x, const TV* __restr
   }
   double tot[2];
   if (!grid_reduce<TV, 2>(v, partials, stride, counter, tot)) return;
-  const double rr = tot[0];
-  ctl->rr = rr;
-  if (rz_here) {
-    ctl->rz_next = tot[1];
-    if (!INIT) ctl_set_beta(ctl);
-  }
-  if (INIT) {
-    ctl->rr0 = rr;
-    ctl->it = 0;
-    ctl->first = 1;
-    ctl->n_inits += 1;
-    ctl->done = !(rr > 0.0) || (ctl->inner_rel >= 1.0);
-    if (!isfinite(rr)) {
-      ctl->status = 6;
-      ctl->done = 1;
-      ctl->outer_done = 1;
-    }
-    return;
-  }
-  ctl->it += 1;
-  ctl->it_total += 1;
-  const double tgt = ctl->inner_rel * ctl->inner_rel * ctl->rr0;
-  if (!isfinite(rr)) {
-    ctl->status = 6;
-    ctl->done = 1;
-    ctl->outer_done = 1;
-  } else if (rr <= tgt) {
-    ctl->done = 1;
-  } else if (ctl->it >= ctl->max_inner) {
-    ctl->done = 1;
-  }
+  fin_update(ctl, tot[0], tot[1], INIT, rz_here);
 }
 
 // One step of the Chebyshev recurrence in three-term form.  With z_0 = 0,

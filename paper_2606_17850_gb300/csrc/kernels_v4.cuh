@@ -1,0 +1,233 @@
+// Vectorised FP32 stencil kernels (used when nx % 4 == 0).
+//
+// Each thread owns 4 consecutive cells of one x-row (one 16-byte load per array)
+// and walks a chunk of layers upwards: the z-1 / z+1 values and the face below
+// stay in registers, so a cell costs one float4 load of the vector, its x/y
+// neighbours come from the float4 itself, two scalar loads and the rows above /
+// below (L1), and the face arrays are read once.  Faces outside the grid are
+// stored as zeros, so boundary terms vanish without per-term branches (a missing
+// neighbour's value is read as 0 and multiplied by a zero conductance).
+//
+// Launch: block (TH_BX, TH_BY4), grid (ceil(nx/(4*TH_BX)), ceil(ny/TH_BY4),
+// ceil(L/zc)); requires nx % 4 == 0 and 16-byte aligned base pointers.
+#pragma once
+
+#include "common.cuh"
+
+#define TH_BY4 8
+
+__device__ __forceinline__ float4 z4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, const float4& v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 ldc4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 ldc4(const __nv_bfloat16* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float cmp(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+struct Walk4 {
+  int x0, y, zs, ze;
+  long long b0;  // index of (x0, y, 0)
+  bool valid;
+};
+
+__device__ __forceinline__ Walk4 walk4_of(const Dims& d, int zc) {
+  Walk4 w;
+  w.x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  w.y = blockIdx.y * blockDim.y + threadIdx.y;
+  w.zs = blockIdx.z * zc;
+  w.ze = min(w.zs + zc, d.L);
+  w.valid = (w.x0 < d.nx) && (w.y < d.ny);
+  w.b0 = (long long)w.x0 + (long long)d.nx * w.y;
+  return w;
+}
+
+// Walks the layers of one 4-cell row segment.  V4(i) returns the operand at cells
+// i..i+3 (float4), V1(j) at one cell.  For each layer z calls
+// epi(i, z, v, acc, dg): v = operand, acc = (A v) and dg = A_ii for the 4 cells,
+// accumulated in the order of stencil_row (s v, +x, -x, +y, -y, +z, -z).
+template <typename TC, typename F4, typename F1, typename E>
+__device__ __forceinline__ void zwalk4(const Dims& d, const Walk4& w, const TC* __restrict__ gx,
+                                       const TC* __restrict__ gy, const TC* __restrict__ gz, const LayerTab* tab,
+                                       F4 V4, F1 V1, E epi) {
+  const long long pxy = d.pxy;
+  const bool hasL = w.x0 > 0, hasR = w.x0 + 4 < d.nx, hasD = w.y > 0, hasU = w.y + 1 < d.ny;
+  float4 vb = z4(), gzb = z4();
+  if (w.zs > 0) {
+    vb = V4(w.b0 + (long long)(w.zs - 1) * pxy);
+    gzb = ldc4(gz + w.b0 + (long long)(w.zs - 1) * pxy);
+  }
+  float4 vc = V4(w.b0 + (long long)w.zs * pxy);
+  for (int z = w.zs; z < w.ze; ++z) {
+    const long long i = w.b0 + (long long)z * pxy;
+    const bool hasA = z + 1 < d.L;
+    const float4 va = hasA ? V4(i + pxy) : z4();
+    const float4 gzv = hasA ? ldc4(gz + i) : z4();
+    const float4 gxv = ldc4(gx + i);
+    const float4 gyv = ldc4(gy + i);
+    const float4 gyd = hasD ? ldc4(gy + i - d.nx) : z4();
+    const float gxl = hasL ? ldc(gx + i - 1) : 0.f;
+    const float vl = hasL ? V1(i - 1) : 0.f;
+    const float vr = hasR ? V1(i + 4) : 0.f;
+    const float4 vu = hasU ? V4(i + d.nx) : z4();
+    const float4 vd = hasD ? V4(i - d.nx) : z4();
+    const float s = __ldg(&tab->s32[z]);
+    float acc[4], dg[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float v = cmp(vc, k);
+      const float right = (k == 3) ? vr : cmp(vc, k + 1);
+      const float left = (k == 0) ? vl : cmp(vc, k - 1);
+      const float gr = cmp(gxv, k);
+      const float gl = (k == 0) ? gxl : cmp(gxv, k - 1);
+      float a = s * v, g = s;
+      a += gr * (v - right);        g += gr;
+      a += gl * (v - left);         g += gl;
+      a += cmp(gyv, k) * (v - cmp(vu, k));  g += cmp(gyv, k);
+      a += cmp(gyd, k) * (v - cmp(vd, k));  g += cmp(gyd, k);
+      a += cmp(gzv, k) * (v - cmp(va, k));  g += cmp(gzv, k);
+      a += cmp(gzb, k) * (v - cmp(vb, k));  g += cmp(gzb, k);
+      acc[k] = a;
+      dg[k] = g;
+    }
+    epi(i, z, vc, acc, dg);
+    vb = vc;
+    vc = va;
+    gzb = gzv;
+  }
+}
+
+// One Chebyshev step (see k_cheb), vectorised.
+template <typename TC, bool SCALED, bool LAST>
+__global__ void __launch_bounds__(TH_BX* TH_BY4)
+    k_cheb_v4(Dims d, int zc, Ctl* ctl, const TC* __restrict__ gx, const TC* __restrict__ gy,
+              const TC* __restrict__ gz, const LayerTab* tab, const float* __restrict__ r,
+              const float* __restrict__ zprev, const float* __restrict__ zcur, float* __restrict__ znext, float c1,
+              float c2, double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const Walk4 w = walk4_of(d, zc);
+  float part[1] = {0.f};
+  if (w.valid) {
+    zwalk4<TC>(d, w, gx, gy, gz, tab, [&](long long i) { return ld4(zcur + i); },
+               [&](long long j) { return zcur[j]; },
+               [&](long long i, int, const float4& v, const float (&acc)[4], const float (&dg)[4]) {
+                 const float4 rv = ld4(r + i);
+                 const float4 zp = zprev ? ld4(zprev + i) : z4();
+                 float o[4];
+#pragma unroll
+                 for (int k = 0; k < 4; ++k) {
+                   const float vk = cmp(v, k);
+                   float res = cmp(rv, k) - acc[k];
+                   if (SCALED) res = res / dg[k];
+                   o[k] = vk + c1 * (vk - cmp(zp, k)) + c2 * res;
+                   if (LAST) part[0] += cmp(rv, k) * o[k];
+                 }
+                 st4(znext + i, make_float4(o[0], o[1], o[2], o[3]));
+               });
+  }
+  if (!LAST) return;
+  double tot[1];
+  if (!grid_reduce<float, 1>(part, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
+}
+
+// Search direction + stencil + p^T A p (see k_spmv_dot), vectorised.
+__global__ void __launch_bounds__(TH_BX* TH_BY4)
+    k_spmv_dot_v4(Dims d, int zc, Ctl* ctl, const float* __restrict__ gx, const float* __restrict__ gy,
+                  const float* __restrict__ gz, const LayerTab* tab, const float* __restrict__ z,
+                  const float* __restrict__ p_old, float* __restrict__ p_new, float* __restrict__ mu,
+                  double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const Walk4 w = walk4_of(d, zc);
+  const int first = ld_int(&ctl->first);
+  const float beta = first ? 0.f : ctl_beta<float>(ctl);
+  float part[1] = {0.f};
+  if (w.valid) {
+    auto P4 = [&](long long i) -> float4 {
+      const float4 a = ld4(z + i);
+      if (first) return a;
+      const float4 b = ld4(p_old + i);
+      return make_float4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z, a.w + beta * b.w);
+    };
+    auto P1 = [&](long long j) -> float { return first ? z[j] : z[j] + beta * p_old[j]; };
+    zwalk4<float>(d, w, gx, gy, gz, tab, P4, P1,
+                  [&](long long i, int, const float4& v, const float (&acc)[4], const float (&)[4]) {
+                    st4(p_new + i, v);
+                    st4(mu + i, make_float4(acc[0], acc[1], acc[2], acc[3]));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) part[0] += cmp(v, k) * acc[k];
+                  });
+  }
+  double tot[1];
+  if (!grid_reduce<float, 1>(part, partials, stride, counter, tot)) return;
+  fin_pap(ctl, tot[0]);
+}
+
+// y = A x, vectorised (FP32).
+template <typename TC>
+__global__ void __launch_bounds__(TH_BX* TH_BY4)
+    k_apply_v4(Dims d, int zc, const TC* __restrict__ gx, const TC* __restrict__ gy, const TC* __restrict__ gz,
+               const LayerTab* tab, const float* __restrict__ x, float* __restrict__ y) {
+  const Walk4 w = walk4_of(d, zc);
+  if (!w.valid) return;
+  zwalk4<TC>(d, w, gx, gy, gz, tab, [&](long long i) { return ld4(x + i); }, [&](long long j) { return x[j]; },
+             [&](long long i, int, const float4&, const float (&acc)[4], const float (&)[4]) {
+               st4(y + i, make_float4(acc[0], acc[1], acc[2], acc[3]));
+             });
+}
+
+// Vectorised k_update (element-wise; one thread per 4 consecutive cells).
+template <bool INIT, int ZMODE>
+__global__ void __launch_bounds__(256)
+    k_update_v4(long long n4, Ctl* ctl, float* __restrict__ x, const float* __restrict__ p, float* __restrict__ r,
+                const float* __restrict__ mu, const float* __restrict__ invd, float* __restrict__ z, float zscale,
+                int scaled, int rz_here, int scale_r, double* partials, int stride, unsigned* counter) {
+  if (!INIT && ld_int(&ctl->done)) return;
+  if (INIT && ld_int(&ctl->outer_done)) return;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float alpha = INIT ? 0.f : ctl_alpha<float>(ctl);
+  const float rs = (INIT && scale_r) ? __ldcg(&ctl->rscale_f) : 1.f;
+  float v[2] = {0.f, 0.f};
+  if (q < n4) {
+    const long long i = 4 * q;
+    float4 rv = ld4(r + i);
+    float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+    if (INIT) {
+      if (x) st4(x + i, z4());
+      if (scale_r) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rr[k] *= rs;
+        st4(r + i, make_float4(rr[0], rr[1], rr[2], rr[3]));
+      }
+    } else {
+      const float4 xv = ld4(x + i), pv = ld4(p + i), mv = ld4(mu + i);
+      st4(x + i, make_float4(xv.x + alpha * pv.x, xv.y + alpha * pv.y, xv.z + alpha * pv.z, xv.w + alpha * pv.w));
+      rr[0] -= alpha * mv.x; rr[1] -= alpha * mv.y; rr[2] -= alpha * mv.z; rr[3] -= alpha * mv.w;
+      st4(r + i, make_float4(rr[0], rr[1], rr[2], rr[3]));
+    }
+    float zz[4] = {rr[0], rr[1], rr[2], rr[3]};
+    if (ZMODE == 1 || (ZMODE == 2 && scaled)) {
+      const float4 iv = __ldg(reinterpret_cast<const float4*>(invd + i));
+      zz[0] *= iv.x; zz[1] *= iv.y; zz[2] *= iv.z; zz[3] *= iv.w;
+    }
+    if (ZMODE == 2) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) zz[k] *= zscale;
+    }
+    if (ZMODE == 1 || ZMODE == 2) st4(z + i, make_float4(zz[0], zz[1], zz[2], zz[3]));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[0] += rr[k] * rr[k];
+      v[1] += rr[k] * zz[k];
+    }
+  }
+  double tot[2];
+  if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
+  fin_update(ctl, tot[0], tot[1], INIT, rz_here);
+}

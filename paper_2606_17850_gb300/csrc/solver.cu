@@ -12,6 +12,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "kernels_v4.cuh"
 
 // ------------------------------------------------------------------ plan
 
@@ -27,6 +28,11 @@ struct Plan {
   std::vector<double> c1, c2;
   double inv_theta = 1.0, lmin = 0.0, lmax = 0.0;
   int pc_spmv = 0;          // stencil applications per preconditioner application
+  // vectorised FP32 kernels (nx % 4 == 0): grid of the z-walk kernels and the update
+  bool v4 = false;
+  int zc = 1;
+  dim3 gb4, tb4;
+  unsigned nbu4 = 1;
 };
 
 static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
@@ -147,6 +153,118 @@ th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* 
   return TH_OK;
 }
 
+// ------------------------------------------------------------------ z-chunk autotuner
+
+static dim3 v4_blocks(const thermal_grid* g, int zc) {
+  return dim3((g->nx + 4 * TH_BX - 1) / (4 * TH_BX), (g->ny + TH_BY4 - 1) / TH_BY4, (g->L + zc - 1) / zc);
+}
+
+template <typename T>
+__global__ void k_fill(long long n, T* a, T v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+__global__ void k_ctl_timing(Ctl* c) {
+  Ctl z = {};
+  z.rz = 1.0; z.rz_next = 1.0; z.pAp = 1.0; z.rr0 = 1e30; z.inner_rel = 1e-20;
+  z.alpha_d = 1.0; z.beta_d = 1.0; z.alpha_f = 1.0f; z.beta_f = 1.0f; z.rnorm = 1.0; z.rscale_f = 1.0f;
+  z.max_inner = 0x7fffffff; z.max_outer = 0x7fffffff; z.tol_rel = 0.0; z.inner_tol = 1e-20;
+  z.steps_per_map = 1; z.n_maps = 1;
+  *c = z;
+}
+
+// Picks how many layers one thread walks in the vectorised kernels: the whole
+// column keeps z-neighbours in registers, shorter chunks give more threads on
+// small grids.  Times a Chebyshev step for each candidate (CUDA events) once per grid.
+static th_status tune_zchunk(thermal_grid* g, cudaStream_t s) {
+  if (g->zc_tuned > 0) return TH_OK;
+  const long long n = g->n;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  for (float* a : {g->r32, g->zc32[0], g->zc32[1], g->zc32[2]}) k_fill<float><<<nb, 256, 0, s>>>(n, a, 1.0f);
+  k_ctl_timing<<<1, 1, 0, s>>>(g->ctl);
+  TH_CHECK_LAUNCH();
+  int cands[4] = {g->L, (g->L + 1) / 2, (g->L + 3) / 4, 1};
+  cudaEvent_t e0, e1;
+  TH_CUDA(cudaEventCreate(&e0));
+  TH_CUDA(cudaEventCreate(&e1));
+  struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
+  const Dims d = grid_dims(g);
+  float best = 1e30f;
+  int best_zc = g->L;
+  for (int ci = 0; ci < 4; ++ci) {
+    const int zc = cands[ci];
+    if (ci > 0 && zc == cands[ci - 1]) continue;
+    const dim3 gb = v4_blocks(g, zc);
+    auto run = [&]() {
+      k_cheb_v4<float, true, false><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(
+          d, zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->r32, g->zc32[0], g->zc32[1], g->zc32[2],
+          0.5f, 0.5f, g->partials, g->partials_stride, g->counters);
+    };
+    run();
+    TH_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; ++r) run();
+    TH_CUDA(cudaEventRecord(e1, s));
+    TH_CUDA(cudaEventSynchronize(e1));
+    TH_CHECK_LAUNCH();
+    float ms = 0.f;
+    TH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_zc = zc;
+    }
+  }
+  g->zc_tuned = best_zc;
+  return TH_OK;
+}
+
+th_status solver_apply_f32(thermal_grid* g, bool bf16, const float* x, float* y, cudaStream_t s) {
+  // the vectorised kernel needs nx % 4 == 0 and 16-byte aligned vectors
+  if (g->nx % 4 != 0 || ((uintptr_t)x & 15u) || ((uintptr_t)y & 15u)) return TH_EINVAL;
+  TH_TRY(grid_ensure_workspace(g, false, s));
+  TH_TRY(tune_zchunk(g, s));
+  const dim3 gb = v4_blocks(g, g->zc_tuned);
+  if (bf16)
+    k_apply_v4<__nv_bfloat16><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(grid_dims(g), g->zc_tuned, g->f16.gx, g->f16.gy,
+                                                                 g->f16.gz, g->tab, x, y);
+  else
+    k_apply_v4<float><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(grid_dims(g), g->zc_tuned, g->f32.gx, g->f32.gy, g->f32.gz,
+                                                         g->tab, x, y);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+// Chebyshev coefficients of the three-term form: z_1 = inv_theta * M r and, for
+// m = 1..k-1, c1[m] = rho_m rho_{m-1}, c2[m] = 2 rho_m / delta (rho_0 = delta/theta,
+// rho_{m} = 1/(2 sigma_1 - rho_{m-1}), sigma_1 = theta/delta).
+static void cheb_coeffs(double lmin, double lmax, int k, std::vector<double>& c1, std::vector<double>& c2,
+                        double* inv_theta) {
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma1 = theta / delta;
+  double rho_prev = 1.0 / sigma1;
+  *inv_theta = 1.0 / theta;
+  c1.assign(k, 0.0);
+  c2.assign(k, 0.0);
+  for (int m = 1; m < k; ++m) {
+    const double rho = 1.0 / (2.0 * sigma1 - rho_prev);
+    c1[m] = rho * rho_prev;
+    c2[m] = 2.0 * rho / delta;
+    rho_prev = rho;
+  }
+}
+
+th_status solver_cheb_coeffs(thermal_grid* g, double dt, const thermal_solve_opts* o, std::vector<float>& c1,
+                             std::vector<float>& c2, float* inv_theta, double* lmin, double* lmax, cudaStream_t s) {
+  double ra, rb, it;
+  TH_TRY(solver_spectral(g, dt, o, &ra, &rb, lmin, lmax, s));
+  std::vector<double> a, b;
+  cheb_coeffs(*lmin, *lmax, o->cheb_degree, a, b, &it);
+  c1.assign(a.begin(), a.end());
+  c2.assign(b.begin(), b.end());
+  *inv_theta = (float)it;
+  return TH_OK;
+}
+
 // ------------------------------------------------------------------ plan setup
 
 static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts* o, int pdtype, bool transient,
@@ -166,22 +284,19 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
   TH_TRY(grid_ensure_tab(g, dt, s));
   TH_TRY(grid_ensure_workspace(g, P.prec == TH_PREC_FP64, s));
   if (P.pc == TH_PC_ZLINE) TH_TRY(grid_ensure_zline(g, dt, s));
+  P.v4 = (g->nx % 4 == 0);
+  if (P.v4) {
+    TH_TRY(tune_zchunk(g, s));
+    P.zc = g->zc_tuned;
+    P.tb4 = dim3(TH_BX, TH_BY4);
+    P.gb4 = v4_blocks(g, P.zc);
+    P.nbu4 = (unsigned)((g->n / 4 + 255) / 256);
+  }
   P.pc_spmv = 0;
   if (P.pc == TH_PC_CHEB) {
     double ra, rb;
     TH_TRY(solver_spectral(g, dt, o, &ra, &rb, &P.lmin, &P.lmax, s));
-    const double theta = 0.5 * (P.lmax + P.lmin), delta = 0.5 * (P.lmax - P.lmin);
-    const double sigma1 = theta / delta;
-    double rho_prev = 1.0 / sigma1;  // rho_0
-    P.inv_theta = 1.0 / theta;
-    P.c1.assign(P.k, 0.0);
-    P.c2.assign(P.k, 0.0);
-    for (int m = 1; m < P.k; ++m) {
-      const double rho = 1.0 / (2.0 * sigma1 - rho_prev);
-      P.c1[m] = rho * rho_prev;
-      P.c2[m] = 2.0 * rho / delta;
-      rho_prev = rho;
-    }
+    cheb_coeffs(P.lmin, P.lmax, P.k, P.c1, P.c2, &P.inv_theta);
     P.pc_spmv = P.k - 1;
   }
   return TH_OK;
@@ -237,6 +352,22 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
   // an INIT without zeroing x must not touch x: pass it through a harmless path
   // (x is only written when INIT && zero_x, or in a regular update).
   TV* xw = (INIT && !zero_x) ? nullptr : x;
+  if constexpr (sizeof(TV) == 4) {
+    if (P.v4) {
+#define TH_UPD4(ZM)                                                                                          \
+  k_update_v4<INIT, ZM><<<P.nbu4, 256, 0, st>>>(P.d.n / 4, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], zs, P.scaled, \
+                                                rz1, scale_r, g->partials, g->partials_stride, g->counters)
+      switch (P.pc) {
+        case TH_PC_NONE: TH_UPD4(0); break;
+        case TH_PC_JACOBI: TH_UPD4(1); break;
+        case TH_PC_CHEB: TH_UPD4(2); break;
+        default: TH_UPD4(3); break;
+      }
+#undef TH_UPD4
+      TH_CHECK_LAUNCH();
+      return TH_OK;
+    }
+  }
 #define TH_UPD(ZM)                                                                                          \
   k_update<TV, INIT, ZM><<<P.gb, P.tb, 0, st>>>(P.d, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], zs, P.scaled, \
                                                 rz1, scale_r, g->partials, g->partials_stride, g->counters)
@@ -261,6 +392,21 @@ static th_status enq_cheb_tail(const Plan& P, const VecSet<TV>& V, const TC* gx,
     TV* znext = V.zc[m % 3];
     const bool last = (m == P.k - 1);
     const TV c1 = (TV)P.c1[m], c2 = (TV)P.c2[m];
+    if constexpr (sizeof(TV) == 4) {
+      if (P.v4) {
+#define TH_CHEB4(SC, LA)                                                                                       \
+  k_cheb_v4<TC, SC, LA><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, gx, gy, gz, g->tab, V.r, zprev, zcur, znext, \
+                                                 c1, c2, g->partials, g->partials_stride, g->counters)
+        if (P.scaled) {
+          if (last) TH_CHEB4(true, true); else TH_CHEB4(true, false);
+        } else {
+          if (last) TH_CHEB4(false, true); else TH_CHEB4(false, false);
+        }
+#undef TH_CHEB4
+        TH_CHECK_LAUNCH();
+        continue;
+      }
+    }
 #define TH_CHEB(SC, LA)                                                                                      \
   k_cheb<TV, TC, SC, LA><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, gx, gy, gz, g->tab, V.r, zprev, zcur, znext, \
                                                 V.invd, c1, c2, g->partials, g->partials_stride, g->counters)
@@ -305,6 +451,10 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
     k_spmv_dot<double, double><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, zf,
                                                       V.p[parity], V.p[1 - parity], V.mu, g->partials,
                                                       g->partials_stride, g->counters);
+  } else if (P.v4) {
+    k_spmv_dot_v4<<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, zf,
+                                           V.p[parity], V.p[1 - parity], V.mu, g->partials, g->partials_stride,
+                                           g->counters);
   } else {
     k_spmv_dot<float, float><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, zf,
                                                     V.p[parity], V.p[1 - parity], V.mu, g->partials,
@@ -319,6 +469,20 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
 
 static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int count_outer, bool out64) {
   thermal_grid* g = P.g;
+  if (!out64 && mode == 0) {  // mixed path: double-float residual
+    const float* nh = P.transient ? g->thn_hi : nullptr;
+    const float* nl = P.transient ? g->thn_lo : nullptr;
+    if (P.pdtype == TH_F32)
+      k_residual_df<float><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
+                                                  (const float* const*)g->dev_ptrs, nh, nl, g->r32, count_outer,
+                                                  g->partials, g->partials_stride, g->counters);
+    else
+      k_residual_df<double><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
+                                                   (const double* const*)g->dev_ptrs, nh, nl, g->r32, count_outer,
+                                                   g->partials, g->partials_stride, g->counters);
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  }
   const double* th = g->theta[0];
   const double* thn = P.transient ? g->theta_n : nullptr;
 #define TH_RES(TP, TR, RP)                                                                                     \
@@ -358,7 +522,7 @@ struct Pieces {
     return enq_iteration<float>(P, V, st, 1);
   }
   th_status outer_close(cudaStream_t st) {  // theta += ||r|| d ; r = b - A theta
-    k_theta_axpy<<<nb1(P.d.n), 256, 0, st>>>(P.d.n, P.g->ctl, P.g->theta[0], P.g->d32);
+    k_theta_axpy_df<<<nb1(P.d.n), 256, 0, st>>>(P.d.n, P.g->ctl, P.g->th_hi, P.g->th_lo, P.g->d32);
     TH_CHECK_LAUNCH();
     return enq_residual(P, st, 0, 1, false);
   }
@@ -376,6 +540,39 @@ struct Pieces {
     return enq_iteration<double>(P, V, st, 1);
   }
 };
+
+// theta set-up, theta_n <- theta and T output in the representation of the path
+// (FP64 for the plain FP64 path, double-float for the mixed path)
+static th_status enq_prepare(const Plan& P, cudaStream_t st, const double* T, double toff, int mode) {
+  thermal_grid* g = P.g;
+  const long long n = P.d.n;
+  if (P.prec == TH_PREC_FP64)
+    k_prepare<<<nb1(n), 256, 0, st>>>(n, T, toff, mode, g->theta[0], g->theta_n);
+  else
+    k_prepare_df<<<nb1(n), 256, 0, st>>>(n, T, toff, mode, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+static th_status enq_finalize(const Plan& P, cudaStream_t st, double toff, double* T) {
+  thermal_grid* g = P.g;
+  const long long n = P.d.n;
+  if (P.prec == TH_PREC_FP64)
+    k_finalize<<<nb1(n), 256, 0, st>>>(n, g->theta[0], toff, T);
+  else
+    k_finalize_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, toff, T);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
+  thermal_grid* g = P.g;
+  const long long n = P.d.n;
+  if (P.prec == TH_PREC_FP64)
+    k_copy64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n);
+  else
+    k_copy_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
 
 // ------------------------------------------------------------------ graph building
 
@@ -517,15 +714,13 @@ static th_status build_graph(const Plan& P, int kind, const CtlInit& ci, GraphEn
     k_ctl_reset<<<1, 1, 0, s0>>>(ctl, ci);
     TH_CHECK_LAUNCH();
     const int prep = (kind == KIND_STEP) ? 2 : 1;
-    k_prepare<<<nb1(n), 256, 0, s0>>>(n, g->stage_T, toff, prep, g->theta[0], g->theta_n);
-    TH_CHECK_LAUNCH();
+    TH_TRY(enq_prepare(P, s0, g->stage_T, toff, prep));
     if (kind == KIND_RUN) {
       cudaGraph_t bs;
       cudaGraphConditionalHandle hs;
       TH_TRY(begin_while(s0, ctl, 2, &bs, &hs));
       TH_TRY(capture_body(bs, gc->cs[1], [&](cudaStream_t sb) -> th_status {
-        k_copy64<<<nb1(n), 256, 0, sb>>>(n, g->theta[0], g->theta_n);
-        TH_CHECK_LAUNCH();
+        TH_TRY(enq_step_copy(P, sb));
         k_step_begin<<<1, 1, 0, sb>>>(ctl);
         TH_CHECK_LAUNCH();
         TH_TRY(emit_solve(P, gc, 1));
@@ -536,9 +731,7 @@ static th_status build_graph(const Plan& P, int kind, const CtlInit& ci, GraphEn
     } else {
       TH_TRY(emit_solve(P, gc, 0));
     }
-    k_finalize<<<nb1(n), 256, 0, s0>>>(n, g->theta[0], toff, g->stage_T);
-    TH_CHECK_LAUNCH();
-    return TH_OK;
+    return enq_finalize(P, s0, toff, g->stage_T);
   });
   if (st != TH_OK) {
     cudaGraphDestroy(G);
@@ -726,13 +919,11 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
     k_ctl_reset<<<1, 1, 0, s>>>(g->ctl, ci);
     TH_CHECK_LAUNCH();
     const int prep = (kind == KIND_STEP) ? 2 : 1;
-    k_prepare<<<nb1(n), 256, 0, s>>>(n, g->stage_T, toff, prep, g->theta[0], g->theta_n);
-    TH_CHECK_LAUNCH();
+    TH_TRY(enq_prepare(P, s, g->stage_T, toff, prep));
     if (kind == KIND_RUN) {
       Ctl h;
       for (int step = 0; step < n_steps; ++step) {
-        k_copy64<<<nb1(n), 256, 0, s>>>(n, g->theta[0], g->theta_n);
-        TH_CHECK_LAUNCH();
+        TH_TRY(enq_step_copy(P, s));
         k_step_begin<<<1, 1, 0, s>>>(g->ctl);
         TH_CHECK_LAUNCH();
         TH_TRY(polled_solve(P, s));
@@ -748,8 +939,7 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
         TH_CHECK_LAUNCH();
       }
     }
-    k_finalize<<<nb1(n), 256, 0, s>>>(n, g->theta[0], toff, g->stage_T);
-    TH_CHECK_LAUNCH();
+    TH_TRY(enq_finalize(P, s, toff, g->stage_T));
   }
   TH_CUDA(cudaEventRecord(e1, s));
   TH_CUDA(cudaMemcpyAsync(T, g->stage_T, tb, t_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -853,25 +1043,10 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 
 // ------------------------------------------------------------------ kernel timing
 
-template <typename T>
-__global__ void k_fill(long long n, T* a, T v) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] = v;
-}
-
-__global__ void k_ctl_timing(Ctl* c) {
-  Ctl z = {};
-  z.rz = 1.0; z.rz_next = 1.0; z.pAp = 1.0; z.rr0 = 1e30; z.inner_rel = 1e-20;
-  z.alpha_d = 1.0; z.beta_d = 1.0; z.alpha_f = 1.0f; z.beta_f = 1.0f; z.rnorm = 1.0; z.rscale_f = 1.0f;
-  z.max_inner = 0x7fffffff; z.max_outer = 0x7fffffff; z.tol_rel = 0.0; z.inner_tol = 1e-20;
-  z.steps_per_map = 1; z.n_maps = 1;
-  *c = z;
-}
-
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 7) return th_fail(TH_EINVAL, "invalid argument");
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 8) return th_fail(TH_EINVAL, "invalid argument");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
@@ -883,10 +1058,15 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   TH_TRY(grid_ensure_workspace(g, true, s));
   const long long n = g->n;
   const unsigned nb = nb1(n);
-  for (float* a : {g->r32, g->d32, g->mu32, g->p32[0], g->p32[1], g->zc32[0], g->zc32[1], g->zc32[2]})
+  for (float* a : {g->r32, g->d32, g->p32[0], g->p32[1], g->zc32[0], g->zc32[1], g->zc32[2]})
     k_fill<float><<<nb, 256, 0, s>>>(n, a, 1.0f);
+  // small mu keeps r = r - alpha mu away from zero over the timed launches, so the
+  // update kernel never decides convergence (which would turn later launches into early exits)
+  k_fill<float><<<nb, 256, 0, s>>>(n, g->mu32, 1e-4f);
   for (double* a : {g->theta[0], g->theta_n, g->r64, g->mu64, g->p64[0], g->p64[1], g->zc64[0], g->zc64[1], g->zc64[2]})
     k_fill<double><<<nb, 256, 0, s>>>(n, a, 1.0);
+  for (float* a : {g->th_hi, g->thn_hi}) k_fill<float><<<nb, 256, 0, s>>>(n, a, 20.0f);
+  for (float* a : {g->th_lo, g->thn_lo}) k_fill<float><<<nb, 256, 0, s>>>(n, a, 1e-7f);
   k_fill<float><<<nb, 256, 0, s>>>(n, (float*)g->stage_p, 1e-4f);
   TH_CHECK_LAUNCH();
   const void* pp[1] = {g->stage_p};
@@ -899,24 +1079,50 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   auto launch = [&]() -> th_status {
     switch (kernel) {
       case 0:
-        k_apply_f32<<<P.gb, P.tb, 0, s>>>(P.d, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->zc32[0], g->zc32[1]);
+        if (P.v4)
+          k_apply_v4<float><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->zc32[0],
+                                                    g->zc32[1]);
+        else
+          k_apply_f32<<<P.gb, P.tb, 0, s>>>(P.d, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->zc32[0], g->zc32[1]);
         break;
       case 1:
+        if (P.v4) {
+          k_cheb_v4<float, true, false><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
+                                                                g->tab, V.r, V.zc[0], V.zc[1], V.zc[2], c1, c2,
+                                                                g->partials, g->partials_stride, g->counters);
+          break;
+        }
         k_cheb<float, float, true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
                                                                 V.r, V.zc[0], V.zc[1], V.zc[2], V.invd, c1, c2,
                                                                 g->partials, g->partials_stride, g->counters);
         break;
       case 2:
+        if (P.v4) {
+          k_cheb_v4<__nv_bfloat16, true, false><<<P.gb4, P.tb4, 0, s>>>(
+              P.d, P.zc, g->ctl, g->f16.gx, g->f16.gy, g->f16.gz, g->tab, V.r, V.zc[0], V.zc[1], V.zc[2], c1, c2,
+              g->partials, g->partials_stride, g->counters);
+          break;
+        }
         k_cheb<float, __nv_bfloat16, true, false><<<P.gb, P.tb, 0, s>>>(
             P.d, g->ctl, g->f16.gx, g->f16.gy, g->f16.gz, g->tab, V.r, V.zc[0], V.zc[1], V.zc[2], V.invd, c1, c2,
             g->partials, g->partials_stride, g->counters);
         break;
       case 3:
+        if (P.v4) {
+          k_spmv_dot_v4<<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, V.zc[0],
+                                                V.p[0], V.p[1], V.mu, g->partials, g->partials_stride, g->counters);
+          break;
+        }
         k_spmv_dot<float, float><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
                                                         V.zc[0], V.p[0], V.p[1], V.mu, g->partials,
                                                         g->partials_stride, g->counters);
         break;
       case 4:
+        if (P.v4) {
+          k_update_v4<false, 1><<<P.nbu4, 256, 0, s>>>(P.d.n / 4, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0],
+                                                      1.0f, 1, 1, 0, g->partials, g->partials_stride, g->counters);
+          break;
+        }
         k_update<float, false, 1><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0], 1.0f,
                                                         1, 1, 0, g->partials, g->partials_stride, g->counters);
         break;
@@ -925,6 +1131,13 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
                                                        (const float* const*)g->dev_ptrs,
                                                        P.transient ? g->theta_n : nullptr, g->r32, 2, 0,
                                                        g->partials, g->partials_stride, g->counters);
+        break;
+      case 8:
+        k_residual_df<float><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
+                                                   (const float* const*)g->dev_ptrs,
+                                                   P.transient ? g->thn_hi : nullptr,
+                                                   P.transient ? g->thn_lo : nullptr, g->r32, 0, g->partials,
+                                                   g->partials_stride, g->counters);
         break;
       case 6:
         k_apply_f64<<<P.gb, P.tb, 0, s>>>(P.d, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, g->zc64[0], g->zc64[1]);
