@@ -58,7 +58,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--degree", type=int, default=6, help="Chebyshev degree k (SpMVs per application)")
+    ap.add_argument("--degree", type=int, default=8, help="Chebyshev degree k (SpMVs per application)")
+    ap.add_argument("--guess", type=int, default=0,
+                    help="transient initial guess: 0 previous step (paper), 1 linear extrapolation")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-stack batched section")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the 2048x2048x10 adjoint section")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -68,6 +72,8 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=N_STEPS,
                     help="backward-Euler steps per trajectory (100 for the measured workload; "
                          "fewer only for short profiling captures)")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not sample nvidia-smi (profiling runs under ncu)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only time each hot kernel on the full-size grid (short ncu target)")
     ap.add_argument("--reps", type=int, default=40, help="launches per kernel timing")
@@ -89,6 +95,17 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------- clocks
+
+class NoClocks:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+    def summary(self):
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (profiling run)"]}
+
 
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -262,7 +279,7 @@ def main():
     maps = [torch.from_numpy(m).cuda() for m in maps_h]
     T = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
     opts = dict(precision="mixed", precond="cheb", cheb_degree=args.degree, tol_rel=1e-8,
-                use_graph=0 if args.polled else 1)
+                use_graph=0 if args.polled else 1, guess=args.guess)
 
     nsteps = args.time_steps
 
@@ -282,7 +299,7 @@ def main():
         stats = trajectory(opts, T, maps)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with (NoClocks() if args.no_clocks else ClockSampler(local)) as clk:
         barrier()
         e0.record(stream)
         for _ in range(args.steps):
@@ -360,12 +377,82 @@ def main():
                          "d2h_bytes_per_step": int(inst.n * 8),
                          "note": "per bench step (one 100-step trajectory): 4 power maps + T_0 to the device, "
                                  "T_100 back, through thermal_run_transient with pinned host buffers"}
+    if not args.no_batched:
+        result["batched"] = batched_section(args)
+    if not args.no_adjoint:
+        result["adjoint"] = adjoint_section(args)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
         dist.destroy_process_group()
+
+
+def _event_ms(fn, reps=1):
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def batched_section(args):
+    """64 independent stacks of uneven size (128^2x4 .. 512^2x8, k perturbed +-20%),
+    steady, FP32 PCG (Chebyshev, degree 30) + FP64 refinement to 1e-8, all in one
+    persistent cooperative launch."""
+    import numpy as np
+    import torch
+    import thermal_inputs as ti
+    from paper_2606_17850_gb300 import ThermalGrid, solve_batched
+    insts = ti.c4_instances()
+    grids = [ThermalGrid.from_stack(i.nx, i.ny, i.stack) for i in insts]
+    powers = [torch.from_numpy(i.power).cuda() for i in insts]
+    Ts = [torch.empty(i.n, dtype=torch.float64, device="cuda") for i in insts]
+    o = dict(tol_rel=1e-8, precond="cheb", cheb_degree=30)
+    solve_batched(grids, powers, Ts, **o)  # set-up: Lanczos per instance
+    ms, stats = _event_ms(lambda: solve_batched(grids, powers, Ts, **o), reps=max(1, args.steps))
+    n = sum(i.n for i in insts)
+    it = sum(s["inner_it"] for s in stats)
+    return {"workload": "64 steady stacks of uneven size (128^2x4, 256^2x6, 384^2x8, 512^2x8; k x U[0.8,1.2])",
+            "unknowns": n, "ms_per_batch_solve": ms, "max_rel_res": max(s["rel_res"] for s in stats),
+            "status": max(s["status"] for s in stats), "inner_it_sum": it,
+            "max_inner_it": max(s["inner_it"] for s in stats),
+            "launch": "one cooperative persistent kernel for all 64 instances"}
+
+
+def adjoint_section(args):
+    """2048 x 2048 x 10 memory-on-logic stack (41.9M unknowns): steady solve, log-sum-exp
+    hotspot objective (beta = 2/K) over the two FEOL layers, adjoint gradient w.r.t. the
+    power map and the 10 layer conductivities."""
+    import numpy as np
+    import torch
+    import thermal_inputs as ti
+    from paper_2606_17850_gb300 import ThermalGrid
+    inst = ti.c5(dtype=np.float32)
+    g = ThermalGrid.from_stack(inst.nx, inst.ny, inst.stack)
+    P = torch.from_numpy(inst.power).cuda()
+    o = dict(precision="mixed", precond="cheb", cheb_degree=30, tol_rel=1e-8)
+    layers = inst.stack.power_layers()
+    T, _ = g.solve_steady(P, **o)  # set-up
+
+    def one():
+        T, s1 = g.solve_steady(P, **o)
+        J, w = g.hotspot_lse(T, layers, 2.0)
+        dP, dk, s2 = g.grad(T, w, dJdP_dtype=torch.float32, **o)
+        return s1, s2, J
+
+    ms, (s1, s2, J) = _event_ms(one, reps=1)
+    return {"workload": "2048x2048x10 memory-on-logic stack, forward solve + LSE + adjoint gradient",
+            "unknowns": inst.n, "ms_forward_plus_gradient": ms, "J": J,
+            "forward_inner_it": s1["inner_it"], "adjoint_inner_it": s2["inner_it"],
+            "rel_res": [s1["rel_res"], s2["rel_res"]]}
 
 
 def kernel_table(grid, n, reps, peak, peak_kind):

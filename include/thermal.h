@@ -89,7 +89,9 @@ typedef struct thermal_solve_opts {
   int use_graph;       /* 1: device-side loop control in a CUDA graph with conditional nodes   */
   int batched_mode;    /* thermal_solve_batched: 0 one persistent launch when possible, 1 one */
                        /* instance after another through the single-grid solver (0)          */
-  int reserved[7];
+  int guess;           /* transient initial guess: 0 the previous step T_n (the paper's warm  */
+                       /* start), 1 linear extrapolation 2 T_n - T_{n-1} inside a step loop (0) */
+  int reserved[6];
 } thermal_solve_opts;
 
 typedef struct thermal_solve_stats {

@@ -34,7 +34,8 @@ class SolveOpts(C.Structure):
         ("use_guess", C.c_int),
         ("use_graph", C.c_int),
         ("batched_mode", C.c_int),
-        ("reserved", C.c_int * 7),
+        ("guess", C.c_int),
+        ("reserved", C.c_int * 6),
     ]
 
 

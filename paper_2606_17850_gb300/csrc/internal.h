@@ -97,6 +97,9 @@ struct thermal_grid {
   float *zc32[3] = {nullptr, nullptr, nullptr};
   // mixed path: theta and theta_n as double-float (hi, lo) pairs
   float *th_hi = nullptr, *th_lo = nullptr, *thn_hi = nullptr, *thn_lo = nullptr;
+  // theta_{n-1} for the extrapolated transient guess (allocated on first use)
+  float *thm_hi = nullptr, *thm_lo = nullptr;
+  double* thm64 = nullptr;
   double* partials = nullptr;   // reduction partials
   int partials_stride = 0;
   unsigned* counters = nullptr; // reduction counters (zeroed)

@@ -167,6 +167,32 @@ __global__ void k_copy_df(long long n, const float* __restrict__ ah, const float
   bl[i] = al[i];
 }
 
+// Start of a step with the extrapolated guess: theta_n <- theta (the solution of
+// the previous step), theta <- 2 theta_n - theta_{n-1}, theta_{n-1} <- theta_n.
+__global__ void k_step_extrap_df(long long n, float* th_hi, float* th_lo, float* thn_hi, float* thn_lo,
+                                 float* thm_hi, float* thm_lo) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const df cur = df_make(th_hi[i], th_lo[i]);
+  const df prev = df_make(thm_hi[i], thm_lo[i]);
+  const df g = df_sub(df_add(cur, cur), prev);
+  thn_hi[i] = cur.hi;
+  thn_lo[i] = cur.lo;
+  thm_hi[i] = cur.hi;
+  thm_lo[i] = cur.lo;
+  th_hi[i] = g.hi;
+  th_lo[i] = g.lo;
+}
+
+__global__ void k_step_extrap64(long long n, double* th, double* thn, double* thm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double cur = th[i];
+  thn[i] = cur;
+  th[i] = 2.0 * cur - thm[i];
+  thm[i] = cur;
+}
+
 // theta += ||r|| d in double-float.
 __global__ void k_theta_axpy_df(long long n, const Ctl* ctl, float* __restrict__ th_hi, float* __restrict__ th_lo,
                                 const float* __restrict__ d) {
@@ -198,18 +224,21 @@ __global__ void k_residual_df(Dims d, Ctl* ctl, Faces32 gh, Faces32 gl, const La
   float v[2] = {0.f, 0.f};
   if (c.valid) {
     const df ti = df_make(th_hi[c.i], th_lo[c.i]);
-    df flux = df_make(0.f, 0.f);
-    auto face = [&](const float* gH, const float* gL, long long fi, long long j) {
+    // the six face fluxes are independent; summing them as a tree keeps the
+    // dependent chain of FP32 operations short (the kernel is latency-bound otherwise)
+    df t[6];
+    auto face = [&](bool has, const float* gH, const float* gL, long long fi, long long j) -> df {
+      if (!has) return df_make(0.f, 0.f);
       const df g = df_make(__ldg(gH + fi), __ldg(gL + fi));
-      const df dlt = df_sub(ti, df_make(th_hi[j], th_lo[j]));
-      flux = df_add(flux, df_mul(g, dlt));
+      return df_mul(g, df_sub(ti, df_make(th_hi[j], th_lo[j])));
     };
-    if (c.x + 1 < d.nx) face(gh.gx, gl.gx, c.i, c.i + 1);
-    if (c.x > 0) face(gh.gx, gl.gx, c.i - 1, c.i - 1);
-    if (c.y + 1 < d.ny) face(gh.gy, gl.gy, c.i, c.i + d.nx);
-    if (c.y > 0) face(gh.gy, gl.gy, c.i - d.nx, c.i - d.nx);
-    if (c.z + 1 < d.L) face(gh.gz, gl.gz, c.i, c.i + d.pxy);
-    if (c.z > 0) face(gh.gz, gl.gz, c.i - d.pxy, c.i - d.pxy);
+    t[0] = face(c.x + 1 < d.nx, gh.gx, gl.gx, c.i, c.i + 1);
+    t[1] = face(c.x > 0, gh.gx, gl.gx, c.i - 1, c.i - 1);
+    t[2] = face(c.y + 1 < d.ny, gh.gy, gl.gy, c.i, c.i + d.nx);
+    t[3] = face(c.y > 0, gh.gy, gl.gy, c.i - d.nx, c.i - d.nx);
+    t[4] = face(c.z + 1 < d.L, gh.gz, gl.gz, c.i, c.i + d.pxy);
+    t[5] = face(c.z > 0, gh.gz, gl.gz, c.i - d.pxy, c.i - d.pxy);
+    const df flux = df_add(df_add(df_add(t[0], t[1]), df_add(t[2], t[3])), df_add(t[4], t[5]));
     const df sink = df_make(__ldg(&tab->sink_hi[c.z]), __ldg(&tab->sink_lo[c.z]));
     df b = df_make((float)P[c.i], 0.f);
     if (sizeof(TP) == 8) b.lo = (float)((double)P[c.i] - (double)b.hi);

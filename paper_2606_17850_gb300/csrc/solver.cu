@@ -29,6 +29,7 @@ struct Plan {
   double inv_theta = 1.0, lmin = 0.0, lmax = 0.0;
   int pc_spmv = 0;          // stencil applications per preconditioner application
   // vectorised FP32 kernels (nx % 4 == 0): grid of the z-walk kernels and the update
+  bool extrap = false;  // extrapolated initial guess in a step loop
   bool v4 = false;
   int zc = 1;
   dim3 gb4, tb4;
@@ -551,6 +552,13 @@ static th_status enq_prepare(const Plan& P, cudaStream_t st, const double* T, do
   else
     k_prepare_df<<<nb1(n), 256, 0, st>>>(n, T, toff, mode, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo);
   TH_CHECK_LAUNCH();
+  if (P.extrap) {  // no history yet: theta_{n-1} = theta_n (the first step starts from T_0)
+    if (P.prec == TH_PREC_FP64)
+      k_copy64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->thm64);
+    else
+      k_copy_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo);
+    TH_CHECK_LAUNCH();
+  }
   return TH_OK;
 }
 static th_status enq_finalize(const Plan& P, cudaStream_t st, double toff, double* T) {
@@ -566,6 +574,14 @@ static th_status enq_finalize(const Plan& P, cudaStream_t st, double toff, doubl
 static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
   thermal_grid* g = P.g;
   const long long n = P.d.n;
+  if (P.extrap) {
+    if (P.prec == TH_PREC_FP64)
+      k_step_extrap64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n, g->thm64);
+    else
+      k_step_extrap_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo, g->thm_hi, g->thm_lo);
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  }
   if (P.prec == TH_PREC_FP64)
     k_copy64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n);
   else
@@ -577,11 +593,11 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
 // ------------------------------------------------------------------ graph building
 
 struct GraphKey {
-  int kind, prec, pc, k, scaled, pdtype, lz;
+  int kind, prec, pc, k, scaled, pdtype, lz, extrap;
   double dt;
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, dt) <
-           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.dt);
+    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, dt) <
+           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.extrap, o.dt);
   }
 };
 struct GraphEntry {
@@ -880,8 +896,24 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
   Plan P;
   const bool transient = (kind == KIND_STEP || kind == KIND_RUN);
+  if (o->guess != 0 && o->guess != 1) return th_fail(TH_EINVAL, "guess must be 0 or 1");
   const double toff = (kind == KIND_ADJ) ? 0.0 : g->t_amb;  // the adjoint state has no offset
   TH_TRY(make_plan(g, transient ? dt : 0.0, o, pdtype, transient, P, s));
+  P.extrap = (kind == KIND_RUN && o->guess == 1);
+  if (P.extrap) {
+    const size_t n = (size_t)g->n;
+    auto al = [&](auto** p, size_t bytes) -> th_status {
+      if (*p) return TH_OK;
+      if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return th_fail(TH_ENOMEM, "allocation of the previous-step state failed");
+      }
+      return TH_OK;
+    };
+    TH_TRY(al(&g->thm_hi, n * sizeof(float)));
+    TH_TRY(al(&g->thm_lo, n * sizeof(float)));
+    TH_TRY(al(&g->thm64, n * sizeof(double)));
+  }
   TH_TRY(ensure_stage(g, 0));
   TH_TRY(stage_power(g, maps, n_maps, pdtype, s));
   const size_t tb = sizeof(double) * (size_t)g->n;
@@ -892,7 +924,8 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   const CtlInit ci = ctl_init(o, kind == KIND_RUN ? n_steps : 1, spm, n_maps);
   TH_CUDA(cudaEventRecord(e0, s));
   if (o->use_graph) {
-    const GraphKey key{kind, P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.transient ? dt : 0.0};
+    const GraphKey key{kind, P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.extrap ? 1 : 0,
+                       P.transient ? dt : 0.0};
     if (!g->graphs) {
       g->graphs = new GraphCache();
       for (auto& sx : g->graphs->cs) TH_CUDA(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));

@@ -76,3 +76,86 @@ def test_fullsize_stencil_sampled_rows(setup):
     ref = sub @ x
     bound = abs(sub) @ np.abs(x)
     assert np.all(np.abs(y[rows] - ref) <= 1e-14 * bound)
+
+
+# ----------------------------------------------------------------- adjoint at 2048 x 2048 x 10
+
+@pytest.fixture(scope="module")
+def c5():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2606_17850_gb300 import ThermalGrid
+    inst = ti.c5(dtype=np.float32)
+    g = ThermalGrid.from_stack(inst.nx, inst.ny, inst.stack)
+    return inst, g
+
+
+def test_fullsize_adjoint_c5(c5):
+    """41.9M unknowns: log-sum-exp hotspot gradient.  Checks that hold at any size:
+    sum_top h S lambda = sum w = 1; the directional derivative along the power of one
+    FEOL layer and along one layer conductivity against central differences (1e-4)."""
+    inst, g = c5
+    st = inst.stack
+    opts = dict(precision="mixed", precond="cheb", cheb_degree=30, tol_rel=1e-10)
+    layers = st.power_layers()
+    beta = 2.0
+    P = torch.from_numpy(inst.power).cuda()
+    T, s = g.solve_steady(P, **opts)
+    J, w = g.hotspot_lse(T, layers, beta)
+    dJdP, dJdk, _ = g.grad(T, w, dJdP_dtype=torch.float64, **opts)
+    S = st.dx * st.dy
+    top = slice((st.L - 1) * inst.nx * inst.ny, st.L * inst.nx * inst.ny)
+    assert abs(st.h * S * dJdP[top].sum().item() - 1.0) < 1e-6
+    # direction: the power of the logic FEOL layer
+    dP = torch.zeros_like(P)
+    sl = slice(layers[0] * inst.nx * inst.ny, (layers[0] + 1) * inst.nx * inst.ny)
+    dP[sl] = P[sl]
+    eps = 1e-3
+    Jp = g.hotspot_lse(g.solve_steady(P + eps * dP, **opts)[0], layers, beta, want_grad=False)[0]
+    Jm = g.hotspot_lse(g.solve_steady(P - eps * dP, **opts)[0], layers, beta, want_grad=False)[0]
+    fd = (Jp - Jm) / (2 * eps)
+    an = float((dJdP * dP.double()).sum())
+    assert abs(fd - an) <= 1e-4 * abs(an), (fd, an)
+    # direction: conductivity of the spreader layer
+    k = st.k()
+    l = 8
+    kp, km = k.copy(), k.copy()
+    kp[l] *= 1 + eps
+    km[l] *= 1 - eps
+    g.set_conductivity(kp)
+    Jp = g.hotspot_lse(g.solve_steady(P, **opts)[0], layers, beta, want_grad=False)[0]
+    g.set_conductivity(km)
+    Jm = g.hotspot_lse(g.solve_steady(P, **opts)[0], layers, beta, want_grad=False)[0]
+    g.set_conductivity(k)
+    fd = (Jp - Jm) / (2 * eps * k[l])
+    assert abs(fd - dJdk[l]) <= 1e-4 * abs(dJdk[l]), (fd, dJdk[l])
+
+
+# ----------------------------------------------------------------- batched: 64 uneven stacks
+
+def test_fullsize_batched_c4():
+    """The 64-instance batch (about 6e7 unknowns) in one persistent launch; every
+    instance converges and sampled instances (one per size class) meet the
+    relative residual against the oracle's own CSR matrix."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2606_17850_gb300 import ThermalGrid, solve_batched
+    insts = ti.c4_instances()
+    grids = [ThermalGrid.from_stack(i.nx, i.ny, i.stack) for i in insts]
+    powers = [torch.from_numpy(i.power).cuda() for i in insts]
+    Ts = [torch.empty(i.n, dtype=torch.float64, device="cuda") for i in insts]
+    stats = solve_batched(grids, powers, Ts, tol_rel=1e-8, precond="cheb", cheb_degree=30)
+    assert all(s["status"] == 0 and s["rel_res"] <= 1e-8 for s in stats)
+    seen = set()
+    for inst, T in zip(insts, Ts):
+        key = (inst.nx, inst.stack.L)
+        if key in seen:
+            continue
+        seen.add(key)
+        A = disc.assemble(inst.nx, inst.ny, inst.stack).tocsr()
+        b = disc.rhs_steady(inst.nx, inst.ny, inst.stack, inst.power.astype(np.float64))
+        assert osolve.rel_residual(A, T.cpu().numpy(), b, inst.stack.t_amb) <= 1.05e-8

@@ -234,9 +234,10 @@ def test_transient_step(prec, nx):
     assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
 
 
+@pytest.mark.parametrize("guess", [0, 1])
 @pytest.mark.parametrize("graph", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_run_transient_schedule(graph, prec):
+def test_run_transient_schedule(graph, prec, guess):
     st = ti.stack_c2()
     nx, ny, dt = 40, 26, 1e-4
     maps = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s + j) for j in (0, 1)], np.float32)
@@ -245,7 +246,7 @@ def test_run_transient_schedule(graph, prec):
     g = grid_of(nx, ny, st)
     T = cuda(np.full(nx * ny * st.L, st.t_amb))
     T, stats = g.run_transient([cuda(m) for m in maps], spm, n_steps, dt, T, precision=prec, tol_rel=1e-10,
-                               cheb_degree=6, use_graph=graph)
+                               cheb_degree=6, use_graph=graph, guess=guess)
     sched = [maps[(s // spm) % 2].astype(np.float64) for s in range(n_steps)]
     ref = osolve.transient(nx, ny, st, sched, dt, np.full(nx * ny * st.L, st.t_amb))[-1]
     assert stats["steps"] == n_steps and stats["status"] == 0
