@@ -39,12 +39,20 @@ SEEDS = (30, 31, 32, 33)
 
 # algorithmic bytes per cell of each timed kernel (reads + writes it must make)
 KERNEL_BYTES = {
-    "cheb_f32": 28,      # gx gy gz (12) + z_m, z_{m-1}, r (12) + z_{m+1} (4)
-    "spmv_dot_f32": 28,  # gx gy gz (12) + z, p_old (8) + p_new, mu (8)
+    # the workload's grid has one conductivity per layer: the solver's FP32 and
+    # double-float kernels take the face conductances from a per-layer table
+    "cheb_f32": 16,      # z_m, z_{m-1}, r (12) + z_{m+1} (4)
+    "spmv_dot_f32": 16,  # z, p_old (8) + p_new, mu (8)
     "update_f32": 32,    # x, r (read+write 16) + p, mu, 1/diag (12) + z (4)
-    "stencil_f32": 20,   # gx gy gz (12) + x (4) + y (4)
+    "stencil_f32": 8,    # x (4) + y (4)
+    "residual_df": 24,   # theta, theta_n as hi+lo (16) + P f32 (4) + r f32 (4)
+    # the same kernels reading per-face arrays (grids with a per-cell conductivity map)
+    "cheb_f32_faces": 28,      # + gx gy gz (12)
+    "spmv_dot_f32_faces": 28,  # + gx gy gz (12)
+    "stencil_f32_faces": 20,   # + gx gy gz (12)
+    "residual_df_faces": 48,   # + gx gy gz hi+lo (24)
     "cheb_bf16": 22,     # gx gy gz bf16 (6) + 16
-    "residual_df": 48,   # gx gy gz hi+lo (24) + theta, theta_n hi+lo (16) + P f32 (4) + r f32 (4)
+    # plain FP64 path
     "residual_f64": 48,  # gx gy gz (24) + theta, theta_n (16) + P f32 (4) + r f32 (4)
     "stencil_f64": 40,   # gx gy gz (24) + x (8) + y (8)
     "cheb_f64": 64,      # gx gy gz (24) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)

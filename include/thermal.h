@@ -144,6 +144,17 @@ th_status thermal_grid_set_geometry(thermal_grid* g, double dx, double dy, const
 /* Replaces the per-layer conductivities k[layers] (host) and recomputes the faces. */
 th_status thermal_grid_set_conductivity(thermal_grid* g, const double* k);
 
+/*
+ * Gives every cell its own conductivity: k_cell[n_cells] (W/(m K), > 0; host or
+ * device, cell order as above).  A face then joins two half cells of different
+ * conductivity, g = S / (l_a/(2 k_a) + l_b/(2 k_b)), and the solver reads the
+ * per-face arrays (layer-uniform grids read a per-layer table instead).  Replaces
+ * any earlier per-layer conductivities until thermal_grid_set_conductivity is
+ * called again.  thermal_grad's dJdk output is not defined for such a grid
+ * (TH_ESTATE).  Synchronous.
+ */
+th_status thermal_grid_set_conductivity_map(thermal_grid* g, const double* k_cell);
+
 /* Frees the grid and all of its device memory.  NULL is accepted. */
 th_status thermal_grid_destroy(thermal_grid* g);
 
@@ -199,16 +210,19 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  * Diagnostic timing of one hot kernel: launches it `reps` times back to back on
  * `stream` between two CUDA events and writes the average duration (ms) of one
  * launch to *ms.  The kernel runs on the grid's own work vectors (filled with
- * finite values first; their contents are overwritten).  kernel ids:
- *   0  FP32 stencil product (Algorithm 2's y = A x)
- *   1  FP32 Chebyshev step on the Jacobi-scaled operator (FP32 coefficients)
- *   2  FP32 Chebyshev step with BF16 coefficients
- *   3  FP32 fused search direction + stencil + p^T A p (Algorithm 1, mu = A p)
+ * finite values first; their contents are overwritten).  Kernels marked (*) read
+ * the per-layer coefficient table on a layer-uniform grid and the per-face arrays
+ * otherwise (the variant the solver runs).  kernel ids:
+ *   0  FP32 stencil product (Algorithm 2's y = A x) (*)
+ *   1  FP32 Chebyshev step on the Jacobi-scaled operator (*)
+ *   2  FP32 Chebyshev step reading BF16 per-face coefficients
+ *   3  FP32 fused search direction + stencil + p^T A p (Algorithm 1, mu = A p) (*)
  *   4  FP32 fused x/r update + Jacobi z + dot products (Algorithm 1, AXPYs)
- *   5  FP64 refinement residual r = b - A theta with ||r||, ||b||
+ *   5  FP64 refinement residual r = b - A theta with ||r||, ||b|| (per-face arrays)
  *   6  FP64 stencil product
  *   7  FP64 Chebyshev step (plain FP64 path)
- *   8  double-float refinement residual (the mixed path's r = b - A theta)
+ *   8  double-float refinement residual (the mixed path's r = b - A theta) (*)
+ *   9, 10, 11, 12  kernels 1, 3, 8, 0 reading the per-face arrays
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

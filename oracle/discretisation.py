@@ -44,18 +44,21 @@ def convective_conductance(stack, half_cell_top=False):
     return 1.0 / (1.0 / (h * S) + top.thickness / (2.0 * top.k * S))
 
 
-def assemble(nx, ny, stack, dt=None, half_cell_top=False):
+def assemble(nx, ny, stack, dt=None, half_cell_top=False, k_cell=None):
     """Assemble the system matrix A of Eq. (steady-state) (dt=None) or Eq. (transient).
 
     Row by row: for every cell, each of its (up to) six neighbours j contributes
     +g to A[i,i] and -g to A[i,j]; a top-layer cell adds h S; with a time step the
-    cell adds C V / dt.  Returns a CSR matrix in FP64.
+    cell adds C V / dt.  ``k_cell`` (optional, N values) gives every cell its own
+    conductivity; a face then joins two half cells of different k.  Returns CSR, FP64.
     """
     k, c, dz, dx, dy = layer_constants(stack)
     L = stack.L
     n = nx * ny * L
     idx = np.arange(n).reshape(L, ny, nx)
     zz, yy, xx = np.meshgrid(np.arange(L), np.arange(ny), np.arange(nx), indexing="ij")
+    if k_cell is not None:
+        return _assemble_kmap(nx, ny, stack, dt, half_cell_top, np.asarray(k_cell, dtype=np.float64).reshape(L, ny, nx))
 
     rows, cols, vals = [], [], []
     diag = np.zeros(n)
@@ -99,6 +102,43 @@ def assemble(nx, ny, stack, dt=None, half_cell_top=False):
     vals.append(diag)
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(n, n)).tocsr()
+    A.sum_duplicates()
+    return A
+
+
+def _assemble_kmap(nx, ny, stack, dt, half_cell_top, kc):
+    """Row-wise assembly with a per-cell conductivity: each face is the series
+    combination of its two half cells, g = S / (l/(2 k_a) + l/(2 k_b))."""
+    k, c, dz, dx, dy = layer_constants(stack)
+    L = stack.L
+    n = nx * ny * L
+    idx = np.arange(n).reshape(L, ny, nx)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(n)
+    dzc = np.broadcast_to(dz[:, None, None], (L, ny, nx))
+
+    def couple(i, j, g):
+        rows.append(i.ravel()); cols.append(j.ravel()); vals.append(-g.ravel())
+        np.add.at(diag, i.ravel(), g.ravel())
+
+    # x faces between (.., x) and (.., x+1), both directions
+    g = face_conductance(dy * dzc[:, :, :-1], dx, kc[:, :, :-1], dx, kc[:, :, 1:])
+    couple(idx[:, :, :-1], idx[:, :, 1:], g)
+    couple(idx[:, :, 1:], idx[:, :, :-1], g)
+    g = face_conductance(dx * dzc[:, :-1, :], dy, kc[:, :-1, :], dy, kc[:, 1:, :])
+    couple(idx[:, :-1, :], idx[:, 1:, :], g)
+    couple(idx[:, 1:, :], idx[:, :-1, :], g)
+    g = face_conductance(dx * dy, dzc[:-1], kc[:-1], dzc[1:], kc[1:])
+    couple(idx[:-1], idx[1:], g)
+    couple(idx[1:], idx[:-1], g)
+    if half_cell_top:
+        raise NotImplementedError("half-cell convective term with a conductivity map")
+    top = idx[L - 1].reshape(-1)
+    diag[top] += convective_conductance(stack)
+    if dt is not None:
+        diag += np.repeat(c * dx * dy * dz / dt, nx * ny)
+    rows.append(np.arange(n)); cols.append(np.arange(n)); vals.append(diag)
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
     A.sum_duplicates()
     return A
 

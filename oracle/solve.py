@@ -62,9 +62,9 @@ class Factorised:
         return x
 
 
-def steady(nx, ny, stack, power, half_cell_top=False):
+def steady(nx, ny, stack, power, half_cell_top=False, k_cell=None):
     """Temperatures (deg C) of Eq. (steady-state) for a power map in W per cell."""
-    A = disc.assemble(nx, ny, stack, half_cell_top=half_cell_top)
+    A = disc.assemble(nx, ny, stack, half_cell_top=half_cell_top, k_cell=k_cell)
     b = disc.rhs_steady(nx, ny, stack, power, half_cell_top)
     return solve_exact(A, b)
 

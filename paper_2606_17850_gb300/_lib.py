@@ -77,6 +77,7 @@ SIGNATURES = {
     "thermal_grid_create": (C.c_int, [C.c_int, C.c_int, C.c_int, _dp, _dp, C.c_double, C.POINTER(_vp)]),
     "thermal_grid_set_geometry": (C.c_int, [_vp, C.c_double, C.c_double, _dp, C.c_double]),
     "thermal_grid_set_conductivity": (C.c_int, [_vp, _dp]),
+    "thermal_grid_set_conductivity_map": (C.c_int, [_vp, _vp]),
     "thermal_grid_destroy": (C.c_int, [_vp]),
     "thermal_grid_dims": (C.c_int, [_vp, C.POINTER(C.c_int64), _ip, _ip, _ip]),
     "thermal_grid_faces": (C.c_int, [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp]),

@@ -86,6 +86,11 @@ class ThermalGrid:
     def set_conductivity(self, k: Sequence[float]):
         L.check(L.load().thermal_grid_set_conductivity(self._h, _darr(k)))
 
+    def set_conductivity_map(self, k_cell: torch.Tensor):
+        """Per-cell conductivities (float64, host or device, n values)."""
+        k_cell = k_cell.contiguous().to(torch.float64)
+        L.check(L.load().thermal_grid_set_conductivity_map(self._h, _ptr(k_cell)))
+
     # ------------------------------------------------------------------ kernels
 
     def faces(self, dt=0.0, device="cuda"):
@@ -113,7 +118,8 @@ class ThermalGrid:
         return tuple(x.value for x in v)
 
     KERNELS = {"stencil_f32": 0, "cheb_f32": 1, "cheb_bf16": 2, "spmv_dot_f32": 3, "update_f32": 4,
-               "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7, "residual_df": 8}
+               "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7, "residual_df": 8,
+               "cheb_f32_faces": 9, "spmv_dot_f32_faces": 10, "residual_df_faces": 11, "stencil_f32_faces": 12}
 
     def kernel_time(self, kernel, reps=50, dt=0.0):
         """Average duration (ms) of one launch of a hot kernel on this grid (CUDA events)."""

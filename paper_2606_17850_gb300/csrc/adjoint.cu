@@ -190,6 +190,8 @@ extern "C" th_status thermal_grad(thermal_grid* g, const double* T, const double
     if (!g || !T || !dJdT) return th_fail(TH_EINVAL, "NULL argument");
     if (dJdP && dJdP_dtype != TH_F32 && dJdP_dtype != TH_F64) return th_fail(TH_EINVAL, "dJdP dtype");
     if (!is_device_pointer(T) || !is_device_pointer(dJdT)) return th_fail(TH_EINVAL, "T and dJdT must be device memory");
+    if (dJdk && !g->uniform)
+      return th_fail(TH_ESTATE, "dJ/dk per layer is not defined for a grid with a per-cell conductivity map");
     cudaStream_t s = (cudaStream_t)stream;
     TH_TRY(grid_ensure_workspace(g, false, s));
     double* lam = nullptr;

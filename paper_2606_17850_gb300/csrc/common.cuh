@@ -38,6 +38,11 @@ struct LayerTab {
   // double-float (hi + lo) copies for the mixed-path residual
   float sink_hi[TH_MAXL], sink_lo[TH_MAXL];  // h dx dy on the top layer, else 0
   float cdt_hi[TH_MAXL], cdt_lo[TH_MAXL];    // c dx dy dz / dt
+  // layer-uniform grids (one conductivity per layer): the interior face
+  // conductances of layer l (x, y) and between layers l and l+1 (z), FP32 and
+  // double-float; faces on the domain boundary are 0.
+  float gxl[TH_MAXL], gyl[TH_MAXL], gzl[TH_MAXL];
+  float gxl_hi[TH_MAXL], gxl_lo[TH_MAXL], gyl_hi[TH_MAXL], gyl_lo[TH_MAXL], gzl_hi[TH_MAXL], gzl_lo[TH_MAXL];
 };
 
 // Control block of one solve, in device memory.  Fields written by the last

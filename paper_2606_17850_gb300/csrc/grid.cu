@@ -112,6 +112,24 @@ __global__ void k_setup_faces(Dims d, const double* __restrict__ geo, double dx,
   f16.gx[c.i] = __double2bfloat16(gx); f16.gy[c.i] = __double2bfloat16(gy); f16.gz[c.i] = __double2bfloat16(gz);
 }
 
+// Per-face conductances from a per-cell conductivity map kc: every face joins two
+// half cells of (possibly) different conductivity.
+__global__ void k_setup_faces_map(Dims d, const double* __restrict__ geo, const double* __restrict__ kc, double dx,
+                                  double dy, Faces64 f64, Faces32 f32, Faces32 f32lo, Faces16 f16) {
+  const Cell c = cell_of(d);
+  if (!c.valid) return;
+  const double dz = geo[TH_MAXL + c.z], k = kc[c.i];
+  const double gx = (c.x + 1 < d.nx) ? series_face(dy * dz, dx, k, dx, kc[c.i + 1]) : 0.0;
+  const double gy = (c.y + 1 < d.ny) ? series_face(dx * dz, dy, k, dy, kc[c.i + d.nx]) : 0.0;
+  const double gz = (c.z + 1 < d.L) ? series_face(dx * dy, dz, k, geo[TH_MAXL + c.z + 1], kc[c.i + d.pxy]) : 0.0;
+  f64.gx[c.i] = gx; f64.gy[c.i] = gy; f64.gz[c.i] = gz;
+  f32.gx[c.i] = (float)gx; f32.gy[c.i] = (float)gy; f32.gz[c.i] = (float)gz;
+  f32lo.gx[c.i] = (float)(gx - (double)(float)gx);
+  f32lo.gy[c.i] = (float)(gy - (double)(float)gy);
+  f32lo.gz[c.i] = (float)(gz - (double)(float)gz);
+  f16.gx[c.i] = __double2bfloat16(gx); f16.gy[c.i] = __double2bfloat16(gy); f16.gz[c.i] = __double2bfloat16(gz);
+}
+
 __device__ __forceinline__ double diag_at(const Faces64& f, const LayerTab* tab, const Dims& d, const Cell& c) {
   double s = __ldg(&tab->s64[c.z]);
   if (c.x + 1 < d.nx) s += f.gx[c.i];
@@ -260,6 +278,8 @@ static th_status compute_faces(thermal_grid* g) {
   return TH_OK;
 }
 
+static inline double dy_of(const thermal_grid* g) { return g->dy; }
+
 th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s) {
   if (!g->geom) return th_fail(TH_ESTATE, "thermal_grid_set_geometry has not been called");
   if (dt > 0.0 && !g->has_c) return th_fail(TH_ESTATE, "grid was created without heat capacities");
@@ -283,6 +303,19 @@ th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s) {
     g->tab_host.dz[l] = g->dz[l];
     df_split(sink, &g->tab_host.sink_hi[l], &g->tab_host.sink_lo[l]);
     df_split(cdt, &g->tab_host.cdt_hi[l], &g->tab_host.cdt_lo[l]);
+    // the same expressions as k_setup_faces, so both paths see identical values
+    const double k = g->k[l], dz = g->dz[l];
+    const double gx = (dy_of(g) * dz) / (g->dx / (2.0 * k) + g->dx / (2.0 * k));
+    const double gy = (g->dx * dz) / (g->dy / (2.0 * k) + g->dy / (2.0 * k));
+    const double gz = (l + 1 < g->L)
+                          ? (g->dx * g->dy) / (dz / (2.0 * k) + g->dz[l + 1] / (2.0 * g->k[l + 1]))
+                          : 0.0;
+    g->tab_host.gxl[l] = (float)gx;
+    g->tab_host.gyl[l] = (float)gy;
+    g->tab_host.gzl[l] = (float)gz;
+    df_split(gx, &g->tab_host.gxl_hi[l], &g->tab_host.gxl_lo[l]);
+    df_split(gy, &g->tab_host.gyl_hi[l], &g->tab_host.gyl_lo[l]);
+    df_split(gz, &g->tab_host.gzl_hi[l], &g->tab_host.gzl_lo[l]);
   }
   g->tab_host.S = S;
   TH_CUDA(cudaMemcpyAsync(g->tab, &g->tab_host, sizeof(LayerTab), cudaMemcpyHostToDevice, s));
@@ -426,9 +459,56 @@ extern "C" th_status thermal_grid_set_conductivity(thermal_grid* g, const double
   if (!g) return th_fail(TH_EINVAL, "grid is NULL");
   TH_TRY(check_layer_array(k, g->L, true, "k"));
   g->k.assign(k, k + g->L);
+  g->uniform = true;
   if (!g->geom) return TH_OK;
   TH_CUDA(cudaDeviceSynchronize());
   return compute_faces(g);
+  ABI_GUARD_END
+}
+
+extern "C" th_status thermal_grid_set_conductivity_map(thermal_grid* g, const double* k_cell) {
+  ABI_GUARD_BEGIN
+  th_clear_error();
+  if (!g || !k_cell) return th_fail(TH_EINVAL, "NULL argument");
+  if (!g->geom) return th_fail(TH_ESTATE, "thermal_grid_set_geometry has not been called");
+  const size_t n = (size_t)g->n;
+  std::vector<double> hk;
+  const double* src = k_cell;
+  if (!is_device_pointer(k_cell)) {
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(k_cell[i]) || !(k_cell[i] > 0.0))
+        return th_fail(TH_EINVAL, "k_cell[%zu] = %g must be finite and > 0", i, k_cell[i]);
+  }
+  double *dk = nullptr, *geo = nullptr;
+  TH_TRY(dalloc(&dk, n));
+  th_status st = dalloc(&geo, 2 * TH_MAXL);
+  double geo_h[2 * TH_MAXL] = {0};
+  for (int l = 0; l < g->L; ++l) {
+    geo_h[l] = g->k[l];
+    geo_h[TH_MAXL + l] = g->dz[l];
+  }
+  cudaError_t e = cudaSuccess;
+  if (st == TH_OK) e = cudaMemcpy(dk, src, n * sizeof(double), cudaMemcpyDefault);
+  if (st == TH_OK && e == cudaSuccess) e = cudaMemcpy(geo, geo_h, sizeof(geo_h), cudaMemcpyHostToDevice);
+  if (st == TH_OK && e == cudaSuccess) {
+    k_setup_faces_map<<<grid_blocks(g), dim3(TH_BX, TH_BY)>>>(grid_dims(g), geo, dk, g->dx, g->dy, g->f64, g->f32,
+                                                              g->f32lo, g->f16);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  cudaFree(dk);
+  if (geo) cudaFree(geo);
+  if (st != TH_OK) return st;
+  if (e != cudaSuccess) return th_fail(TH_ECUDA, "conductivity map setup failed: %s", cudaGetErrorString(e));
+  g->uniform = false;
+  g->tab_valid = false;
+  g->zl_valid = false;
+  g->lanczos_cache.clear();
+  if (g->graphs) {
+    graph_cache_free(g->graphs);
+    g->graphs = nullptr;
+  }
+  return TH_OK;
   ABI_GUARD_END
 }
 

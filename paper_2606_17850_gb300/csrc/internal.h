@@ -67,6 +67,7 @@ struct thermal_grid {
   std::vector<double> k, c, dz;
   double h = 0, dx = 0, dy = 0, t_amb = 0;
   bool has_c = false, geom = false;
+  bool uniform = true;  // one conductivity per layer (no per-cell map): layer-table kernels apply
   int device = 0;
 
   Faces64 f64;

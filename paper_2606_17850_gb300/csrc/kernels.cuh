@@ -208,7 +208,7 @@ __global__ void k_theta_axpy_df(long long n, const Ctl* ctl, float* __restrict__
 // r = P + cdt (theta_n - theta) - sink theta - sum_faces g (theta_i - theta_j) in
 // double-float (theta, g, cdt and sink as hi + lo pairs); r rounded to FP32 for the
 // inner solve; ||r||^2 and ||b||^2 (b = P + cdt theta_n) reduced as in k_residual.
-template <typename TP>
+template <typename TP, bool UNI>
 __global__ void k_residual_df(Dims d, Ctl* ctl, Faces32 gh, Faces32 gl, const LayerTab* tab,
                               const float* __restrict__ th_hi, const float* __restrict__ th_lo,
                               const TP* const* ptab, const float* __restrict__ thn_hi,
@@ -232,12 +232,28 @@ __global__ void k_residual_df(Dims d, Ctl* ctl, Faces32 gh, Faces32 gl, const La
       const df g = df_make(__ldg(gH + fi), __ldg(gL + fi));
       return df_mul(g, df_sub(ti, df_make(th_hi[j], th_lo[j])));
     };
-    t[0] = face(c.x + 1 < d.nx, gh.gx, gl.gx, c.i, c.i + 1);
-    t[1] = face(c.x > 0, gh.gx, gl.gx, c.i - 1, c.i - 1);
-    t[2] = face(c.y + 1 < d.ny, gh.gy, gl.gy, c.i, c.i + d.nx);
-    t[3] = face(c.y > 0, gh.gy, gl.gy, c.i - d.nx, c.i - d.nx);
-    t[4] = face(c.z + 1 < d.L, gh.gz, gl.gz, c.i, c.i + d.pxy);
-    t[5] = face(c.z > 0, gh.gz, gl.gz, c.i - d.pxy, c.i - d.pxy);
+    auto uface = [&](bool has, float gH, float gL, long long j) -> df {  // layer-table conductance
+      if (!has) return df_make(0.f, 0.f);
+      return df_mul(df_make(gH, gL), df_sub(ti, df_make(th_hi[j], th_lo[j])));
+    };
+    if (UNI) {
+      const float xh = __ldg(&tab->gxl_hi[c.z]), xl = __ldg(&tab->gxl_lo[c.z]);
+      const float yh = __ldg(&tab->gyl_hi[c.z]), yl = __ldg(&tab->gyl_lo[c.z]);
+      t[0] = uface(c.x + 1 < d.nx, xh, xl, c.i + 1);
+      t[1] = uface(c.x > 0, xh, xl, c.i - 1);
+      t[2] = uface(c.y + 1 < d.ny, yh, yl, c.i + d.nx);
+      t[3] = uface(c.y > 0, yh, yl, c.i - d.nx);
+      t[4] = uface(c.z + 1 < d.L, __ldg(&tab->gzl_hi[c.z]), __ldg(&tab->gzl_lo[c.z]), c.i + d.pxy);
+      t[5] = (c.z > 0) ? uface(true, __ldg(&tab->gzl_hi[c.z - 1]), __ldg(&tab->gzl_lo[c.z - 1]), c.i - d.pxy)
+                       : df_make(0.f, 0.f);
+    } else {
+      t[0] = face(c.x + 1 < d.nx, gh.gx, gl.gx, c.i, c.i + 1);
+      t[1] = face(c.x > 0, gh.gx, gl.gx, c.i - 1, c.i - 1);
+      t[2] = face(c.y + 1 < d.ny, gh.gy, gl.gy, c.i, c.i + d.nx);
+      t[3] = face(c.y > 0, gh.gy, gl.gy, c.i - d.nx, c.i - d.nx);
+      t[4] = face(c.z + 1 < d.L, gh.gz, gl.gz, c.i, c.i + d.pxy);
+      t[5] = face(c.z > 0, gh.gz, gl.gz, c.i - d.pxy, c.i - d.pxy);
+    }
     const df flux = df_add(df_add(df_add(t[0], t[1]), df_add(t[2], t[3])), df_add(t[4], t[5]));
     const df sink = df_make(__ldg(&tab->sink_hi[c.z]), __ldg(&tab->sink_lo[c.z]));
     df b = df_make((float)P[c.i], 0.f);

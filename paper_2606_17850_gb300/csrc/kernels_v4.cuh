@@ -51,7 +51,12 @@ __device__ __forceinline__ Walk4 walk4_of(const Dims& d, int zc) {
 // i..i+3 (float4), V1(j) at one cell.  For each layer z calls
 // epi(i, z, v, acc, dg): v = operand, acc = (A v) and dg = A_ii for the 4 cells,
 // accumulated in the order of stencil_row (s v, +x, -x, +y, -y, +z, -z).
-template <typename TC, typename F4, typename F1, typename E>
+__device__ __forceinline__ float4 f4s(float v) { return make_float4(v, v, v, v); }
+
+// UNI: the grid has one conductivity per layer, so the face conductances come from
+// the per-layer table (gxl, gyl, gzl) and are 0 on the domain boundary: no face
+// arrays are read.  Otherwise they are read from the per-face arrays gx, gy, gz.
+template <typename TC, bool UNI, typename F4, typename F1, typename E>
 __device__ __forceinline__ void zwalk4(const Dims& d, const Walk4& w, const TC* __restrict__ gx,
                                        const TC* __restrict__ gy, const TC* __restrict__ gz, const LayerTab* tab,
                                        F4 V4, F1 V1, E epi) {
@@ -60,18 +65,29 @@ __device__ __forceinline__ void zwalk4(const Dims& d, const Walk4& w, const TC* 
   float4 vb = z4(), gzb = z4();
   if (w.zs > 0) {
     vb = V4(w.b0 + (long long)(w.zs - 1) * pxy);
-    gzb = ldc4(gz + w.b0 + (long long)(w.zs - 1) * pxy);
+    gzb = UNI ? f4s(__ldg(&tab->gzl[w.zs - 1])) : ldc4(gz + w.b0 + (long long)(w.zs - 1) * pxy);
   }
   float4 vc = V4(w.b0 + (long long)w.zs * pxy);
   for (int z = w.zs; z < w.ze; ++z) {
     const long long i = w.b0 + (long long)z * pxy;
     const bool hasA = z + 1 < d.L;
     const float4 va = hasA ? V4(i + pxy) : z4();
-    const float4 gzv = hasA ? ldc4(gz + i) : z4();
-    const float4 gxv = ldc4(gx + i);
-    const float4 gyv = ldc4(gy + i);
-    const float4 gyd = hasD ? ldc4(gy + i - d.nx) : z4();
-    const float gxl = hasL ? ldc(gx + i - 1) : 0.f;
+    float4 gzv, gxv, gyv, gyd;
+    float gxl;
+    if (UNI) {
+      const float cx = __ldg(&tab->gxl[z]), cy = __ldg(&tab->gyl[z]);
+      gzv = f4s(hasA ? __ldg(&tab->gzl[z]) : 0.f);
+      gxv = make_float4(cx, cx, cx, hasR ? cx : 0.f);
+      gyv = f4s(hasU ? cy : 0.f);
+      gyd = f4s(hasD ? cy : 0.f);
+      gxl = hasL ? cx : 0.f;
+    } else {
+      gzv = hasA ? ldc4(gz + i) : z4();
+      gxv = ldc4(gx + i);
+      gyv = ldc4(gy + i);
+      gyd = hasD ? ldc4(gy + i - d.nx) : z4();
+      gxl = hasL ? ldc(gx + i - 1) : 0.f;
+    }
     const float vl = hasL ? V1(i - 1) : 0.f;
     const float vr = hasR ? V1(i + 4) : 0.f;
     const float4 vu = hasU ? V4(i + d.nx) : z4();
@@ -103,7 +119,7 @@ __device__ __forceinline__ void zwalk4(const Dims& d, const Walk4& w, const TC* 
 }
 
 // One Chebyshev step (see k_cheb), vectorised.
-template <typename TC, bool SCALED, bool LAST>
+template <typename TC, bool SCALED, bool LAST, bool UNI>
 __global__ void __launch_bounds__(TH_BX* TH_BY4)
     k_cheb_v4(Dims d, int zc, Ctl* ctl, const TC* __restrict__ gx, const TC* __restrict__ gy,
               const TC* __restrict__ gz, const LayerTab* tab, const float* __restrict__ r,
@@ -113,7 +129,7 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
   const Walk4 w = walk4_of(d, zc);
   float part[1] = {0.f};
   if (w.valid) {
-    zwalk4<TC>(d, w, gx, gy, gz, tab, [&](long long i) { return ld4(zcur + i); },
+    zwalk4<TC, UNI>(d, w, gx, gy, gz, tab, [&](long long i) { return ld4(zcur + i); },
                [&](long long j) { return zcur[j]; },
                [&](long long i, int, const float4& v, const float (&acc)[4], const float (&dg)[4]) {
                  const float4 rv = ld4(r + i);
@@ -138,6 +154,7 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
 }
 
 // Search direction + stencil + p^T A p (see k_spmv_dot), vectorised.
+template <bool UNI>
 __global__ void __launch_bounds__(TH_BX* TH_BY4)
     k_spmv_dot_v4(Dims d, int zc, Ctl* ctl, const float* __restrict__ gx, const float* __restrict__ gy,
                   const float* __restrict__ gz, const LayerTab* tab, const float* __restrict__ z,
@@ -156,7 +173,7 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
       return make_float4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z, a.w + beta * b.w);
     };
     auto P1 = [&](long long j) -> float { return first ? z[j] : z[j] + beta * p_old[j]; };
-    zwalk4<float>(d, w, gx, gy, gz, tab, P4, P1,
+    zwalk4<float, UNI>(d, w, gx, gy, gz, tab, P4, P1,
                   [&](long long i, int, const float4& v, const float (&acc)[4], const float (&)[4]) {
                     st4(p_new + i, v);
                     st4(mu + i, make_float4(acc[0], acc[1], acc[2], acc[3]));
@@ -170,13 +187,13 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
 }
 
 // y = A x, vectorised (FP32).
-template <typename TC>
+template <typename TC, bool UNI>
 __global__ void __launch_bounds__(TH_BX* TH_BY4)
     k_apply_v4(Dims d, int zc, const TC* __restrict__ gx, const TC* __restrict__ gy, const TC* __restrict__ gz,
                const LayerTab* tab, const float* __restrict__ x, float* __restrict__ y) {
   const Walk4 w = walk4_of(d, zc);
   if (!w.valid) return;
-  zwalk4<TC>(d, w, gx, gy, gz, tab, [&](long long i) { return ld4(x + i); }, [&](long long j) { return x[j]; },
+  zwalk4<TC, UNI>(d, w, gx, gy, gz, tab, [&](long long i) { return ld4(x + i); }, [&](long long j) { return x[j]; },
              [&](long long i, int, const float4&, const float (&acc)[4], const float (&)[4]) {
                st4(y + i, make_float4(acc[0], acc[1], acc[2], acc[3]));
              });

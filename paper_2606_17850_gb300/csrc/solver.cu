@@ -5,6 +5,7 @@
 // replays a CUDA graph whose loops are conditional WHILE nodes.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -13,6 +14,19 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "kernels_v4.cuh"
+
+// Runs the statement with the constexpr bool U = cond (template switch for the
+// layer-table coefficient variants).
+#define TH_UNI(cond, ...)             \
+  do {                                \
+    if (cond) {                       \
+      constexpr bool U = true;        \
+      __VA_ARGS__;                    \
+    } else {                          \
+      constexpr bool U = false;       \
+      __VA_ARGS__;                    \
+    }                                 \
+  } while (0)
 
 // ------------------------------------------------------------------ plan
 
@@ -30,6 +44,7 @@ struct Plan {
   int pc_spmv = 0;          // stencil applications per preconditioner application
   // vectorised FP32 kernels (nx % 4 == 0): grid of the z-walk kernels and the update
   bool extrap = false;  // extrapolated initial guess in a step loop
+  bool uni = false;     // layer-table coefficients (grid with one conductivity per layer)
   bool v4 = false;
   int zc = 1;
   dim3 gb4, tb4;
@@ -198,9 +213,9 @@ static th_status tune_zchunk(thermal_grid* g, cudaStream_t s) {
     if (ci > 0 && zc == cands[ci - 1]) continue;
     const dim3 gb = v4_blocks(g, zc);
     auto run = [&]() {
-      k_cheb_v4<float, true, false><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(
-          d, zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->r32, g->zc32[0], g->zc32[1], g->zc32[2],
-          0.5f, 0.5f, g->partials, g->partials_stride, g->counters);
+      TH_UNI(g->uniform, k_cheb_v4<float, true, false, U><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(
+                             d, zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->r32, g->zc32[0],
+                             g->zc32[1], g->zc32[2], 0.5f, 0.5f, g->partials, g->partials_stride, g->counters));
     };
     run();
     TH_CUDA(cudaEventRecord(e0, s));
@@ -225,12 +240,12 @@ th_status solver_apply_f32(thermal_grid* g, bool bf16, const float* x, float* y,
   TH_TRY(grid_ensure_workspace(g, false, s));
   TH_TRY(tune_zchunk(g, s));
   const dim3 gb = v4_blocks(g, g->zc_tuned);
-  if (bf16)
-    k_apply_v4<__nv_bfloat16><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(grid_dims(g), g->zc_tuned, g->f16.gx, g->f16.gy,
-                                                                 g->f16.gz, g->tab, x, y);
+  if (bf16)  // BF16 coefficient storage: always the per-face arrays
+    k_apply_v4<__nv_bfloat16, false><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(grid_dims(g), g->zc_tuned, g->f16.gx,
+                                                                        g->f16.gy, g->f16.gz, g->tab, x, y);
   else
-    k_apply_v4<float><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(grid_dims(g), g->zc_tuned, g->f32.gx, g->f32.gy, g->f32.gz,
-                                                         g->tab, x, y);
+    TH_UNI(g->uniform, k_apply_v4<float, U><<<gb, dim3(TH_BX, TH_BY4), 0, s>>>(
+                           grid_dims(g), g->zc_tuned, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, x, y));
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
@@ -286,6 +301,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
   TH_TRY(grid_ensure_workspace(g, P.prec == TH_PREC_FP64, s));
   if (P.pc == TH_PC_ZLINE) TH_TRY(grid_ensure_zline(g, dt, s));
   P.v4 = (g->nx % 4 == 0);
+  P.uni = g->uniform;
   if (P.v4) {
     TH_TRY(tune_zchunk(g, s));
     P.zc = g->zc_tuned;
@@ -393,11 +409,14 @@ static th_status enq_cheb_tail(const Plan& P, const VecSet<TV>& V, const TC* gx,
     TV* znext = V.zc[m % 3];
     const bool last = (m == P.k - 1);
     const TV c1 = (TV)P.c1[m], c2 = (TV)P.c2[m];
+    constexpr bool tc_f32 = std::is_same<TC, float>::value;  // layer table only replaces FP32 faces
     if constexpr (sizeof(TV) == 4) {
       if (P.v4) {
-#define TH_CHEB4(SC, LA)                                                                                       \
-  k_cheb_v4<TC, SC, LA><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, gx, gy, gz, g->tab, V.r, zprev, zcur, znext, \
-                                                 c1, c2, g->partials, g->partials_stride, g->counters)
+#define TH_CHEB4(SC, LA)                                                                                     \
+  TH_UNI(P.uni && tc_f32,                                                                                    \
+         k_cheb_v4<TC, SC, LA, U><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, gx, gy, gz, g->tab, V.r, zprev, \
+                                                           zcur, znext, c1, c2, g->partials,                  \
+                                                           g->partials_stride, g->counters))
         if (P.scaled) {
           if (last) TH_CHEB4(true, true); else TH_CHEB4(true, false);
         } else {
@@ -453,9 +472,9 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
                                                       V.p[parity], V.p[1 - parity], V.mu, g->partials,
                                                       g->partials_stride, g->counters);
   } else if (P.v4) {
-    k_spmv_dot_v4<<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, zf,
-                                           V.p[parity], V.p[1 - parity], V.mu, g->partials, g->partials_stride,
-                                           g->counters);
+    TH_UNI(P.uni, k_spmv_dot_v4<U><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
+                                                           g->tab, zf, V.p[parity], V.p[1 - parity], V.mu,
+                                                           g->partials, g->partials_stride, g->counters));
   } else {
     k_spmv_dot<float, float><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, zf,
                                                     V.p[parity], V.p[1 - parity], V.mu, g->partials,
@@ -474,13 +493,14 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
     const float* nh = P.transient ? g->thn_hi : nullptr;
     const float* nl = P.transient ? g->thn_lo : nullptr;
     if (P.pdtype == TH_F32)
-      k_residual_df<float><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
-                                                  (const float* const*)g->dev_ptrs, nh, nl, g->r32, count_outer,
-                                                  g->partials, g->partials_stride, g->counters);
+      TH_UNI(P.uni, k_residual_df<float, U><<<P.gb, P.tb, 0, st>>>(
+                        P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo, (const float* const*)g->dev_ptrs,
+                        nh, nl, g->r32, count_outer, g->partials, g->partials_stride, g->counters));
     else
-      k_residual_df<double><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
-                                                   (const double* const*)g->dev_ptrs, nh, nl, g->r32, count_outer,
-                                                   g->partials, g->partials_stride, g->counters);
+      TH_UNI(P.uni, k_residual_df<double, U><<<P.gb, P.tb, 0, st>>>(
+                        P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
+                        (const double* const*)g->dev_ptrs, nh, nl, g->r32, count_outer, g->partials,
+                        g->partials_stride, g->counters));
     TH_CHECK_LAUNCH();
     return TH_OK;
   }
@@ -1079,7 +1099,7 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 8) return th_fail(TH_EINVAL, "invalid argument");
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 12) return th_fail(TH_EINVAL, "invalid argument");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
@@ -1110,19 +1130,21 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   VecSet<double> W = vec64(g);
   const float c1 = 0.5f, c2 = 0.5f;
   auto launch = [&]() -> th_status {
-    switch (kernel) {
+    const bool uni = g->uniform && kernel < 9;  // ids 9..12: the per-face variants
+    const int kk = (kernel >= 9) ? (int[]){1, 3, 8, 0}[kernel - 9] : kernel;
+    switch (kk) {
       case 0:
         if (P.v4)
-          k_apply_v4<float><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->zc32[0],
-                                                    g->zc32[1]);
+          TH_UNI(uni, k_apply_v4<float, U><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->f32.gx, g->f32.gy, g->f32.gz,
+                                                                  g->tab, g->zc32[0], g->zc32[1]));
         else
           k_apply_f32<<<P.gb, P.tb, 0, s>>>(P.d, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, g->zc32[0], g->zc32[1]);
         break;
       case 1:
         if (P.v4) {
-          k_cheb_v4<float, true, false><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
-                                                                g->tab, V.r, V.zc[0], V.zc[1], V.zc[2], c1, c2,
-                                                                g->partials, g->partials_stride, g->counters);
+          TH_UNI(uni, k_cheb_v4<float, true, false, U><<<P.gb4, P.tb4, 0, s>>>(
+                          P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, V.r, V.zc[0], V.zc[1], V.zc[2],
+                          c1, c2, g->partials, g->partials_stride, g->counters));
           break;
         }
         k_cheb<float, float, true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
@@ -1131,7 +1153,7 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
         break;
       case 2:
         if (P.v4) {
-          k_cheb_v4<__nv_bfloat16, true, false><<<P.gb4, P.tb4, 0, s>>>(
+          k_cheb_v4<__nv_bfloat16, true, false, false><<<P.gb4, P.tb4, 0, s>>>(
               P.d, P.zc, g->ctl, g->f16.gx, g->f16.gy, g->f16.gz, g->tab, V.r, V.zc[0], V.zc[1], V.zc[2], c1, c2,
               g->partials, g->partials_stride, g->counters);
           break;
@@ -1142,13 +1164,14 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
         break;
       case 3:
         if (P.v4) {
-          k_spmv_dot_v4<<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab, V.zc[0],
-                                                V.p[0], V.p[1], V.mu, g->partials, g->partials_stride, g->counters);
+          TH_UNI(uni, k_spmv_dot_v4<U><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
+                                                              g->tab, V.zc[0], V.p[0], V.p[1], V.mu, g->partials,
+                                                              g->partials_stride, g->counters));
           break;
         }
         k_spmv_dot<float, float><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
-                                                        V.zc[0], V.p[0], V.p[1], V.mu, g->partials,
-                                                        g->partials_stride, g->counters);
+                                                       V.zc[0], V.p[0], V.p[1], V.mu, g->partials,
+                                                       g->partials_stride, g->counters);
         break;
       case 4:
         if (P.v4) {
@@ -1165,21 +1188,20 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
                                                        P.transient ? g->theta_n : nullptr, g->r32, 2, 0,
                                                        g->partials, g->partials_stride, g->counters);
         break;
-      case 8:
-        k_residual_df<float><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo,
-                                                   (const float* const*)g->dev_ptrs,
-                                                   P.transient ? g->thn_hi : nullptr,
-                                                   P.transient ? g->thn_lo : nullptr, g->r32, 0, g->partials,
-                                                   g->partials_stride, g->counters);
-        break;
       case 6:
         k_apply_f64<<<P.gb, P.tb, 0, s>>>(P.d, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, g->zc64[0], g->zc64[1]);
         break;
-      default:
+      case 7:
         k_cheb<double, double, true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f64.gx, g->f64.gy, g->f64.gz,
                                                                   g->tab, W.r, W.zc[0], W.zc[1], W.zc[2], W.invd,
                                                                   0.5, 0.5, g->partials, g->partials_stride,
                                                                   g->counters);
+        break;
+      default:
+        TH_UNI(uni, k_residual_df<float, U><<<P.gb, P.tb, 0, s>>>(
+                        P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo, (const float* const*)g->dev_ptrs,
+                        P.transient ? g->thn_hi : nullptr, P.transient ? g->thn_lo : nullptr, g->r32, 0,
+                        g->partials, g->partials_stride, g->counters));
         break;
     }
     TH_CHECK_LAUNCH();

@@ -113,6 +113,74 @@ def test_stencil_symmetry_fp64():
     assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
 
 
+def _kmap(st, nx, ny, seed=5):
+    return np.repeat(st.k(), nx * ny) * np.random.default_rng(seed).uniform(0.5, 2.0, nx * ny * st.L)
+
+
+@pytest.mark.parametrize("nx", [36, 37])
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-14), ("mixed", 2e-6)])
+def test_conductivity_map_faces_and_stencil(nx, prec, rtol):
+    """Per-cell conductivities: faces against the oracle's half-cell series and the
+    stencil product through the per-face kernels (scalar and vectorised)."""
+    st = ti.stack_c2()
+    ny, dt = 23, 1e-4
+    kc = _kmap(st, nx, ny)
+    A = disc.assemble(nx, ny, st, dt=dt, k_cell=kc).tocsr()
+    g = grid_of(nx, ny, st)
+    g.set_conductivity_map(torch.from_numpy(kc))
+    f = {k: v.cpu().numpy() for k, v in g.faces(dt).items()}
+    np.testing.assert_allclose(f["diag"], A.diagonal(), rtol=1e-14, atol=0)
+    xd = cuda(ti.random_vector(A.shape[0], 2), torch.float64 if prec == "fp64" else torch.float32)
+    y = g.apply(xd, dt, prec).cpu().double().numpy()
+    x_used = xd.cpu().double().numpy()
+    assert np.all(np.abs(y - A @ x_used) <= rtol * (abs(A) @ np.abs(x_used)))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_conductivity_map_solve(prec):
+    st = ti.stack_c2()
+    nx, ny = 40, 29
+    kc = _kmap(st, nx, ny, 8)
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (3, 4)], np.float64)
+    g = grid_of(nx, ny, st)
+    g.set_conductivity_map(cuda(kc))
+    T, stats = g.solve_steady(cuda(P), precision=prec, cheb_degree=12, tol_rel=1e-10)
+    ref = osolve.steady(nx, ny, st, P, k_cell=kc)
+    assert stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+def test_uniform_map_equals_layer_table():
+    """A map holding the layer values gives the same faces as the per-layer setup, and
+    the per-face kernels then agree with the layer-table kernels."""
+    st = ti.stack_c2()
+    nx, ny, dt = 44, 21, 1e-4
+    P = cuda(ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (5, 6)], np.float32))
+    a, b = grid_of(nx, ny, st), grid_of(nx, ny, st)
+    b.set_conductivity_map(cuda(np.repeat(st.k(), nx * ny)))
+    fa, fb = a.faces(dt), b.faces(dt)
+    for k in ("gx", "gy", "gz", "diag"):
+        assert torch.equal(fa[k], fb[k]), k
+    Ta, _ = a.solve_steady(P, tol_rel=1e-10)
+    Tb, _ = b.solve_steady(P, tol_rel=1e-10)
+    assert (Ta - Tb).abs().max().item() <= 1e-7 * (Ta - st.t_amb).abs().max().item()
+
+
+def test_grad_k_undefined_with_map():
+    from paper_2606_17850_gb300 import ThermalError
+    st = ti.stack_c1()
+    g = grid_of(16, 12, st)
+    g.set_conductivity_map(cuda(_kmap(st, 16, 12)))
+    P = cuda(ti.power_cells(st, 16, 12, [ti.density_uniform_hotspots(16, 12, 1)], np.float64))
+    T, _ = g.solve_steady(P, tol_rel=1e-10)
+    J, w = g.hotspot_lse(T, st.power_layers(), 2.0)
+    with pytest.raises(ThermalError) as e:
+        g.grad(T, w)
+    assert e.value.status == 7
+    dJdP, _, _ = g.grad(T, w, want_k=False, tol_rel=1e-10)
+    assert torch.isfinite(dJdP).all()
+
+
 # ----------------------------------------------------------------- A3/A4: preconditioners
 
 @pytest.mark.parametrize("dt", [0.0, 1e-4])

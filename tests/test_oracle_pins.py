@@ -371,3 +371,41 @@ def test_lse_properties():
     assert 3.0 < J < 3.0 + np.log(3) / 2.0
     assert w[3] == 0.0 and abs(w.sum() - 1.0) < 1e-15
     np.testing.assert_allclose(J, np.log(np.sum(np.exp(2.0 * T[:3]))) / 2.0, rtol=1e-15)
+
+
+def _bruteforce_kmap(nx, ny, stack, kc, x):
+    """Face loop with per-cell conductivities (series half cells), pure Python."""
+    L = stack.L
+    dx, dy = stack.dx, stack.dy
+    dz = [l.thickness for l in stack.layers]
+    y = np.zeros(nx * ny * L)
+    at = lambda i, j, z: i + nx * (j + ny * z)
+    for z in range(L):
+        for j in range(ny):
+            for i in range(nx):
+                a = at(i, j, z)
+                for (b, S, la, lb) in ((at(i + 1, j, z) if i + 1 < nx else None, dy * dz[z], dx, dx),
+                                       (at(i, j + 1, z) if j + 1 < ny else None, dx * dz[z], dy, dy),
+                                       (at(i, j, z + 1) if z + 1 < L else None, dx * dy, dz[z], dz[z + 1] if z + 1 < L else 0)):
+                    if b is None:
+                        continue
+                    g = S / (la / (2 * kc[a]) + lb / (2 * kc[b]))
+                    y[a] += g * (x[a] - x[b]); y[b] += g * (x[b] - x[a])
+                if z == L - 1:
+                    y[a] += stack.h * dx * dy * x[a]
+    return y
+
+
+def test_kmap_assembly_bruteforce_and_uniform_limit():
+    """Per-cell conductivities: face loop brute force; a map equal to the layer values
+    reproduces the layer-wise assembly."""
+    st = ti.stack_c2()
+    nx, ny = 4, 3
+    n = nx * ny * st.L
+    kc = np.repeat(st.k(), nx * ny) * np.random.default_rng(3).uniform(0.5, 2.0, n)
+    A = disc.assemble(nx, ny, st, k_cell=kc)
+    x = ti.random_vector(n, 4)
+    np.testing.assert_allclose(A @ x, _bruteforce_kmap(nx, ny, st, kc, x), rtol=1e-12, atol=1e-18)
+    assert abs(A - A.T).max() == 0.0
+    Au = disc.assemble(nx, ny, st, k_cell=np.repeat(st.k(), nx * ny))
+    np.testing.assert_allclose((Au - disc.assemble(nx, ny, st)).toarray(), 0.0, atol=1e-15 * abs(Au).max())
