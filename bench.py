@@ -42,6 +42,7 @@ KERNEL_BYTES = {
     # the workload's grid has one conductivity per layer: the solver's FP32 and
     # double-float kernels take the face conductances from a per-layer table
     "cheb_f32": 16,      # z_m, z_{m-1}, r (12) + z_{m+1} (4)
+    "cheb_tb4": 20,      # four fused steps: z_m, z_{m-1}, r read once (12) + z_{m+4}, z_{m+3} (8)
     "spmv_dot_f32": 16,  # z, p_old (8) + p_new, mu (8)
     "update_f32": 32,    # x, r (read+write 16) + p, mu, 1/diag (12) + z (4)
     "stencil_f32": 8,    # x (4) + y (4)
@@ -57,7 +58,7 @@ KERNEL_BYTES = {
     "stencil_f64": 40,   # gx gy gz (24) + x (8) + y (8)
     "cheb_f64": 64,      # gx gy gz (24) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)
 }
-DOMINANT = "cheb_f32"
+DOMINANT = "cheb_tb4"
 
 
 def parse():

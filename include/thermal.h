@@ -91,7 +91,9 @@ typedef struct thermal_solve_opts {
                        /* instance after another through the single-grid solver (0)          */
   int guess;           /* transient initial guess: 0 the previous step T_n (the paper's warm  */
                        /* start), 1 linear extrapolation 2 T_n - T_{n-1} inside a step loop (0) */
-  int reserved[6];
+  int cheb_fuse;       /* Chebyshev steps per launch on layer-uniform grids (temporal blocking */
+                       /* in shared memory): 0 auto (4), 1 one step per launch, 2..4 (0)      */
+  int reserved[5];
 } thermal_solve_opts;
 
 typedef struct thermal_solve_stats {
@@ -223,6 +225,7 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  *   7  FP64 Chebyshev step (plain FP64 path)
  *   8  double-float refinement residual (the mixed path's r = b - A theta) (*)
  *   9, 10, 11, 12  kernels 1, 3, 8, 0 reading the per-face arrays
+ *  13  four Chebyshev steps fused in one launch (temporal blocking, layer-uniform grids)
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

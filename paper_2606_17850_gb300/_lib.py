@@ -35,7 +35,8 @@ class SolveOpts(C.Structure):
         ("use_graph", C.c_int),
         ("batched_mode", C.c_int),
         ("guess", C.c_int),
-        ("reserved", C.c_int * 6),
+        ("cheb_fuse", C.c_int),
+        ("reserved", C.c_int * 5),
     ]
 
 

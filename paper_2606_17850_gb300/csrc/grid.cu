@@ -75,6 +75,7 @@ th_status validate_opts(const thermal_solve_opts* o) {
     return th_fail(TH_EINVAL, "cheb_degree must lie in [1, 1000]");
   if (o->precond == TH_PC_CHEB && (o->lanczos_steps < 2 || o->lanczos_steps > 1000))
     return th_fail(TH_EINVAL, "lanczos_steps must lie in [2, 1000]");
+  if (o->cheb_fuse < 0 || o->cheb_fuse > 4) return th_fail(TH_EINVAL, "cheb_fuse must lie in [0, 4]");
   return TH_OK;
 }
 

@@ -14,6 +14,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "kernels_v4.cuh"
+#include "kernels_tb.cuh"
 
 // Runs the statement with the constexpr bool U = cond (template switch for the
 // layer-table coefficient variants).
@@ -45,6 +46,13 @@ struct Plan {
   // vectorised FP32 kernels (nx % 4 == 0): grid of the z-walk kernels and the update
   bool extrap = false;  // extrapolated initial guess in a step loop
   bool uni = false;     // layer-table coefficients (grid with one conductivity per layer)
+  // temporal blocking of the FP32 Chebyshev tail: chunks of fused steps over a
+  // pool of four FP32 buffers {zc0, zc1, zc2, mu} (indices 0..3)
+  struct Chunk { int steps, m0, in_cur, in_prev, out_cur, out_prev; };
+  bool fused = false;  // temporal blocking active
+  int tb_ty = 16;
+  std::vector<Chunk> chunks;
+  int zfin = -1;  // pool index of the preconditioned vector (-1: the per-step rule)
   bool v4 = false;
   int zc = 1;
   dim3 gb4, tb4;
@@ -281,6 +289,10 @@ th_status solver_cheb_coeffs(thermal_grid* g, double dt, const thermal_solve_opt
   return TH_OK;
 }
 
+struct Plan;
+static size_t tb_smem(const Plan& P);
+static th_status tb_attributes(size_t sm);
+
 // ------------------------------------------------------------------ plan setup
 
 static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts* o, int pdtype, bool transient,
@@ -315,6 +327,35 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     TH_TRY(solver_spectral(g, dt, o, &ra, &rb, &P.lmin, &P.lmax, s));
     cheb_coeffs(P.lmin, P.lmax, P.k, P.c1, P.c2, &P.inv_theta);
     P.pc_spmv = P.k - 1;
+    const int fuse = o->cheb_fuse == 0 ? TB_H : o->cheb_fuse;
+    if (P.prec != TH_PREC_FP64 && P.v4 && P.uni && fuse > 1 && P.k > 1) {
+      // shared memory: 3 arrays x L x (TY + 2H) x TB_EX floats; two blocks per SM if possible
+      const size_t per_ty16 = (size_t)3 * g->L * (16 + 2 * TB_H) * TB_EX * 4;
+      const size_t per_ty8 = (size_t)3 * g->L * (8 + 2 * TB_H) * TB_EX * 4;
+      if (per_ty16 <= 110 * 1024) P.tb_ty = 16;
+      else if (per_ty8 <= 110 * 1024) P.tb_ty = 8;
+      else P.tb_ty = 0;
+      if (P.tb_ty > 0) {
+        P.fused = true;
+        int cur = 0, prev = -1, m = 1, left = P.k - 1;
+        while (left > 0) {
+          const int st = std::min(fuse, left);
+          int oc = -1, op = -1;
+          for (int b = 0; b < 4 && (oc < 0 || op < 0); ++b) {
+            if (b == cur || b == prev) continue;
+            if (oc < 0) oc = b; else op = b;
+          }
+          const bool last = (left == st);
+          P.chunks.push_back(Plan::Chunk{st, m, cur, prev, oc, last ? -1 : op});
+          prev = last ? -1 : op;
+          cur = oc;
+          m += st;
+          left -= st;
+        }
+        P.zfin = cur;
+        TH_TRY(tb_attributes(tb_smem(P)));
+      }
+    }
   }
   return TH_OK;
 }
@@ -348,6 +389,9 @@ static VecSet<double> vec64(thermal_grid* g) {
 }
 
 template <typename TV> static TV* z_final(const Plan& P, const VecSet<TV>& V) {
+  if constexpr (sizeof(TV) == 4) {
+    if (P.fused) return P.zfin == 3 ? V.mu : V.zc[P.zfin];
+  }
   switch (P.pc) {
     case TH_PC_NONE: return V.r;
     case TH_PC_CHEB: return V.zc[(P.k - 1) % 3];
@@ -399,10 +443,68 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
   return TH_OK;
 }
 
+static size_t tb_smem(const Plan& P) { return (size_t)3 * P.d.L * (P.tb_ty + 2 * TB_H) * TB_EX * sizeof(float); }
+
+template <int TY, bool SC, bool LA>
+static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
+  thermal_grid* g = P.g;
+  float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
+  TBCoef cf;
+  for (int j = 0; j < TB_H; ++j) {
+    cf.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
+    cf.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+  }
+  const size_t sm = tb_smem(P);
+  const dim3 grid((P.d.nx + TB_TX - 1) / TB_TX, (P.d.ny + TY - 1) / TY);
+  k_cheb_tb<TY, SC, LA><<<grid, TB_THREADS, sm, st>>>(P.d, c.steps, g->ctl, g->tab, V.r,
+                                                      c.in_prev >= 0 ? pool[c.in_prev] : nullptr, pool[c.in_cur],
+                                                      pool[c.out_cur], c.out_prev >= 0 ? pool[c.out_prev] : nullptr,
+                                                      cf, g->partials, g->partials_stride, g->counters);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st) {
+  for (size_t ci = 0; ci < P.chunks.size(); ++ci) {
+    const bool last = (ci + 1 == P.chunks.size());
+    const Plan::Chunk& c = P.chunks[ci];
+#define TH_TBL(TY)                                                       \
+  if (P.scaled) {                                                        \
+    if (last) TH_TRY((tb_launch<TY, true, true>(P, V, st, c)));          \
+    else TH_TRY((tb_launch<TY, true, false>(P, V, st, c)));              \
+  } else {                                                               \
+    if (last) TH_TRY((tb_launch<TY, false, true>(P, V, st, c)));         \
+    else TH_TRY((tb_launch<TY, false, false>(P, V, st, c)));             \
+  }
+    if (P.tb_ty == 16) {
+      TH_TBL(16)
+    } else {
+      TH_TBL(8)
+    }
+#undef TH_TBL
+  }
+  return TH_OK;
+}
+
+// the fused kernels need more than 48 KB of dynamic shared memory
+static th_status tb_attributes(size_t sm) {
+  static size_t done = 0;
+  if (sm <= done) return TH_OK;
+#define TH_TBA(TY, SC, LA) TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<TY, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))
+  TH_TBA(16, true, true); TH_TBA(16, true, false); TH_TBA(16, false, true); TH_TBA(16, false, false);
+  TH_TBA(8, true, true); TH_TBA(8, true, false); TH_TBA(8, false, true); TH_TBA(8, false, false);
+#undef TH_TBA
+  done = sm;
+  return TH_OK;
+}
+
 template <typename TV, typename TC>
 static th_status enq_cheb_tail(const Plan& P, const VecSet<TV>& V, const TC* gx, const TC* gy, const TC* gz,
                                cudaStream_t st) {
   thermal_grid* g = P.g;
+  if constexpr (sizeof(TV) == 4) {
+    if (P.fused) return tb_chain(P, V, st);
+  }
   for (int m = 1; m < P.k; ++m) {
     const TV* zprev = (m >= 2) ? V.zc[(m - 2) % 3] : nullptr;
     const TV* zcur = V.zc[(m - 1) % 3];
@@ -1099,12 +1201,15 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 12) return th_fail(TH_EINVAL, "invalid argument");
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 13) return th_fail(TH_EINVAL, "invalid argument");
+  if (kernel == 13 && !(g->uniform && g->nx % 4 == 0))
+    return th_fail(TH_EINVAL, "fused Chebyshev steps need a layer-uniform grid with nx %% 4 == 0");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
-  o.precond = TH_PC_JACOBI;
-  o.precision = (kernel >= 5) ? TH_PREC_FP64 : TH_PREC_MIXED_IR;
+  o.precond = (kernel == 13) ? TH_PC_CHEB : TH_PC_JACOBI;
+  o.cheb_degree = 5;  // one chunk of four fused steps
+  o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64 : TH_PREC_MIXED_IR;
   Plan P;
   TH_TRY(make_plan(g, dt, &o, TH_F32, dt > 0.0, P, s));
   TH_TRY(ensure_stage(g, sizeof(float) * (size_t)g->n));
@@ -1131,6 +1236,7 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   const float c1 = 0.5f, c2 = 0.5f;
   auto launch = [&]() -> th_status {
     const bool uni = g->uniform && kernel < 9;  // ids 9..12: the per-face variants
+    if (kernel == 13) return tb_chain(P, V, s);
     const int kk = (kernel >= 9) ? (int[]){1, 3, 8, 0}[kernel - 9] : kernel;
     switch (kk) {
       case 0:

@@ -226,6 +226,23 @@ def test_preconditioner_apply(pc, scaled, nx):
     np.testing.assert_allclose(z, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("k", [2, 5, 8, 12])
+@pytest.mark.parametrize("dt", [0.0, 1e-4])
+def test_fused_chebyshev_equals_stepwise(k, dt):
+    """Temporal blocking (up to 4 steps per launch in shared memory) computes the same
+    polynomial as one launch per step: tiles with ragged x/y tails, 1..3 chunks."""
+    st = ti.stack_c2()
+    nx, ny = 76, 37           # nx % 32 != 0 and ny % 16 != 0: partial tiles on both axes
+    g = grid_of(nx, ny, st)
+    r = cuda(ti.random_vector(nx * ny * st.L, 5).astype(np.float32))
+    z1 = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=1)
+    zf = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=0)
+    z3 = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=3)
+    scale = z1.abs().max().item()
+    assert (zf - z1).abs().max().item() <= 1e-6 * scale
+    assert (z3 - z1).abs().max().item() <= 1e-6 * scale
+
+
 # ----------------------------------------------------------------- A5/A6: steady solves
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
