@@ -78,6 +78,7 @@ struct Ctl {
   int steps_per_map;
   int n_maps;
   int steps_done;
+  int map_idx;      // power map of the current step: (step / steps_per_map) % n_maps
   int n_inits;      // inner solves started
   long long lanczos_spmv;
   // scalars precomputed once by the last block of the kernel that produces them,

@@ -48,6 +48,7 @@ __global__ void k_step_end(Ctl* c) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   c->step += 1;
   c->steps_done += 1;
+  c->map_idx = (c->step / c->steps_per_map) % c->n_maps;
 }
 
 // which: 0 inner loop (!done), 1 outer loop (!outer_done), 2 step loop (step < n_steps,
@@ -112,10 +113,7 @@ __global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, con
                            unsigned* counter) {
   if (mode != 2 && ld_int(&ctl->outer_done)) return;
   const Cell c = cell_of(d);
-  if (ptab) {
-    const int st = ld_int(&ctl->step), spm = ctl->steps_per_map, nm = ctl->n_maps;
-    P = ptab[(st / spm) % nm];
-  }
+  if (ptab) P = ptab[ld_int(&ctl->map_idx)];
   float v[2] = {0.f, 0.f};
   if (c.valid) {
     const double ti = theta[c.i];
@@ -216,11 +214,7 @@ __global__ void k_residual_df(Dims d, Ctl* ctl, Faces32 gh, Faces32 gl, const La
                               double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->outer_done)) return;
   const Cell c = cell_of(d);
-  const TP* P;
-  {
-    const int st = ld_int(&ctl->step), spm = ctl->steps_per_map, nm = ctl->n_maps;
-    P = ptab[(st / spm) % nm];
-  }
+  const TP* P = ptab[ld_int(&ctl->map_idx)];
   float v[2] = {0.f, 0.f};
   if (c.valid) {
     const df ti = df_make(th_hi[c.i], th_lo[c.i]);

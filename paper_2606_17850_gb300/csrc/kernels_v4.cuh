@@ -13,6 +13,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 #define TH_BY4 8
 
@@ -247,4 +248,96 @@ __global__ void __launch_bounds__(256)
   double tot[2];
   if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
   fin_update(ctl, tot[0], tot[1], INIT, rz_here);
+}
+
+// power map values of 4 consecutive cells as double-floats
+__device__ __forceinline__ void ldp4(const float* p, df (&o)[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = df_make(v.x, 0.f); o[1] = df_make(v.y, 0.f); o[2] = df_make(v.z, 0.f); o[3] = df_make(v.w, 0.f);
+}
+__device__ __forceinline__ void ldp4(const double* p, df (&o)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double v = __ldg(p + k);
+    const float h = (float)v;
+    o[k] = df_make(h, (float)(v - (double)h));
+  }
+}
+
+// The double-float refinement residual (see k_residual_df) on a layer-uniform
+// grid, vectorised: per cell r = P + cdt (theta_n - theta) - sink theta - flux with
+// flux = gx (2 theta - theta_r - theta_l) + gy (2 theta - theta_u - theta_d)
+//      + gza (theta - theta_above) + gzb (theta - theta_below),
+// an absent neighbour taking the cell's own value (its difference is exactly 0).
+template <typename TP>
+__global__ void __launch_bounds__(TH_BX* TH_BY4)
+    k_residual_df_v4(Dims d, int zc, Ctl* ctl, const LayerTab* tab, const float* __restrict__ th_hi,
+                     const float* __restrict__ th_lo, const TP* const* ptab, const float* __restrict__ thn_hi,
+                     const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer, double* partials,
+                     int stride, unsigned* counter) {
+  if (ld_int(&ctl->outer_done)) return;
+  const Walk4 w = walk4_of(d, zc);
+  const TP* P = ptab[ld_int(&ctl->map_idx)];
+  float v[2] = {0.f, 0.f};
+  if (w.valid) {
+    const long long pxy = d.pxy;
+    const bool hasL = w.x0 > 0, hasR = w.x0 + 4 < d.nx, hasD = w.y > 0, hasU = w.y + 1 < d.ny;
+    float4 hb = z4(), lb = z4();
+    if (w.zs > 0) {
+      hb = ld4(th_hi + w.b0 + (long long)(w.zs - 1) * pxy);
+      lb = ld4(th_lo + w.b0 + (long long)(w.zs - 1) * pxy);
+    }
+    float4 hc = ld4(th_hi + w.b0 + (long long)w.zs * pxy), lc = ld4(th_lo + w.b0 + (long long)w.zs * pxy);
+    for (int z = w.zs; z < w.ze; ++z) {
+      const long long i = w.b0 + (long long)z * pxy;
+      const bool hasA = z + 1 < d.L, hasB = z > 0;
+      const float4 ha = hasA ? ld4(th_hi + i + pxy) : hc, la = hasA ? ld4(th_lo + i + pxy) : lc;
+      const float4 hu = hasU ? ld4(th_hi + i + d.nx) : hc, lu = hasU ? ld4(th_lo + i + d.nx) : lc;
+      const float4 hd = hasD ? ld4(th_hi + i - d.nx) : hc, ld_ = hasD ? ld4(th_lo + i - d.nx) : lc;
+      const float hl1 = hasL ? th_hi[i - 1] : hc.x, ll1 = hasL ? th_lo[i - 1] : lc.x;
+      const float hr1 = hasR ? th_hi[i + 4] : hc.w, lr1 = hasR ? th_lo[i + 4] : lc.w;
+      const float4 hbz = hasB ? hb : hc, lbz = hasB ? lb : lc;
+      df pv[4];
+      ldp4(P + i, pv);
+      float4 nh = z4(), nl = z4();
+      if (thn_hi) {
+        nh = ld4(thn_hi + i);
+        nl = ld4(thn_lo + i);
+      }
+      const df gx = df_make(__ldg(&tab->gxl_hi[z]), __ldg(&tab->gxl_lo[z]));
+      const df gy = df_make(__ldg(&tab->gyl_hi[z]), __ldg(&tab->gyl_lo[z]));
+      const df ga = df_make(__ldg(&tab->gzl_hi[z]), __ldg(&tab->gzl_lo[z]));
+      const df gb = hasB ? df_make(__ldg(&tab->gzl_hi[z - 1]), __ldg(&tab->gzl_lo[z - 1])) : df_make(0.f, 0.f);
+      const df sk = df_make(__ldg(&tab->sink_hi[z]), __ldg(&tab->sink_lo[z]));
+      const df cd = df_make(__ldg(&tab->cdt_hi[z]), __ldg(&tab->cdt_lo[z]));
+      float o[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const df t = df_make(cmp(hc, k), cmp(lc, k));
+        const df tr = (k == 3) ? df_make(hr1, lr1) : df_make(cmp(hc, k + 1), cmp(lc, k + 1));
+        const df tl = (k == 0) ? df_make(hl1, ll1) : df_make(cmp(hc, k - 1), cmp(lc, k - 1));
+        const df dx = df_add(df_sub(t, tr), df_sub(t, tl));
+        const df dy = df_add(df_sub(t, df_make(cmp(hu, k), cmp(lu, k))), df_sub(t, df_make(cmp(hd, k), cmp(ld_, k))));
+        const df fa = df_mul(ga, df_sub(t, df_make(cmp(ha, k), cmp(la, k))));
+        const df fb = df_mul(gb, df_sub(t, df_make(cmp(hbz, k), cmp(lbz, k))));
+        const df flux = df_add(df_add(df_mul(gx, dx), df_mul(gy, dy)), df_add(fa, fb));
+        df b = pv[k];
+        df rr = df_sub(df_sub(b, df_mul(sk, t)), flux);
+        if (thn_hi) {
+          const df tn = df_make(cmp(nh, k), cmp(nl, k));
+          rr = df_add(rr, df_mul(cd, df_sub(tn, t)));
+          b = df_add(b, df_mul(cd, tn));
+        }
+        o[k] = rr.hi + rr.lo;
+        v[0] += o[k] * o[k];
+        v[1] += b.hi * b.hi;
+      }
+      st4(r + i, make_float4(o[0], o[1], o[2], o[3]));
+      hb = hc; lb = lc;
+      hc = ha; lc = la;
+    }
+  }
+  double tot[2];
+  if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
+  fin_residual(ctl, tot[0], tot[1], 0, count_outer);
 }

@@ -289,9 +289,6 @@ th_status solver_cheb_coeffs(thermal_grid* g, double dt, const thermal_solve_opt
   return TH_OK;
 }
 
-struct Plan;
-static size_t tb_smem(const Plan& P);
-static th_status tb_attributes(size_t sm);
 
 // ------------------------------------------------------------------ plan setup
 
@@ -329,12 +326,8 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     P.pc_spmv = P.k - 1;
     const int fuse = o->cheb_fuse == 0 ? TB_H : o->cheb_fuse;
     if (P.prec != TH_PREC_FP64 && P.v4 && P.uni && fuse > 1 && P.k > 1) {
-      // shared memory: 3 arrays x L x (TY + 2H) x TB_EX floats; two blocks per SM if possible
-      const size_t per_ty16 = (size_t)3 * g->L * (16 + 2 * TB_H) * TB_EX * 4;
-      const size_t per_ty8 = (size_t)3 * g->L * (8 + 2 * TB_H) * TB_EX * 4;
-      if (per_ty16 <= 110 * 1024) P.tb_ty = 16;
-      else if (per_ty8 <= 110 * 1024) P.tb_ty = 8;
-      else P.tb_ty = 0;
+      // register columns: up to 8 layers with 40 x 24 threads, up to 12 with 40 x 16
+      P.tb_ty = g->L <= 8 ? 16 : (g->L <= 12 ? 8 : 0);
       if (P.tb_ty > 0) {
         P.fused = true;
         int cur = 0, prev = -1, m = 1, left = P.k - 1;
@@ -353,7 +346,6 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
           left -= st;
         }
         P.zfin = cur;
-        TH_TRY(tb_attributes(tb_smem(P)));
       }
     }
   }
@@ -443,9 +435,7 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
   return TH_OK;
 }
 
-static size_t tb_smem(const Plan& P) { return (size_t)3 * P.d.L * (P.tb_ty + 2 * TB_H) * TB_EX * sizeof(float); }
-
-template <int TY, bool SC, bool LA>
+template <int LM, int TY, bool SC, bool LA>
 static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   thermal_grid* g = P.g;
   float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
@@ -454,12 +444,10 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
     cf.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
     cf.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
   }
-  const size_t sm = tb_smem(P);
   const dim3 grid((P.d.nx + TB_TX - 1) / TB_TX, (P.d.ny + TY - 1) / TY);
-  k_cheb_tb<TY, SC, LA><<<grid, TB_THREADS, sm, st>>>(P.d, c.steps, g->ctl, g->tab, V.r,
-                                                      c.in_prev >= 0 ? pool[c.in_prev] : nullptr, pool[c.in_cur],
-                                                      pool[c.out_cur], c.out_prev >= 0 ? pool[c.out_prev] : nullptr,
-                                                      cf, g->partials, g->partials_stride, g->counters);
+  k_cheb_tb<LM, TY, SC, LA><<<grid, dim3(TB_EX, TY + 2 * TB_H), 0, st>>>(
+      P.d, c.steps, g->ctl, g->tab, V.r, c.in_prev >= 0 ? pool[c.in_prev] : nullptr, pool[c.in_cur], pool[c.out_cur],
+      c.out_prev >= 0 ? pool[c.out_prev] : nullptr, cf, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
@@ -468,33 +456,21 @@ static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st
   for (size_t ci = 0; ci < P.chunks.size(); ++ci) {
     const bool last = (ci + 1 == P.chunks.size());
     const Plan::Chunk& c = P.chunks[ci];
-#define TH_TBL(TY)                                                       \
-  if (P.scaled) {                                                        \
-    if (last) TH_TRY((tb_launch<TY, true, true>(P, V, st, c)));          \
-    else TH_TRY((tb_launch<TY, true, false>(P, V, st, c)));              \
-  } else {                                                               \
-    if (last) TH_TRY((tb_launch<TY, false, true>(P, V, st, c)));         \
-    else TH_TRY((tb_launch<TY, false, false>(P, V, st, c)));             \
+#define TH_TBL(LM, TY)                                                       \
+  if (P.scaled) {                                                            \
+    if (last) TH_TRY((tb_launch<LM, TY, true, true>(P, V, st, c)));          \
+    else TH_TRY((tb_launch<LM, TY, true, false>(P, V, st, c)));              \
+  } else {                                                                   \
+    if (last) TH_TRY((tb_launch<LM, TY, false, true>(P, V, st, c)));         \
+    else TH_TRY((tb_launch<LM, TY, false, false>(P, V, st, c)));             \
   }
     if (P.tb_ty == 16) {
-      TH_TBL(16)
+      TH_TBL(8, 16)
     } else {
-      TH_TBL(8)
+      TH_TBL(12, 8)
     }
 #undef TH_TBL
   }
-  return TH_OK;
-}
-
-// the fused kernels need more than 48 KB of dynamic shared memory
-static th_status tb_attributes(size_t sm) {
-  static size_t done = 0;
-  if (sm <= done) return TH_OK;
-#define TH_TBA(TY, SC, LA) TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<TY, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))
-  TH_TBA(16, true, true); TH_TBA(16, true, false); TH_TBA(16, false, true); TH_TBA(16, false, false);
-  TH_TBA(8, true, true); TH_TBA(8, true, false); TH_TBA(8, false, true); TH_TBA(8, false, false);
-#undef TH_TBA
-  done = sm;
   return TH_OK;
 }
 
@@ -594,6 +570,18 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
   if (!out64 && mode == 0) {  // mixed path: double-float residual
     const float* nh = P.transient ? g->thn_hi : nullptr;
     const float* nl = P.transient ? g->thn_lo : nullptr;
+    if (P.uni && P.v4) {
+      if (P.pdtype == TH_F32)
+        k_residual_df_v4<float><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
+                                                         (const float* const*)g->dev_ptrs, nh, nl, g->r32,
+                                                         count_outer, g->partials, g->partials_stride, g->counters);
+      else
+        k_residual_df_v4<double><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
+                                                          (const double* const*)g->dev_ptrs, nh, nl, g->r32,
+                                                          count_outer, g->partials, g->partials_stride, g->counters);
+      TH_CHECK_LAUNCH();
+      return TH_OK;
+    }
     if (P.pdtype == TH_F32)
       TH_UNI(P.uni, k_residual_df<float, U><<<P.gb, P.tb, 0, st>>>(
                         P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo, (const float* const*)g->dev_ptrs,
@@ -1304,6 +1292,14 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
                                                                   g->counters);
         break;
       default:
+        if (uni && P.v4) {
+          k_residual_df_v4<float><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
+                                                          (const float* const*)g->dev_ptrs,
+                                                          P.transient ? g->thn_hi : nullptr,
+                                                          P.transient ? g->thn_lo : nullptr, g->r32, 0, g->partials,
+                                                          g->partials_stride, g->counters);
+          break;
+        }
         TH_UNI(uni, k_residual_df<float, U><<<P.gb, P.tb, 0, s>>>(
                         P.d, g->ctl, g->f32, g->f32lo, g->tab, g->th_hi, g->th_lo, (const float* const*)g->dev_ptrs,
                         P.transient ? g->thn_hi : nullptr, P.transient ? g->thn_lo : nullptr, g->r32, 0,
