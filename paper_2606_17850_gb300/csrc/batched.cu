@@ -10,9 +10,10 @@
 // instance that has converged drops out of every later phase (its tiles are
 // skipped); the loops end when no instance is active.
 //
-// Within one persistent kernel L1 is not invalidated at a grid barrier, so every
-// load of a vector written during the kernel uses the L2 path (__ldcg); face
-// conductances and tables are immutable and use the read-only path.
+// Vectors written during the kernel are read with ordinary (coherent) loads: the
+// grid-wide barrier makes every write before it visible to every thread after it.
+// Only immutable data (face conductances, tables) uses the non-coherent read-only
+// path (__ldg); control fields are read through L2 (__ldcg).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -52,8 +53,9 @@ struct BArgs {
   int max_sweeps;    // safety cap on inner sweeps of the whole batch
 };
 
-__device__ __forceinline__ float lcg(const float* p) { return __ldcg(p); }
-__device__ __forceinline__ double lcg(const double* p) { return __ldcg(p); }
+// loads of vectors written earlier in the same kernel (ordinary, coherent loads)
+__device__ __forceinline__ float lcg(const float* p) { return *p; }
+__device__ __forceinline__ double lcg(const double* p) { return *p; }
 
 __device__ __forceinline__ Cell tile_cell(const BInst& I, int t) {
   const int loc = t - I.tile0;

@@ -1,121 +1,212 @@
 // Temporal blocking of the Chebyshev preconditioner (layer-uniform grids).
 //
 // The preconditioner's steps need no reductions (Sec. 4.3: only SpMVs and AXPYs),
-// so several of them can run inside one kernel on a tile.  A block owns a
-// TB_TX x TY column tile (all layers) grown by a TB_H-cell halo in x and y; each
-// thread owns one column of the grown tile and keeps that column's z_m, z_{m-1}
-// and r in registers.  For every step the threads publish z_m into a shared-memory
-// copy of the tile, read their four in-plane neighbours from it (the z neighbours
-// are in their own registers) and form z_{m+1}.  The region whose neighbours are
-// still valid shrinks by one cell per step, so after S <= TB_H steps the interior
-// holds z_{m+S}.  Face conductances come from the per-layer table (the grid has
-// one conductivity per layer).  DRAM traffic per S steps is the three inputs once
-// plus one or two outputs (~20 B/cell) instead of 16 B/cell per step.
+// so several of them can run inside one kernel on a tile.  A tile is TB_TX x TY
+// columns (all layers) grown by a TB_H-cell halo in x and y.  Each thread owns one
+// column of the grown tile and keeps that column's z_m, z_{m-1} and r in registers;
+// per step it publishes z_m into a shared-memory plane, reads its four in-plane
+// neighbours from there (the z neighbours are its own registers) and forms z_{m+1}.
+// The region whose neighbours are still valid shrinks by one cell per step, so
+// after S <= TB_H steps the tile interior holds z_{m+S}.
 //
-// Launch: block (TB_EX, TY + 2 TB_H), grid (ceil(nx/TB_TX), ceil(ny/TY)); needs
-// nx % 4 == 0 is not required (columns are loaded one float at a time).
+// Blackwell data movement: the kernel is persistent (one CTA per SM walks the tile
+// list) and the next tile's three input boxes (z_m, z_{m-1}, r: TB_EX x EY x L
+// floats each) are fetched by the tensor memory accelerator into a staging buffer
+// while the current tile computes; completion is tracked by an mbarrier.  Two plane
+// buffers alternate between steps, so a step needs a single CTA barrier.
+//
+// Per-layer constants (face conductances of the layer table, sink, the inverse
+// diagonal for every in-plane boundary case) and the step coefficients are kernel
+// parameters, so the stencil's multiplications take them straight from the
+// constant bank.  Missing neighbours (domain edges) are read as the cell itself,
+// which makes their difference term exactly zero, as the adiabatic boundary
+// requires; the accumulation order equals the one-step kernels' (s v, +x, -x, +y,
+// -y, +z, -z).
+//
+// DRAM traffic per S steps: the three inputs once plus one or two outputs
+// (about 20 B/cell) instead of 16 B/cell per step.
 #pragma once
+
+#include <cuda.h>
 
 #include "common.cuh"
 
 #define TB_H 4
 #define TB_TX 32
 #define TB_EX (TB_TX + 2 * TB_H)
+// bounded mbarrier wait: try_wait suspends for a hardware time slice per attempt,
+// so this limit is on the order of a second
+#define TB_WAIT_LIMIT (1 << 20)
 
-struct TBCoef {
-  float c1[TB_H], c2[TB_H];
+template <int LMAX>
+struct TBParams {
+  float c1[TB_H], c2[TB_H];     // Chebyshev step coefficients of this chunk
+  float s[LMAX];                // sink (+ capacity) per layer
+  float gx[LMAX], gy[LMAX];     // in-plane face conductances per layer
+  float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
+  float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
 };
 
+__device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tb_mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tb_smem(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void tb_mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tb_smem(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool tb_mbar_try(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(tb_smem(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool tb_mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < TB_WAIT_LIMIT; ++it)
+    if (tb_mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tb_tma_3d(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(tb_smem(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(tb_smem(bar))
+      : "memory");
+}
+
+// dynamic shared memory of one CTA: staging (3 boxes) + two planes + mbarrier,
+// plus room to align the staging boxes to 128 bytes
+template <int LMAX, int TY>
+constexpr size_t tb_smem_bytes() {
+  return (size_t)(3 + 2) * LMAX * (TY + 2 * TB_H) * TB_EX * sizeof(float) + 16 + 128;
+}
+
 template <int LMAX, int TY, bool SCALED, bool LAST>
-__global__ void __launch_bounds__(TB_EX*(TY + 2 * TB_H))
-    k_cheb_tb(Dims d, int steps, Ctl* ctl, const LayerTab* tab, const float* __restrict__ r,
-              const float* __restrict__ zprev, const float* __restrict__ zcur, float* __restrict__ out_cur,
-              float* __restrict__ out_prev, TBCoef cf, double* partials, int stride, unsigned* counter) {
+__global__ void __launch_bounds__(TB_EX*(TY + 2 * TB_H), 1)
+    k_cheb_tb(Dims d, int ntx, int ntiles, int steps, int has_prev, Ctl* ctl,
+              const __grid_constant__ CUtensorMap m_cur, const __grid_constant__ CUtensorMap m_prev,
+              const __grid_constant__ CUtensorMap m_r, float* __restrict__ out_cur, float* __restrict__ out_prev,
+              const __grid_constant__ TBParams<LMAX> P, double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->done)) return;
   constexpr int EY = TY + 2 * TB_H;
-  __shared__ float plane[LMAX][EY][TB_EX];
-  __shared__ float cgx[LMAX], cgy[LMAX], cgz[LMAX], cs[LMAX];
+  constexpr int PL = EY * TB_EX;  // floats per layer plane
+  extern __shared__ __align__(128) float tb_dyn[];
+  float* tb_sm = tb_dyn + (((128u - (tb_smem(tb_dyn) & 127u)) & 127u) >> 2);  // 128-byte aligned
+  float* stage = tb_sm;                    // [3][LMAX][EY][TB_EX]: z_m, z_{m-1}, r
+  float* plane = tb_sm + 3 * LMAX * PL;    // [2][LMAX][EY][TB_EX]
+  unsigned long long* bar = (unsigned long long*)(tb_sm + 5 * LMAX * PL);
   const int L = d.L;
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
-  if (tid < L) {
-    cgx[tid] = __ldg(&tab->gxl[tid]);
-    cgy[tid] = __ldg(&tab->gyl[tid]);
-    cgz[tid] = __ldg(&tab->gzl[tid]);
-    cs[tid] = __ldg(&tab->s32[tid]);
+  const unsigned box_bytes = (unsigned)(L * PL * sizeof(float));
+  const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
+
+  if (tid == 0) {
+    tb_mbar_init(bar, 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  const int gx = blockIdx.x * TB_TX - TB_H + ex;
-  const int gy = blockIdx.y * TY - TB_H + ey;
-  const bool inside = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
-  const long long base = (long long)gx + (long long)d.nx * gy;
-  float cur[LMAX], prv[LMAX], rr[LMAX];
-#pragma unroll
-  for (int z = 0; z < LMAX; ++z) {
-    cur[z] = 0.f;
-    prv[z] = 0.f;
-    rr[z] = 0.f;
-    if (z < L && inside) {
-      const long long i = base + d.pxy * z;
-      cur[z] = zcur[i];
-      if (zprev) prv[z] = zprev[i];
-      rr[z] = __ldg(r + i);
-    }
-  }
-  const bool hasR = gx + 1 < d.nx, hasL = gx > 0, hasU = gy + 1 < d.ny, hasD = gy > 0;
-  __syncthreads();  // coefficients ready
-  for (int j = 0; j < steps; ++j) {
-#pragma unroll
-    for (int z = 0; z < LMAX; ++z)
-      if (z < L) plane[z][ey][ex] = cur[z];
-    __syncthreads();
-    const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
-    if (upd) {
-      const float c1 = cf.c1[j], c2 = cf.c2[j];
-      float nxt[LMAX];
-#pragma unroll
-      for (int z = 0; z < LMAX; ++z) {
-        nxt[z] = 0.f;
-        if (z < L) {
-          const float v = cur[z];
-          const float cx = cgx[z], cy = cgy[z];
-          const float gr = hasR ? cx : 0.f, gl = hasL ? cx : 0.f, gu = hasU ? cy : 0.f, gd = hasD ? cy : 0.f;
-          const float ga = (z + 1 < L) ? cgz[z] : 0.f;
-          const float gb = (z > 0) ? cgz[z > 0 ? z - 1 : 0] : 0.f;
-          const float va = (z + 1 < LMAX && z + 1 < L) ? cur[z + 1 < LMAX ? z + 1 : z] : 0.f;
-          const float vb = (z > 0) ? cur[z > 0 ? z - 1 : 0] : 0.f;
-          const float s = cs[z];
-          // same accumulation order as stencil_row / zwalk4: s v, +x, -x, +y, -y, +z, -z
-          float a = s * v, g = s;
-          a += gr * (v - plane[z][ey][ex + 1]);  g += gr;
-          a += gl * (v - plane[z][ey][ex - 1]);  g += gl;
-          a += gu * (v - plane[z][ey + 1][ex]);  g += gu;
-          a += gd * (v - plane[z][ey - 1][ex]);  g += gd;
-          a += ga * (v - va);                    g += ga;
-          a += gb * (v - vb);                    g += gb;
-          float res = rr[z] - a;
-          if (SCALED) res = res / g;
-          nxt[z] = v + c1 * (v - prv[z]) + c2 * res;
-        }
-      }
-#pragma unroll
-      for (int z = 0; z < LMAX; ++z) {
-        prv[z] = cur[z];
-        cur[z] = nxt[z];
-      }
-    }
-    __syncthreads();  // everyone has read the plane before the next step overwrites it
-  }
-  // the interior columns hold z_{m+steps} (cur) and z_{m+steps-1} (prv)
+  __syncthreads();
+  auto issue = [&](int t) {
+    const int x0 = (t % ntx) * TB_TX - TB_H, y0 = (t / ntx) * TY - TB_H;
+    tb_mbar_expect(bar, tx_bytes);
+    tb_tma_3d(stage, &m_cur, x0, y0, 0, bar);
+    if (has_prev) tb_tma_3d(stage + LMAX * PL, &m_prev, x0, y0, 0, bar);
+    tb_tma_3d(stage + 2 * LMAX * PL, &m_r, x0, y0, 0, bar);
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+
   float part[1] = {0.f};
-  const bool interior = inside && ex >= TB_H && ex < TB_H + TB_TX && ey >= TB_H && ey < TB_H + TY;
-  if (interior) {
+  unsigned parity = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const bool timed_out = !tb_mbar_wait(bar, parity);
+    if (__syncthreads_or(timed_out)) {
+      if (tid == 0) {
+        tb_mbar_wait(bar, parity);  // give the copy in flight a second chance to land
+        ctl->status = 3;
+        atomicExch(&ctl->done, 1);
+      }
+      break;
+    }
+    parity ^= 1u;
+    const int gx = (t % ntx) * TB_TX - TB_H + ex;
+    const int gy = (t / ntx) * TY - TB_H + ey;
+    const bool inside = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+    float cur[LMAX], prv[LMAX], rr[LMAX], inv[LMAX];
+    const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
-      if (z < L) {
-        const long long i = base + d.pxy * z;
-        out_cur[i] = cur[z];
-        if (out_prev) out_prev[i] = prv[z];
-        if (LAST) part[0] += rr[z] * cur[z];
+      const bool on = z < L;
+      cur[z] = on ? stage[z * PL + tid] : 0.f;
+      prv[z] = (on && has_prev) ? stage[(LMAX + z) * PL + tid] : 0.f;
+      rr[z] = on ? stage[(2 * LMAX + z) * PL + tid] : 0.f;
+      inv[z] = P.invd[nxf + 3 * nyf][z];
+    }
+    __syncthreads();  // staging buffer consumed by every thread
+    const int tn = t + gridDim.x;
+    if (tid == 0 && tn < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(tn);
+    }
+    // neighbour offsets inside a plane; a missing neighbour reads the cell itself
+    const int oR = tid + ((gx + 1 < d.nx) ? 1 : 0), oL = tid - ((gx > 0) ? 1 : 0);
+    const int oU = tid + ((gy + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gy > 0) ? TB_EX : 0);
+#pragma unroll
+    for (int j = 0; j < TB_H; ++j) {
+      if (j < steps) {
+        float* pl = plane + (j & 1) * LMAX * PL;
+#pragma unroll
+        for (int z = 0; z < LMAX; ++z)
+          if (z < L) pl[z * PL + tid] = cur[z];
+        __syncthreads();
+        const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
+        if (upd) {
+          float below = 0.f;  // z_m of the layer below (before its update)
+#pragma unroll
+          for (int z = 0; z < LMAX; ++z) {
+            if (z < L) {
+              const float v = cur[z];
+              const float va = (z + 1 < LMAX) ? cur[z + 1 < LMAX ? z + 1 : z] : 0.f;
+              const float* q = pl + z * PL;
+              float a = P.s[z] * v;
+              a += P.gx[z] * (v - q[oR]);
+              a += P.gx[z] * (v - q[oL]);
+              a += P.gy[z] * (v - q[oU]);
+              a += P.gy[z] * (v - q[oD]);
+              a += P.gzu[z] * (v - va);
+              if (z > 0) a += P.gzd[z] * (v - below);
+              float res = rr[z] - a;
+              if (SCALED) res *= inv[z];
+              const float nxt = v + P.c1[j] * (v - prv[z]) + P.c2[j] * res;
+              below = v;
+              prv[z] = v;
+              cur[z] = nxt;
+            }
+          }
+        }
+      }
+    }
+    // the interior columns hold z_{m+steps} (cur) and z_{m+steps-1} (prv)
+    const bool interior = inside && ex >= TB_H && ex < TB_H + TB_TX && ey >= TB_H && ey < TB_H + TY;
+    if (interior) {
+      const long long base = (long long)gx + (long long)d.nx * gy;
+#pragma unroll
+      for (int z = 0; z < LMAX; ++z) {
+        if (z < L) {
+          const long long i = base + d.pxy * z;
+          out_cur[i] = cur[z];
+          if (out_prev) out_prev[i] = prv[z];
+          if (LAST) part[0] += rr[z] * cur[z];
+        }
       }
     }
   }

@@ -16,6 +16,8 @@
 #include "kernels_v4.cuh"
 #include "kernels_tb.cuh"
 
+#include <cudaTypedefs.h>
+
 // Runs the statement with the constexpr bool U = cond (template switch for the
 // layer-table coefficient variants).
 #define TH_UNI(cond, ...)             \
@@ -435,19 +437,100 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
   return TH_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda)
+static PFN_cuTensorMapEncodeTiled_v12000 tensormap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D map of one FP32 field (x fastest, then y, then layer) with a box of
+// TB_EX x ey x L cells; cells outside the grid read as zero.
+static th_status tb_map(CUtensorMap* m, const Dims& d, const float* base, int ey) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensormap_encoder();
+  if (!enc) return th_fail(TH_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if (((uintptr_t)base & 15) != 0 || (d.nx % 4) != 0)
+    return th_fail(TH_EINVAL, "tensor map needs a 16-byte aligned base and nx %% 4 == 0");
+  const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.L};
+  const cuuint64_t strides[2] = {(cuuint64_t)d.nx * sizeof(float), (cuuint64_t)d.pxy * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)TB_EX, (cuuint32_t)ey, (cuuint32_t)d.L};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return th_fail(TH_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return TH_OK;
+}
+
+static int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (n[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n[dev] = v > 0 ? v : 1;
+  }
+  return n[dev];
+}
+
 template <int LM, int TY, bool SC, bool LA>
 static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   thermal_grid* g = P.g;
+  constexpr int EY = TY + 2 * TB_H;
   float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
-  TBCoef cf;
+  TBParams<LM> prm;
+  std::memset(&prm, 0, sizeof(prm));
   for (int j = 0; j < TB_H; ++j) {
-    cf.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
-    cf.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+    prm.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
+    prm.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
   }
-  const dim3 grid((P.d.nx + TB_TX - 1) / TB_TX, (P.d.ny + TY - 1) / TY);
-  k_cheb_tb<LM, TY, SC, LA><<<grid, dim3(TB_EX, TY + 2 * TB_H), 0, st>>>(
-      P.d, c.steps, g->ctl, g->tab, V.r, c.in_prev >= 0 ? pool[c.in_prev] : nullptr, pool[c.in_cur], pool[c.out_cur],
-      c.out_prev >= 0 ? pool[c.out_prev] : nullptr, cf, g->partials, g->partials_stride, g->counters);
+  const LayerTab& T = g->tab_host;
+  const int L = P.d.L;
+  for (int z = 0; z < L; ++z) {
+    prm.s[z] = T.s32[z];
+    prm.gx[z] = T.gxl[z];
+    prm.gy[z] = T.gyl[z];
+    prm.gzu[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
+    prm.gzd[z] = (z > 0) ? T.gzl[z - 1] : 0.f;
+    // diagonal summed in the one-step kernels' order: s, +x, -x, +y, -y, +z, -z
+    for (int nyf = 0; nyf < 3; ++nyf)
+      for (int nxf = 0; nxf < 3; ++nxf) {
+        float dg = prm.s[z];
+        dg += nxf >= 1 ? prm.gx[z] : 0.f;
+        dg += nxf >= 2 ? prm.gx[z] : 0.f;
+        dg += nyf >= 1 ? prm.gy[z] : 0.f;
+        dg += nyf >= 2 ? prm.gy[z] : 0.f;
+        dg += prm.gzu[z];
+        dg += prm.gzd[z];
+        prm.invd[nxf + 3 * nyf][z] = 1.0f / dg;
+      }
+  }
+  CUtensorMap mc, mp, mr;
+  TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], EY));
+  TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], EY));
+  TH_TRY(tb_map(&mr, P.d, V.r, EY));
+  const int ntx = (P.d.nx + TB_TX - 1) / TB_TX;
+  const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
+  const size_t smem = tb_smem_bytes<LM, TY>();
+  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, TY, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int nblk = std::min(ntiles, sm_count());
+  if (nblk > g->partials_stride) return th_fail(TH_ESTATE, "partials buffer smaller than the temporal-blocking grid");
+  k_cheb_tb<LM, TY, SC, LA><<<nblk, dim3(TB_EX, EY), smem, st>>>(
+      P.d, ntx, ntiles, c.steps, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, pool[c.out_cur],
+      c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
