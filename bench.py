@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the stencil-vs-CSR SpMV comparison")
     ap.add_argument("--polled", action="store_true",
                     help="host-polled loop instead of the CUDA graph (same kernels; for per-kernel profiling)")
     ap.add_argument("--time-steps", type=int, default=N_STEPS,
@@ -386,6 +387,8 @@ def main():
                          "d2h_bytes_per_step": int(inst.n * 8),
                          "note": "per bench step (one 100-step trajectory): 4 power maps + T_0 to the device, "
                                  "T_100 back, through thermal_run_transient with pinned host buffers"}
+    if not args.no_ablation:
+        result["spmv_ablation"] = ablation_section(grid, inst.n, args.reps, result.get("kernels"), peak)
     if not args.no_batched:
         result["batched"] = batched_section(args)
     if not args.no_adjoint:
@@ -410,6 +413,39 @@ def _event_ms(fn, reps=1):
     e1.record(s)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps, out
+
+
+# algorithmic bytes per row of the CSR product (Sec. 5.5 comparison): row offset,
+# ~7 (column index + value) pairs, x and y
+CSR_BYTES = {"f32": 4 + 7 * (4 + 4) + 4 + 4, "f64": 4 + 7 * (4 + 8) + 8 + 8}
+
+
+def ablation_section(grid, n, reps, kern, peak):
+    """Stencil product vs a CSR copy of the same matrix (Sec. 5.5, Table abl_spmv):
+    row-wise (scalar) and 8-lane (vector) CSR in FP32 and FP64 on the 1024x1024x8
+    transient matrix, against the stencil kernels timed the same way."""
+    import torch
+    out = {}
+    x64 = torch.rand(n, dtype=torch.float64, device="cuda")
+    for prec, x in (("f32", x64.float()), ("f64", x64)):
+        y_st = grid.apply(x, DT, "fp64" if prec == "f64" else "mixed")
+        for var in ("scalar", "vector"):
+            y, ms = grid.csr_spmv(x, dt=DT, variant=var, reps=reps)
+            diff = ((y - y_st).abs().max() / y_st.abs().max()).item()
+            gbs = CSR_BYTES[prec] * n / (ms * 1e-3) / 1e9
+            out[f"csr_{var}_{prec}"] = {"ms": ms, "bytes_per_cell": CSR_BYTES[prec], "GB/s": gbs,
+                                        "frac_of_peak": gbs / peak, "max_rel_diff_vs_stencil": diff}
+    st = {}
+    for name in ("stencil_f32", "stencil_f32_faces", "stencil_f64"):
+        st[name] = kern[name]["ms"] if kern and name in kern else grid.kernel_time(name, reps=reps, dt=DT)
+    out["stencil_ms"] = st
+    out["speedup_stencil_vs_csr_scalar"] = {
+        "f64 (faces FP64)": out["csr_scalar_f64"]["ms"] / st["stencil_f64"],
+        "f32 (faces FP32)": out["csr_scalar_f32"]["ms"] / st["stencil_f32_faces"],
+        "f32 (layer table)": out["csr_scalar_f32"]["ms"] / st["stencil_f32"]}
+    out["note"] = ("same matrix (transient, dt=1e-4) in CSR with 32-bit indices; the paper reports 2.0-2.2x "
+                   "for its diagonal-wise kernels over CSR on a different GPU")
+    return out
 
 
 def batched_section(args):

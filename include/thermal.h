@@ -187,6 +187,24 @@ th_status thermal_apply(thermal_grid* g, double dt, int precision, const void* x
                         void* stream);
 
 /*
+ * y = A x through a compressed-sparse-row copy of the same matrix, for the
+ * stencil-vs-CSR comparison of Sec. 5.5 (Ablation Study I, Table abl_spmv); not
+ * used by any solve.  The CSR matrix is assembled on the device from the FP64
+ * faces (rows in cell order, columns ascending, 32-bit offsets), used, and freed
+ * inside the call.
+ * variant: 0 = one thread per row (the row-wise baseline), 1 = eight lanes per row.
+ * precision: TH_PREC_FP64 (x, y double) or TH_PREC_MIXED_IR (x, y float; values
+ *   rounded from FP64 once).  dt > 0 adds the capacity term of a backward-Euler step.
+ * x, y: device, n_cells elements, must not overlap.  The product is launched
+ *   1 + reps times; when ms is non-NULL the last reps launches are timed with CUDA
+ *   events on `stream` and *ms receives the mean duration of one.  Synchronises
+ *   `stream` before returning.  TH_EINVAL for a bad argument or more than 2^31 - 1
+ *   non-zeros; TH_ENOMEM / TH_ECUDA when device allocation or a launch fails.
+ */
+th_status thermal_csr_spmv(thermal_grid* g, int variant, int precision, double dt, const void* x, void* y,
+                           int reps, double* ms, void* stream);
+
+/*
  * z = M^{-1} r for the preconditioner selected by opts (precond, cheb_degree,
  * cheb_scaled, lanczos_steps), in FP32 (r, z: device float, n_cells).  For
  * TH_PC_CHEB the spectral interval is estimated first (cached per grid and dt).

@@ -95,6 +95,7 @@ SIGNATURES = {
     "thermal_grad": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, _dp, C.POINTER(SolveOpts), C.POINTER(SolveStats), _vp]),
     "thermal_solve_batched": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.c_int, C.POINTER(_vp),
                                         C.POINTER(SolveOpts), C.POINTER(SolveStats), _vp]),
+    "thermal_csr_spmv": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, C.c_int, _dp, _vp]),
     "thermal_apply_dot_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, C.POINTER(C.c_float), _vp,
                                             _vp, _vp, _vp]),
 }

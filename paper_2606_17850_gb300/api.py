@@ -129,6 +129,18 @@ class ThermalGrid:
         L.check(L.load().thermal_kernel_time(self._h, kid, int(reps), float(dt), C.byref(ms), _stream()))
         return ms.value
 
+    def csr_spmv(self, x: torch.Tensor, dt: float = 0.0, variant: str = "scalar", reps: int = 0):
+        """y = A x through a CSR copy of the matrix (Sec. 5.5 comparison).  x float32 or
+        float64 on the device.  Returns (y, ms): ms is the mean launch time over reps
+        timed launches, or None when reps == 0."""
+        prec = "fp64" if x.dtype == torch.float64 else "mixed"
+        y = torch.empty_like(x)
+        ms = C.c_double()
+        L.check(L.load().thermal_csr_spmv(self._h, {"scalar": 0, "vector": 1}[variant], PRECISION[prec], float(dt),
+                                          _ptr(x), _ptr(y), max(int(reps), 1),
+                                          C.byref(ms) if reps > 0 else None, _stream()))
+        return y, (ms.value if reps > 0 else None)
+
     # ------------------------------------------------------------------ solves
 
     def solve_steady(self, power: torch.Tensor, T: Optional[torch.Tensor] = None, **opts):

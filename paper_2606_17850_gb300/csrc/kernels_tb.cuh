@@ -32,8 +32,8 @@
 #include "common.cuh"
 
 #define TB_H 4
-#define TB_TX 32
-#define TB_EX (TB_TX + 2 * TB_H)
+#define TB_EX 32                // grown tile width: one warp per row
+#define TB_TX (TB_EX - 2 * TB_H)  // interior columns per tile
 // bounded mbarrier wait: try_wait suspends for a hardware time slice per attempt,
 // so this limit is on the order of a second
 #define TB_WAIT_LIMIT (1 << 20)
@@ -86,19 +86,22 @@ __device__ __forceinline__ void tb_tma_3d(float* dst, const CUtensorMap* map, in
 
 // dynamic shared memory of one CTA: staging (3 boxes) + two planes + mbarrier,
 // plus room to align the staging boxes to 128 bytes
-template <int LMAX, int TY>
+template <int LMAX, int EY>
 constexpr size_t tb_smem_bytes() {
-  return (size_t)(3 + 2) * LMAX * (TY + 2 * TB_H) * TB_EX * sizeof(float) + 16 + 128;
+  return (size_t)(3 + 2) * LMAX * EY * TB_EX * sizeof(float) + 16 + 128;
 }
 
-template <int LMAX, int TY, bool SCALED, bool LAST>
-__global__ void __launch_bounds__(TB_EX*(TY + 2 * TB_H), 1)
-    k_cheb_tb(Dims d, int ntx, int ntiles, int steps, int has_prev, Ctl* ctl,
+// Layers L..LMAX-1 (when the stack has fewer than LMAX layers) are carried as
+// zeros: their coefficients and inverse diagonal are 0, so they stay 0 and the
+// step loop needs no per-layer guard.
+template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST>
+__global__ void __launch_bounds__(TB_EX * EY, 1)
+    k_cheb_tb(Dims d, int ntx, int ntiles, int has_prev, Ctl* ctl,
               const __grid_constant__ CUtensorMap m_cur, const __grid_constant__ CUtensorMap m_prev,
               const __grid_constant__ CUtensorMap m_r, float* __restrict__ out_cur, float* __restrict__ out_prev,
               const __grid_constant__ TBParams<LMAX> P, double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->done)) return;
-  constexpr int EY = TY + 2 * TB_H;
+  constexpr int TY = EY - 2 * TB_H;
   constexpr int PL = EY * TB_EX;  // floats per layer plane
   extern __shared__ __align__(128) float tb_dyn[];
   float* tb_sm = tb_dyn + (((128u - (tb_smem(tb_dyn) & 127u)) & 127u) >> 2);  // 128-byte aligned
@@ -161,41 +164,37 @@ __global__ void __launch_bounds__(TB_EX*(TY + 2 * TB_H), 1)
     const int oR = tid + ((gx + 1 < d.nx) ? 1 : 0), oL = tid - ((gx > 0) ? 1 : 0);
     const int oU = tid + ((gy + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gy > 0) ? TB_EX : 0);
 #pragma unroll
-    for (int j = 0; j < TB_H; ++j) {
-      if (j < steps) {
-        float* pl = plane + (j & 1) * LMAX * PL;
+    for (int j = 0; j < STEPS; ++j) {
+      float* pl = plane + (j & 1) * LMAX * PL;
 #pragma unroll
-        for (int z = 0; z < LMAX; ++z)
-          if (z < L) pl[z * PL + tid] = cur[z];
-        __syncthreads();
-        const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
-        if (upd) {
-          float below = 0.f;  // z_m of the layer below (before its update)
+      for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = cur[z];
+      __syncthreads();
+      // rows outside the shrinking valid region skip the step as whole warps
+      const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
+      if (upd) {
+        float below = 0.f;  // z_m of the layer below (before its update)
 #pragma unroll
-          for (int z = 0; z < LMAX; ++z) {
-            if (z < L) {
-              const float v = cur[z];
-              const float va = (z + 1 < LMAX) ? cur[z + 1 < LMAX ? z + 1 : z] : 0.f;
-              const float* q = pl + z * PL;
-              float a = P.s[z] * v;
-              a += P.gx[z] * (v - q[oR]);
-              a += P.gx[z] * (v - q[oL]);
-              a += P.gy[z] * (v - q[oU]);
-              a += P.gy[z] * (v - q[oD]);
-              a += P.gzu[z] * (v - va);
-              if (z > 0) a += P.gzd[z] * (v - below);
-              float res = rr[z] - a;
-              if (SCALED) res *= inv[z];
-              const float nxt = v + P.c1[j] * (v - prv[z]) + P.c2[j] * res;
-              below = v;
-              prv[z] = v;
-              cur[z] = nxt;
-            }
-          }
+        for (int z = 0; z < LMAX; ++z) {
+          const float v = cur[z];
+          const float va = (z + 1 < LMAX) ? cur[z + 1 < LMAX ? z + 1 : z] : 0.f;
+          const float* q = pl + z * PL;
+          float a = P.s[z] * v;
+          a += P.gx[z] * (v - q[oR]);
+          a += P.gx[z] * (v - q[oL]);
+          a += P.gy[z] * (v - q[oU]);
+          a += P.gy[z] * (v - q[oD]);
+          if (z + 1 < LMAX) a += P.gzu[z] * (v - va);
+          if (z > 0) a += P.gzd[z] * (v - below);
+          float res = rr[z] - a;
+          if (SCALED) res *= inv[z];
+          const float nxt = v + P.c1[j] * (v - prv[z]) + P.c2[j] * res;
+          below = v;
+          prv[z] = v;
+          cur[z] = nxt;
         }
       }
     }
-    // the interior columns hold z_{m+steps} (cur) and z_{m+steps-1} (prv)
+    // the interior columns hold z_{m+STEPS} (cur) and z_{m+STEPS-1} (prv)
     const bool interior = inside && ex >= TB_H && ex < TB_H + TB_TX && ey >= TB_H && ey < TB_H + TY;
     if (interior) {
       const long long base = (long long)gx + (long long)d.nx * gy;

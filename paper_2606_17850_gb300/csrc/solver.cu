@@ -52,7 +52,7 @@ struct Plan {
   // pool of four FP32 buffers {zc0, zc1, zc2, mu} (indices 0..3)
   struct Chunk { int steps, m0, in_cur, in_prev, out_cur, out_prev; };
   bool fused = false;  // temporal blocking active
-  int tb_ty = 16;
+  int tb_lmax = 8;  // layer capacity of the fused kernel (8: 32 x 32 tiles, 12: 32 x 24)
   std::vector<Chunk> chunks;
   int zfin = -1;  // pool index of the preconditioned vector (-1: the per-step rule)
   bool v4 = false;
@@ -328,9 +328,9 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     P.pc_spmv = P.k - 1;
     const int fuse = o->cheb_fuse == 0 ? TB_H : o->cheb_fuse;
     if (P.prec != TH_PREC_FP64 && P.v4 && P.uni && fuse > 1 && P.k > 1) {
-      // register columns: up to 8 layers with 40 x 24 threads, up to 12 with 40 x 16
-      P.tb_ty = g->L <= 8 ? 16 : (g->L <= 12 ? 8 : 0);
-      if (P.tb_ty > 0) {
+      // register columns: up to 8 layers with 32 x 32 threads, up to 12 with 32 x 24
+      P.tb_lmax = g->L <= 8 ? 8 : (g->L <= 12 ? 12 : 0);
+      if (P.tb_lmax > 0) {
         P.fused = true;
         int cur = 0, prev = -1, m = 1, left = P.k - 1;
         while (left > 0) {
@@ -486,10 +486,10 @@ static int sm_count() {
   return n[dev];
 }
 
-template <int LM, int TY, bool SC, bool LA>
+template <int LM, int EY, int ST, bool SC, bool LA>
 static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   thermal_grid* g = P.g;
-  constexpr int EY = TY + 2 * TB_H;
+  constexpr int TY = EY - 2 * TB_H;
   float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
   TBParams<LM> prm;
   std::memset(&prm, 0, sizeof(prm));
@@ -524,35 +524,46 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   TH_TRY(tb_map(&mr, P.d, V.r, EY));
   const int ntx = (P.d.nx + TB_TX - 1) / TB_TX;
   const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
-  const size_t smem = tb_smem_bytes<LM, TY>();
-  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, TY, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = tb_smem_bytes<LM, EY>();
+  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, EY, ST, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
   const int nblk = std::min(ntiles, sm_count());
   if (nblk > g->partials_stride) return th_fail(TH_ESTATE, "partials buffer smaller than the temporal-blocking grid");
-  k_cheb_tb<LM, TY, SC, LA><<<nblk, dim3(TB_EX, EY), smem, st>>>(
-      P.d, ntx, ntiles, c.steps, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, pool[c.out_cur],
+  k_cheb_tb<LM, EY, ST, SC, LA><<<nblk, dim3(TB_EX, EY), smem, st>>>(
+      P.d, ntx, ntiles, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, pool[c.out_cur],
       c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
+}
+
+// chunk dispatch on (steps, last chunk)
+template <int LM, int EY, bool SC, bool LA>
+static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
+  switch (c.steps) {
+    case 1: return tb_launch<LM, EY, 1, SC, LA>(P, V, st, c);
+    case 2: return tb_launch<LM, EY, 2, SC, LA>(P, V, st, c);
+    case 3: return tb_launch<LM, EY, 3, SC, LA>(P, V, st, c);
+    case 4: return tb_launch<LM, EY, 4, SC, LA>(P, V, st, c);
+    default: return th_fail(TH_ESTATE, "temporal-blocking chunk with %d steps", c.steps);
+  }
+}
+
+template <int LM, int EY, bool SC>
+static th_status tb_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last) {
+  return last ? tb_steps<LM, EY, SC, true>(P, V, st, c) : tb_steps<LM, EY, SC, false>(P, V, st, c);
 }
 
 static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st) {
   for (size_t ci = 0; ci < P.chunks.size(); ++ci) {
     const bool last = (ci + 1 == P.chunks.size());
     const Plan::Chunk& c = P.chunks[ci];
-#define TH_TBL(LM, TY)                                                       \
-  if (P.scaled) {                                                            \
-    if (last) TH_TRY((tb_launch<LM, TY, true, true>(P, V, st, c)));          \
-    else TH_TRY((tb_launch<LM, TY, true, false>(P, V, st, c)));              \
-  } else {                                                                   \
-    if (last) TH_TRY((tb_launch<LM, TY, false, true>(P, V, st, c)));         \
-    else TH_TRY((tb_launch<LM, TY, false, false>(P, V, st, c)));             \
-  }
-    if (P.tb_ty == 16) {
-      TH_TBL(8, 16)
+    if (P.tb_lmax == 8) {
+      if (P.scaled) TH_TRY((tb_chunk<8, 32, true>(P, V, st, c, last)));
+      else TH_TRY((tb_chunk<8, 32, false>(P, V, st, c, last)));
     } else {
-      TH_TBL(12, 8)
+      if (P.scaled) TH_TRY((tb_chunk<12, 24, true>(P, V, st, c, last)));
+      else TH_TRY((tb_chunk<12, 24, false>(P, V, st, c, last)));
     }
-#undef TH_TBL
   }
   return TH_OK;
 }

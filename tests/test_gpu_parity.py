@@ -113,6 +113,38 @@ def test_stencil_symmetry_fp64():
     assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
 
 
+# ------------------------------------------------- Sec. 5.5: CSR copy of the matrix
+
+@pytest.mark.parametrize("variant", ["scalar", "vector"])
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-14), ("mixed", 2e-6)])
+@pytest.mark.parametrize("nx,ny,mk,dt", [(37, 21, "c2", 1e-4), (5, 3, "c1", 0.0), (1, 1, "c1", 0.0)])
+def test_csr_spmv_matches_oracle(variant, prec, rtol, nx, ny, mk, dt):
+    """The CSR product (device-assembled, closed-form row offsets) equals the oracle's
+    row-wise CSR product, including 1-cell-wide grids and the transient diagonal."""
+    st = STACKS[mk]()
+    A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None).tocsr()
+    g = grid_of(nx, ny, st)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    xd = cuda(ti.random_vector(A.shape[0], 23, lo=-2.0, hi=3.0), dtype)
+    y, ms = g.csr_spmv(xd, dt=dt, variant=variant, reps=2)
+    assert ms is not None and ms > 0
+    xh = xd.cpu().double().numpy()
+    err = np.abs(y.cpu().double().numpy() - A @ xh)
+    assert np.all(err <= rtol * (abs(A) @ np.abs(xh))), np.max(err / (abs(A) @ np.abs(xh)))
+
+
+def test_csr_spmv_rejects_bad_arguments():
+    st = ti.stack_c1()
+    g = grid_of(8, 8, st)
+    x = cuda(np.ones(8 * 8 * st.L), torch.float64)
+    with pytest.raises(Exception):
+        g.csr_spmv(x, variant="diagonal")
+    import ctypes as C
+    from paper_2606_17850_gb300 import _lib as L
+    assert L.load().thermal_csr_spmv(g._h, 0, 0, 0.0, C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), 1,
+                                     None, None) == L.TH_EINVAL
+
+
 def _kmap(st, nx, ny, seed=5):
     return np.repeat(st.k(), nx * ny) * np.random.default_rng(seed).uniform(0.5, 2.0, nx * ny * st.L)
 
