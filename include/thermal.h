@@ -243,7 +243,9 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  *   7  FP64 Chebyshev step (plain FP64 path)
  *   8  double-float refinement residual (the mixed path's r = b - A theta) (*)
  *   9, 10, 11, 12  kernels 1, 3, 8, 0 reading the per-face arrays
- *  13  four Chebyshev steps fused in one launch (temporal blocking, layer-uniform grids)
+ *  13, 14, 15  four, two, three Chebyshev steps fused in one launch (temporal
+ *      blocking; an inner chunk reading z_m, z_{m-1}, r and writing z_{m+S},
+ *      z_{m+S-1}); layer-uniform grids with nx % 4 == 0, else TH_EINVAL
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

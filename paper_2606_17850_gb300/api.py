@@ -120,7 +120,7 @@ class ThermalGrid:
     KERNELS = {"stencil_f32": 0, "cheb_f32": 1, "cheb_bf16": 2, "spmv_dot_f32": 3, "update_f32": 4,
                "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7, "residual_df": 8,
                "cheb_f32_faces": 9, "spmv_dot_f32_faces": 10, "residual_df_faces": 11, "stencil_f32_faces": 12,
-               "cheb_tb4": 13}
+               "cheb_tb4": 13, "cheb_tb2": 14, "cheb_tb3": 15}
 
     def kernel_time(self, kernel, reps=50, dt=0.0):
         """Average duration (ms) of one launch of a hot kernel on this grid (CUDA events)."""

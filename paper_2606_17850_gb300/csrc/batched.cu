@@ -1,19 +1,25 @@
 // Batched steady solves of independent stacks in one persistent launch.
 //
-// All instances' cells are cut into 32 x 8 single-layer tiles and listed in one
-// work list.  One cooperative kernel runs FP64 iterative refinement around FP32
-// PCG (Algorithm 1; Jacobi or Chebyshev preconditioner) for every instance: each
-// phase (residual, search direction + stencil, update, Chebyshev step, ...) walks
-// the tiles of the still-active instances, a grid-wide barrier separates phases,
-// and one block per instance finishes that instance's reductions and takes its
-// loop decisions with the same functions the single-grid kernels use.  An
-// instance that has converged drops out of every later phase (its tiles are
-// skipped); the loops end when no instance is active.
+// Every instance is cut into tiles of 128 x 8 columns (all layers): the thread
+// block of the vectorised z-walk kernels, 32 x 8 threads with 4 cells each.  All
+// instances' tiles form one work list.  One cooperative kernel runs FP64 iterative
+// refinement around FP32 PCG (Algorithm 1; Jacobi or Chebyshev preconditioner) for
+// every instance: each phase (residual, search direction + stencil, update,
+// Chebyshev step, ...) walks the tiles of the still-active instances, a grid-wide
+// barrier separates phases, and one block per instance finishes that instance's
+// reductions and takes its loop decisions with the same functions the single-grid
+// kernels use.  An instance that has converged drops out of every later phase (its
+// tiles are skipped); the loops end when no instance is active.
+//
+// Per tile, the block copies the instance descriptor and the loop scalars it needs
+// into shared memory once (one L2 round trip), then the stencil phases run the
+// z-walk engine of the single-grid kernels (per-layer coefficient table on grids
+// with one conductivity per layer, per-face arrays otherwise).
 //
 // Vectors written during the kernel are read with ordinary (coherent) loads: the
 // grid-wide barrier makes every write before it visible to every thread after it.
-// Only immutable data (face conductances, tables) uses the non-coherent read-only
-// path (__ldg); control fields are read through L2 (__ldcg).
+// Only immutable data (face conductances, tables, coefficients) uses the
+// non-coherent read-only path (__ldg); control fields are read through L2 (__ldcg).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -22,12 +28,13 @@
 #include <vector>
 
 #include "internal.h"
+#include "kernels_v4.cuh"
 
 namespace cg = cooperative_groups;
 
 struct BInst {
   Dims d;
-  int tile0, ntiles, tbx, tby;
+  int tile0, ntiles, tbx, uni;
   Faces32 f32;
   Faces64 f64;
   const LayerTab* tab;
@@ -43,6 +50,7 @@ struct BInst {
   float inv_theta;
   Ctl* ctl;
 };
+static_assert(sizeof(BInst) % 4 == 0, "descriptor copied as 32-bit words");
 
 struct BArgs {
   const BInst* inst;
@@ -53,21 +61,12 @@ struct BArgs {
   int max_sweeps;    // safety cap on inner sweeps of the whole batch
 };
 
-// loads of vectors written earlier in the same kernel (ordinary, coherent loads)
-__device__ __forceinline__ float lcg(const float* p) { return *p; }
-__device__ __forceinline__ double lcg(const double* p) { return *p; }
-
-__device__ __forceinline__ Cell tile_cell(const BInst& I, int t) {
-  const int loc = t - I.tile0;
-  const int bx = loc % I.tbx, by = (loc / I.tbx) % I.tby, z = loc / (I.tbx * I.tby);
-  Cell c;
-  c.x = bx * TH_BX + threadIdx.x;
-  c.y = by * TH_BY + threadIdx.y;
-  c.z = z;
-  c.valid = (c.x < I.d.nx) && (c.y < I.d.ny);
-  c.i = (long long)c.x + (long long)I.d.nx * ((long long)c.y + (long long)I.d.ny * z);
-  return c;
-}
+// loop scalars of one instance, read once per tile
+struct BCtl {
+  int act, first;
+  float alpha, beta, rscale;
+  double rnorm;
+};
 
 // Instance predicates (control fields change only in finish steps, between barriers).
 enum { ACT_ALL = 0, ACT_OUTER = 1, ACT_INNER = 2 };
@@ -91,35 +90,65 @@ __device__ bool any_active(const BArgs& A, int what) {
   return r;
 }
 
-// One phase over the active instances' tiles; body(I, c, v) fills NQ per-thread
-// partial sums, reduced per tile into partials[q][t].
+__device__ __forceinline__ Walk4 tile_walk(const BInst& I, int t) {
+  const int loc = t - I.tile0;
+  const int bx = loc % I.tbx, by = loc / I.tbx;
+  Walk4 w;
+  w.x0 = 4 * (bx * TH_BX + threadIdx.x);
+  w.y = by * TH_BY4 + threadIdx.y;
+  w.zs = 0;
+  w.ze = I.d.L;
+  w.valid = (w.x0 < I.d.nx) && (w.y < I.d.ny);
+  w.b0 = (long long)w.x0 + (long long)I.d.nx * w.y;
+  return w;
+}
+
+// One phase over the active instances' tiles: body(I, C, w, v) with the tile's
+// instance I and loop scalars C in shared memory fills NQ per-thread partial sums,
+// reduced per tile into partials[q][t].
 template <int NQ, class F>
 __device__ void phase(const BArgs& A, int what, F body) {
+  __shared__ BInst si;
+  __shared__ BCtl sc;
   __shared__ double sm[2][32];
   const int tid = thread_linear_id(), nw = (block_threads() + 31) >> 5;
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
-    const BInst& I = A.inst[A.tile_inst[t]];
-    if (!active(I.ctl, what)) continue;
-    const Cell c = tile_cell(I, t);
-    float v[NQ > 0 ? NQ : 1] = {};
-    if (c.valid) body(I, c, v);
-    if (NQ > 0) {
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const float w = warp_sum(v[q]);
-        if ((tid & 31) == 0) sm[q][tid >> 5] = (double)w;
-      }
-      __syncthreads();
-      if (tid == 0) {
+    const int ii = __ldg(A.tile_inst + t);
+    const int* src = reinterpret_cast<const int*>(A.inst + ii);
+    int* dst = reinterpret_cast<int*>(&si);
+    for (int q = tid; q < (int)(sizeof(BInst) / 4); q += block_threads()) dst[q] = __ldg(src + q);
+    if (tid == 0) {
+      const Ctl* c = A.inst[ii].ctl;
+      sc.act = active(c, what);
+      sc.first = __ldcg(&c->first);
+      sc.alpha = __ldcg(&c->alpha_f);
+      sc.beta = __ldcg(&c->beta_f);
+      sc.rscale = __ldcg(&c->rscale_f);
+      sc.rnorm = __ldcg(&c->rnorm);
+    }
+    __syncthreads();
+    if (sc.act) {
+      const Walk4 w = tile_walk(si, t);
+      float v[NQ > 0 ? NQ : 1] = {};
+      if (w.valid) body(si, sc, w, v);
+      if (NQ > 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          double s = 0.0;
-          for (int w = 0; w < nw; ++w) s += sm[q][w];
-          A.partials[(size_t)q * A.ntiles + t] = s;
+          const float s = warp_sum(v[q]);
+          if ((tid & 31) == 0) sm[q][tid >> 5] = (double)s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            double s = 0.0;
+            for (int w2 = 0; w2 < nw; ++w2) s += sm[q][w2];
+            A.partials[(size_t)q * A.ntiles + t] = s;
+          }
         }
       }
-      __syncthreads();
     }
+    __syncthreads();  // descriptor and scalars are reused by the next tile
   }
 }
 
@@ -154,45 +183,88 @@ __device__ void finish(const BArgs& A, int what, F fin) {
   }
 }
 
-template <typename TP>
-__device__ void body_residual(const BInst& I, const Cell& c, float (&v)[2]) {
-  double dg;
-  const double ti = lcg(I.theta + c.i);
-  const double a = stencil_row<double>(I.f64.gx, I.f64.gy, I.f64.gz, I.d, c, __ldg(&I.tab->s64[c.z]), ti,
-                                       [&](long long j) { return lcg(I.theta + j); }, dg);
-  const double b = (double)((const TP*)I.P)[c.i];
-  const double ri = b - a;
-  I.r[c.i] = (float)ri;
-  const float rf = (float)ri, bf = (float)b;
-  v[0] = rf * rf;
-  v[1] = bf * bf;
+// the layers of a tile column segment: f(i) for i = index of its first cell in each layer
+template <class F>
+__device__ __forceinline__ void for_layers(const BInst& I, const Walk4& w, F f) {
+  for (int z = 0; z < I.d.L; ++z) f(w.b0 + (long long)z * I.d.pxy, z);
 }
 
-// z for the Jacobi / first Chebyshev iterate / none
-__device__ __forceinline__ float z_of(const BArgs& A, const BInst& I, const Cell& c, float ri) {
-  if (A.pc == TH_PC_JACOBI) return ri * __ldg(I.invd + c.i);
-  if (A.pc == TH_PC_CHEB) return (A.scaled ? ri * __ldg(I.invd + c.i) : ri) * I.inv_theta;
-  return ri;
+// FP64 refinement residual r = P - A theta of 4 cells per layer, and ||r||^2, ||P||^2
+template <typename TP>
+__device__ void body_residual(const BInst& I, const Walk4& w, float (&v)[2]) {
+  for_layers(I, w, [&](long long i0, int z) {
+    const double s = __ldg(&I.tab->s64[z]);
+    float o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Cell c;
+      c.x = w.x0 + k;
+      c.y = w.y;
+      c.z = z;
+      c.i = i0 + k;
+      c.valid = true;
+      double dg;
+      const double ti = I.theta[c.i];
+      const double a = stencil_row<double>(I.f64.gx, I.f64.gy, I.f64.gz, I.d, c, s, ti,
+                                           [&](long long j) { return I.theta[j]; }, dg);
+      const double b = (double)((const TP*)I.P)[c.i];
+      const float rf = (float)(b - a), bf = (float)b;
+      o[k] = rf;
+      v[0] += rf * rf;
+      v[1] += bf * bf;
+    }
+    st4(I.r + i0, make_float4(o[0], o[1], o[2], o[3]));
+  });
+}
+
+// z for the Jacobi / first Chebyshev iterate / none, 4 cells
+__device__ __forceinline__ float4 z_of4(const BArgs& A, const BInst& I, long long i, const float4& r) {
+  if (A.pc == TH_PC_NONE) return r;
+  float4 z = r;
+  if (A.pc == TH_PC_JACOBI || A.scaled) {
+    const float4 iv = __ldg(reinterpret_cast<const float4*>(I.invd + i));
+    z = make_float4(r.x * iv.x, r.y * iv.y, r.z * iv.z, r.w * iv.w);
+  }
+  if (A.pc == TH_PC_CHEB) z = make_float4(z.x * I.inv_theta, z.y * I.inv_theta, z.z * I.inv_theta, z.w * I.inv_theta);
+  return z;
+}
+
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+
+// stencil walk over a tile with the instance's coefficient source
+template <typename F4, typename F1, typename E>
+__device__ __forceinline__ void walk(const BInst& I, const Walk4& w, F4 V4, F1 V1, E epi) {
+  if (I.uni)
+    zwalk4<float, true>(I.d, w, I.f32.gx, I.f32.gy, I.f32.gz, I.tab, V4, V1, epi);
+  else
+    zwalk4<float, false>(I.d, w, I.f32.gx, I.f32.gy, I.f32.gz, I.tab, V4, V1, epi);
 }
 
 __device__ void cheb_tail(const BArgs& A, cg::grid_group& grid) {
   for (int m = 1; m < A.k; ++m) {
     const bool last = (m == A.k - 1);
-    phase<1>(A, ACT_INNER, [&](const BInst& I, const Cell& c, float (&v)[1]) {
+    phase<1>(A, ACT_INNER, [&](const BInst& I, const BCtl&, const Walk4& w, float (&v)[1]) {
       const float* zprev = (m >= 2) ? I.zc[(m - 2) % 3] : nullptr;
       const float* zcur = I.zc[(m - 1) % 3];
       float* znext = I.zc[m % 3];
-      float dg;
-      const float zi = lcg(zcur + c.i);
-      const float az = stencil_row<float>(I.f32.gx, I.f32.gy, I.f32.gz, I.d, c, __ldg(&I.tab->s32[c.z]), zi,
-                                          [&](long long j) { return lcg(zcur + j); }, dg);
-      const float ri = lcg(I.r + c.i);
-      float res = ri - az;
-      if (A.scaled) res = res / dg;
-      const float zp = zprev ? lcg(zprev + c.i) : 0.f;
-      const float zn = zi + __ldg(I.c1 + m) * (zi - zp) + __ldg(I.c2 + m) * res;
-      znext[c.i] = zn;
-      if (last) v[0] = ri * zn;
+      const float c1 = __ldg(I.c1 + m), c2 = __ldg(I.c2 + m);
+      walk(I, w, [&](long long i) { return ld4(zcur + i); }, [&](long long j) { return zcur[j]; },
+           [&](long long i, int, const float4& zv, const float (&acc)[4], const float (&dg)[4]) {
+             const float4 rv = ld4(I.r + i);
+             const float4 zp = zprev ? ld4(zprev + i) : z4();
+             float o[4];
+#pragma unroll
+             for (int k = 0; k < 4; ++k) {
+               const float zk = cmp(zv, k);
+               float res = cmp(rv, k) - acc[k];
+               if (A.scaled) res = res / dg[k];
+               o[k] = zk + c1 * (zk - cmp(zp, k)) + c2 * res;
+               if (last) v[0] += cmp(rv, k) * o[k];
+             }
+             st4(znext + i, make_float4(o[0], o[1], o[2], o[3]));
+           });
     });
     grid.sync();
     if (last) {
@@ -206,7 +278,7 @@ __device__ void cheb_tail(const BArgs& A, cg::grid_group& grid) {
 }
 
 template <typename TP>
-__global__ void __launch_bounds__(TH_NT) k_batched(BArgs A) {
+__global__ void __launch_bounds__(TH_BX* TH_BY4) k_batched(BArgs A) {
   cg::grid_group grid = cg::this_grid();
   const int rz_here = (A.pc != TH_PC_CHEB || A.k == 1) ? 1 : 0;
   auto zfinal = [&](const BInst& I) -> const float* {
@@ -215,25 +287,33 @@ __global__ void __launch_bounds__(TH_NT) k_batched(BArgs A) {
     return I.zc[0];
   };
   // theta from the initial guess
-  phase<0>(A, ACT_ALL, [&](const BInst& I, const Cell& c, float (&)[1]) {
-    I.theta[c.i] = I.T_in ? I.T_in[c.i] - I.t_amb : 0.0;
+  phase<0>(A, ACT_ALL, [&](const BInst& I, const BCtl&, const Walk4& w, float (&)[1]) {
+    for_layers(I, w, [&](long long i0, int) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) I.theta[i0 + k] = I.T_in ? I.T_in[i0 + k] - I.t_amb : 0.0;
+    });
   });
   grid.sync();
-  phase<2>(A, ACT_OUTER, [&](const BInst& I, const Cell& c, float (&v)[2]) { body_residual<TP>(I, c, v); });
+  phase<2>(A, ACT_OUTER, [&](const BInst& I, const BCtl&, const Walk4& w, float (&v)[2]) {
+    body_residual<TP>(I, w, v);
+  });
   grid.sync();
   finish<2>(A, ACT_OUTER, [&](Ctl* ctl, const double (&t)[2]) { fin_residual(ctl, t[0], t[1], 0, 0); });
   grid.sync();
   int sweeps = 0;
   while (any_active(A, ACT_OUTER)) {
     // start of an inner solve: r scaled to unit norm, d = 0, z_0 = M r
-    phase<2>(A, ACT_OUTER, [&](const BInst& I, const Cell& c, float (&v)[2]) {
-      const float ri = lcg(I.r + c.i) * __ldcg(&I.ctl->rscale_f);
-      I.r[c.i] = ri;
-      I.dv[c.i] = 0.f;
-      const float zi = z_of(A, I, c, ri);
-      if (A.pc != TH_PC_NONE) I.zc[0][c.i] = zi;
-      v[0] = ri * ri;
-      v[1] = ri * zi;
+    phase<2>(A, ACT_OUTER, [&](const BInst& I, const BCtl& C, const Walk4& w, float (&v)[2]) {
+      for_layers(I, w, [&](long long i, int) {
+        float4 r = ld4(I.r + i);
+        r = make_float4(r.x * C.rscale, r.y * C.rscale, r.z * C.rscale, r.w * C.rscale);
+        st4(I.r + i, r);
+        st4(I.dv + i, z4());
+        const float4 z = z_of4(A, I, i, r);
+        if (A.pc != TH_PC_NONE) st4(I.zc[0] + i, z);
+        v[0] += dot4(r, r);
+        v[1] += dot4(r, z);
+      });
     });
     grid.sync();
     finish<2>(A, ACT_OUTER, [&](Ctl* ctl, const double (&t)[2]) { fin_update(ctl, t[0], t[1], true, rz_here); });
@@ -243,32 +323,44 @@ __global__ void __launch_bounds__(TH_NT) k_batched(BArgs A) {
     while (any_active(A, ACT_INNER) && sweeps < A.max_sweeps) {
       ++sweeps;
       // p_new = z + beta p_old, mu = A p_new, p^T mu
-      phase<1>(A, ACT_INNER, [&](const BInst& I, const Cell& c, float (&v)[1]) {
+      phase<1>(A, ACT_INNER, [&](const BInst& I, const BCtl& C, const Walk4& w, float (&v)[1]) {
         const float* z = zfinal(I);
         const float* po = I.p[parity];
-        const int first = __ldcg(&I.ctl->first);
-        const float beta = first ? 0.f : __ldcg(&I.ctl->beta_f);
-        auto pv = [&](long long j) -> float { return first ? lcg(z + j) : lcg(z + j) + beta * lcg(po + j); };
-        const float pi = pv(c.i);
-        float dg;
-        const float ai = stencil_row<float>(I.f32.gx, I.f32.gy, I.f32.gz, I.d, c, __ldg(&I.tab->s32[c.z]), pi, pv, dg);
-        I.p[1 - parity][c.i] = pi;
-        I.mu[c.i] = ai;
-        v[0] = pi * ai;
+        float* pn = I.p[1 - parity];
+        const int first = C.first;
+        const float beta = first ? 0.f : C.beta;
+        auto P4 = [&](long long i) -> float4 {
+          const float4 a = ld4(z + i);
+          if (first) return a;
+          const float4 b = ld4(po + i);
+          return make_float4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z, a.w + beta * b.w);
+        };
+        auto P1 = [&](long long j) -> float { return first ? z[j] : z[j] + beta * po[j]; };
+        walk(I, w, P4, P1, [&](long long i, int, const float4& pv, const float (&acc)[4], const float (&)[4]) {
+          st4(pn + i, pv);
+          st4(I.mu + i, make_float4(acc[0], acc[1], acc[2], acc[3]));
+#pragma unroll
+          for (int k = 0; k < 4; ++k) v[0] += cmp(pv, k) * acc[k];
+        });
       });
       grid.sync();
       finish<1>(A, ACT_INNER, [&](Ctl* ctl, const double (&t)[1]) { fin_pap(ctl, t[0]); });
       grid.sync();
       // d += alpha p, r -= alpha mu, z = M r
-      phase<2>(A, ACT_INNER, [&](const BInst& I, const Cell& c, float (&v)[2]) {
-        const float alpha = __ldcg(&I.ctl->alpha_f);
-        I.dv[c.i] = lcg(I.dv + c.i) + alpha * lcg(I.p[1 - parity] + c.i);
-        const float ri = lcg(I.r + c.i) - alpha * lcg(I.mu + c.i);
-        I.r[c.i] = ri;
-        const float zi = z_of(A, I, c, ri);
-        if (A.pc != TH_PC_NONE) I.zc[0][c.i] = zi;
-        v[0] = ri * ri;
-        v[1] = ri * zi;
+      phase<2>(A, ACT_INNER, [&](const BInst& I, const BCtl& C, const Walk4& w, float (&v)[2]) {
+        const float alpha = C.alpha;
+        const float* pn = I.p[1 - parity];
+        for_layers(I, w, [&](long long i, int) {
+          const float4 d = ld4(I.dv + i), p = ld4(pn + i), m = ld4(I.mu + i);
+          float4 r = ld4(I.r + i);
+          st4(I.dv + i, make_float4(d.x + alpha * p.x, d.y + alpha * p.y, d.z + alpha * p.z, d.w + alpha * p.w));
+          r = make_float4(r.x - alpha * m.x, r.y - alpha * m.y, r.z - alpha * m.z, r.w - alpha * m.w);
+          st4(I.r + i, r);
+          const float4 z = z_of4(A, I, i, r);
+          if (A.pc != TH_PC_NONE) st4(I.zc[0] + i, z);
+          v[0] += dot4(r, r);
+          v[1] += dot4(r, z);
+        });
       });
       grid.sync();
       finish<2>(A, ACT_INNER, [&](Ctl* ctl, const double (&t)[2]) { fin_update(ctl, t[0], t[1], false, rz_here); });
@@ -277,18 +369,27 @@ __global__ void __launch_bounds__(TH_NT) k_batched(BArgs A) {
       parity ^= 1;
     }
     // theta += ||r|| d, then the true FP64 residual decides the outer loop
-    phase<0>(A, ACT_OUTER, [&](const BInst& I, const Cell& c, float (&)[1]) {
-      I.theta[c.i] = lcg(I.theta + c.i) + __ldcg(&I.ctl->rnorm) * (double)lcg(I.dv + c.i);
+    phase<0>(A, ACT_OUTER, [&](const BInst& I, const BCtl& C, const Walk4& w, float (&)[1]) {
+      for_layers(I, w, [&](long long i0, int) {
+        const float4 d = ld4(I.dv + i0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) I.theta[i0 + k] += C.rnorm * (double)cmp(d, k);
+      });
     });
     grid.sync();
-    phase<2>(A, ACT_OUTER, [&](const BInst& I, const Cell& c, float (&v)[2]) { body_residual<TP>(I, c, v); });
+    phase<2>(A, ACT_OUTER, [&](const BInst& I, const BCtl&, const Walk4& w, float (&v)[2]) {
+      body_residual<TP>(I, w, v);
+    });
     grid.sync();
     finish<2>(A, ACT_OUTER, [&](Ctl* ctl, const double (&t)[2]) { fin_residual(ctl, t[0], t[1], 0, 1); });
     grid.sync();
     if (sweeps >= A.max_sweeps) break;
   }
-  phase<0>(A, ACT_ALL, [&](const BInst& I, const Cell& c, float (&)[1]) {
-    I.T_out[c.i] = lcg(I.theta + c.i) + I.t_amb;
+  phase<0>(A, ACT_ALL, [&](const BInst& I, const BCtl&, const Walk4& w, float (&)[1]) {
+    for_layers(I, w, [&](long long i0, int) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) I.T_out[i0 + k] = I.theta[i0 + k] + I.t_amb;
+    });
   });
 }
 
@@ -351,10 +452,10 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
     BInst& I = hi[i];
     std::memset(&I, 0, sizeof(I));
     I.d = grid_dims(g);
-    I.tbx = (g->nx + TH_BX - 1) / TH_BX;
-    I.tby = (g->ny + TH_BY - 1) / TH_BY;
+    I.tbx = (g->nx + 4 * TH_BX - 1) / (4 * TH_BX);
     I.tile0 = ntiles;
-    I.ntiles = I.tbx * I.tby * g->L;
+    I.ntiles = I.tbx * ((g->ny + TH_BY4 - 1) / TH_BY4);
+    I.uni = g->uniform ? 1 : 0;
     ntiles += I.ntiles;
     for (int t = 0; t < I.ntiles; ++t) tile_inst.push_back(i);
     I.f32 = g->f32;
@@ -424,7 +525,7 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
   TH_CUDA(cudaGetDevice(&dev));
   TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   void* fn = power_dtype == TH_F64 ? (void*)k_batched<double> : (void*)k_batched<float>;
-  TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH_NT, 0));
+  TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH_BX * TH_BY4, 0));
   if (per_sm < 1) return th_fail(TH_ECUDA, "batched kernel cannot be resident");
   const int nblocks = std::max(1, std::min(ntiles, sms * per_sm));
   void* args[] = {&A};
@@ -433,7 +534,7 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
   TH_CUDA(cudaEventCreate(&e1));
   struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
   TH_CUDA(cudaEventRecord(e0, s));
-  TH_CUDA(cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(TH_BX, TH_BY), args, 0, s));
+  TH_CUDA(cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(TH_BX, TH_BY4), args, 0, s));
   TH_CUDA(cudaEventRecord(e1, s));
   TH_CUDA(cudaStreamSynchronize(s));
   float ms = 0.f;
@@ -470,16 +571,18 @@ extern "C" th_status thermal_solve_batched(thermal_grid* const* grids, int n, co
     TH_TRY(validate_opts(opts));
     if (power_dtype != TH_F32 && power_dtype != TH_F64) return th_fail(TH_EINVAL, "power dtype");
     if (n == 0) return TH_OK;
-    bool all_dev = true;
+    bool all_dev = true, v4 = true;
     for (int i = 0; i < n; ++i) {
       if (!grids[i] || !power[i] || !T[i]) return th_fail(TH_EINVAL, "instance %d has a NULL pointer", i);
       if (!grids[i]->geom) return th_fail(TH_ESTATE, "instance %d has no geometry", i);
       all_dev = all_dev && is_device_pointer(power[i]) && is_device_pointer(T[i]);
+      v4 = v4 && grids[i]->nx % 4 == 0 && ((uintptr_t)power[i] % 16) == 0;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // the persistent kernel covers the mixed path with the point-wise preconditioners;
-    // other combinations run the instances one after another through the single-grid solver
-    const bool fused = all_dev && opts->precision != TH_PREC_FP64 &&
+    // the persistent kernel covers the mixed path with the Jacobi, Chebyshev and no
+    // preconditioner on grids with nx % 4 == 0; other combinations run the instances
+    // one after another through the single-grid solver
+    const bool fused = all_dev && v4 && opts->precision != TH_PREC_FP64 &&
                        (opts->precond == TH_PC_NONE || opts->precond == TH_PC_JACOBI || opts->precond == TH_PC_CHEB) &&
                        opts->batched_mode == 0;
     if (fused) return persistent(grids, n, power, power_dtype, T, opts, stats, s);

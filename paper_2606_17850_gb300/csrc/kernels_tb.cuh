@@ -1,16 +1,16 @@
 // Temporal blocking of the Chebyshev preconditioner (layer-uniform grids).
 //
 // The preconditioner's steps need no reductions (Sec. 4.3: only SpMVs and AXPYs),
-// so several of them can run inside one kernel on a tile.  A tile is TB_TX x TY
-// columns (all layers) grown by a TB_H-cell halo in x and y.  Each thread owns one
+// so several of them can run inside one kernel on a tile.  For S steps a tile is
+// (32 - 2S) x (EY - 2S) columns (all layers) grown by an S-cell halo in x and y.  Each thread owns one
 // column of the grown tile and keeps that column's z_m, z_{m-1} and r in registers;
 // per step it publishes z_m into a shared-memory plane, reads its four in-plane
 // neighbours from there (the z neighbours are its own registers) and forms z_{m+1}.
 // The region whose neighbours are still valid shrinks by one cell per step, so
-// after S <= TB_H steps the tile interior holds z_{m+S}.
+// after the S <= TB_H steps the tile interior holds z_{m+S}.
 //
 // Blackwell data movement: the kernel is persistent (one CTA per SM walks the tile
-// list) and the next tile's three input boxes (z_m, z_{m-1}, r: TB_EX x EY x L
+// list) and the next tile's three input boxes (z_m, z_{m-1}, r: TB_BW x EY x L
 // floats each) are fetched by the tensor memory accelerator into a staging buffer
 // while the current tile computes; completion is tracked by an mbarrier.  Two plane
 // buffers alternate between steps, so a step needs a single CTA barrier.
@@ -31,12 +31,11 @@
 
 #include "common.cuh"
 
-#define TB_H 4
-#define TB_EX 32                // grown tile width: one warp per row
-#define TB_TX (TB_EX - 2 * TB_H)  // interior columns per tile
-// bounded mbarrier wait: try_wait suspends for a hardware time slice per attempt,
-// so this limit is on the order of a second
-#define TB_WAIT_LIMIT (1 << 20)
+#define TB_H 4    // most steps per launch
+#define TB_EX 32  // grown tile width in threads: one warp per row
+#define TB_BW 36  // staged box width: the grown tile's first column rounded down to 16 bytes, + 32
+// bounded mbarrier wait: give up after about one second of device time
+#define TB_WAIT_NS 1000000000ull
 
 template <int LMAX>
 struct TBParams {
@@ -69,10 +68,19 @@ __device__ __forceinline__ bool tb_mbar_try(unsigned long long* bar, unsigned pa
   return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long tb_clock_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// true when the phase completed; false after about TB_WAIT_NS of device time
 __device__ __forceinline__ bool tb_mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (int it = 0; it < TB_WAIT_LIMIT; ++it)
-    if (tb_mbar_try(bar, parity)) return true;
-  return false;
+  if (tb_mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = tb_clock_ns();
+  while (!tb_mbar_try(bar, parity))
+    if (tb_clock_ns() - t0 > TB_WAIT_NS) return false;
+  return true;
 }
 
 __device__ __forceinline__ void tb_tma_3d(float* dst, const CUtensorMap* map, int x, int y, int z,
@@ -88,12 +96,13 @@ __device__ __forceinline__ void tb_tma_3d(float* dst, const CUtensorMap* map, in
 // plus room to align the staging boxes to 128 bytes
 template <int LMAX, int EY>
 constexpr size_t tb_smem_bytes() {
-  return (size_t)(3 + 2) * LMAX * EY * TB_EX * sizeof(float) + 16 + 128;
+  return ((size_t)3 * LMAX * EY * TB_BW + (size_t)2 * LMAX * EY * TB_EX) * sizeof(float) + 16 + 128;
 }
 
-// Layers L..LMAX-1 (when the stack has fewer than LMAX layers) are carried as
-// zeros: their coefficients and inverse diagonal are 0, so they stay 0 and the
-// step loop needs no per-layer guard.
+// STEPS steps with a halo of STEPS cells: the interior is (32 - 2 STEPS) x
+// (EY - 2 STEPS) columns.  Layers L..LMAX-1 (when the stack has fewer than LMAX
+// layers) are carried as zeros: their coefficients and inverse diagonal are 0, so
+// they stay 0 and the step loop needs no per-layer guard.
 template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST>
 __global__ void __launch_bounds__(TB_EX * EY, 1)
     k_cheb_tb(Dims d, int ntx, int ntiles, int has_prev, Ctl* ctl,
@@ -101,17 +110,19 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
               const __grid_constant__ CUtensorMap m_r, float* __restrict__ out_cur, float* __restrict__ out_prev,
               const __grid_constant__ TBParams<LMAX> P, double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->done)) return;
-  constexpr int TY = EY - 2 * TB_H;
+  constexpr int H = STEPS;
+  constexpr int TX = TB_EX - 2 * H, TY = EY - 2 * H;  // interior of a tile
   constexpr int PL = EY * TB_EX;  // floats per layer plane
+  constexpr int SL = EY * TB_BW;  // floats per staged layer
   extern __shared__ __align__(128) float tb_dyn[];
   float* tb_sm = tb_dyn + (((128u - (tb_smem(tb_dyn) & 127u)) & 127u) >> 2);  // 128-byte aligned
-  float* stage = tb_sm;                    // [3][LMAX][EY][TB_EX]: z_m, z_{m-1}, r
-  float* plane = tb_sm + 3 * LMAX * PL;    // [2][LMAX][EY][TB_EX]
-  unsigned long long* bar = (unsigned long long*)(tb_sm + 5 * LMAX * PL);
+  float* stage = tb_sm;                    // [3][LMAX][EY][TB_BW]: z_m, z_{m-1}, r
+  float* plane = tb_sm + 3 * LMAX * SL;    // [2][LMAX][EY][TB_EX]
+  unsigned long long* bar = (unsigned long long*)(plane + 2 * LMAX * PL);
   const int L = d.L;
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
-  const unsigned box_bytes = (unsigned)(L * PL * sizeof(float));
+  const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
   const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
 
   if (tid == 0) {
@@ -119,12 +130,14 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
+  // the box starts at the grown tile's first column rounded down to a multiple of 4
+  // cells (a 16-byte boundary, as the tensor copy requires)
   auto issue = [&](int t) {
-    const int x0 = (t % ntx) * TB_TX - TB_H, y0 = (t / ntx) * TY - TB_H;
+    const int xa = ((t % ntx) * TX - H) & ~3, y0 = (t / ntx) * TY - H;
     tb_mbar_expect(bar, tx_bytes);
-    tb_tma_3d(stage, &m_cur, x0, y0, 0, bar);
-    if (has_prev) tb_tma_3d(stage + LMAX * PL, &m_prev, x0, y0, 0, bar);
-    tb_tma_3d(stage + 2 * LMAX * PL, &m_r, x0, y0, 0, bar);
+    tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
+    if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+    tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
 
@@ -141,17 +154,19 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       break;
     }
     parity ^= 1u;
-    const int gx = (t % ntx) * TB_TX - TB_H + ex;
-    const int gy = (t / ntx) * TY - TB_H + ey;
+    const int x0 = (t % ntx) * TX - H;
+    const int gx = x0 + ex;
+    const int gy = (t / ntx) * TY - H + ey;
+    const int st = ey * TB_BW + ex + (x0 - (x0 & ~3));  // this column in a staged layer
     const bool inside = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
     float cur[LMAX], prv[LMAX], rr[LMAX], inv[LMAX];
     const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
       const bool on = z < L;
-      cur[z] = on ? stage[z * PL + tid] : 0.f;
-      prv[z] = (on && has_prev) ? stage[(LMAX + z) * PL + tid] : 0.f;
-      rr[z] = on ? stage[(2 * LMAX + z) * PL + tid] : 0.f;
+      cur[z] = on ? stage[z * SL + st] : 0.f;
+      prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
+      rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
       inv[z] = P.invd[nxf + 3 * nyf][z];
     }
     __syncthreads();  // staging buffer consumed by every thread
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       }
     }
     // the interior columns hold z_{m+STEPS} (cur) and z_{m+STEPS-1} (prv)
-    const bool interior = inside && ex >= TB_H && ex < TB_H + TB_TX && ey >= TB_H && ey < TB_H + TY;
+    const bool interior = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
     if (interior) {
       const long long base = (long long)gx + (long long)d.nx * gy;
 #pragma unroll

@@ -456,7 +456,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensormap_encoder() {
 }
 
 // 3-D map of one FP32 field (x fastest, then y, then layer) with a box of
-// TB_EX x ey x L cells; cells outside the grid read as zero.
+// TB_BW x ey x L cells; cells outside the grid read as zero.
 static th_status tb_map(CUtensorMap* m, const Dims& d, const float* base, int ey) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensormap_encoder();
   if (!enc) return th_fail(TH_ECUDA, "cuTensorMapEncodeTiled is not available");
@@ -464,7 +464,7 @@ static th_status tb_map(CUtensorMap* m, const Dims& d, const float* base, int ey
     return th_fail(TH_EINVAL, "tensor map needs a 16-byte aligned base and nx %% 4 == 0");
   const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.L};
   const cuuint64_t strides[2] = {(cuuint64_t)d.nx * sizeof(float), (cuuint64_t)d.pxy * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)TB_EX, (cuuint32_t)ey, (cuuint32_t)d.L};
+  const cuuint32_t box[3] = {(cuuint32_t)TB_BW, (cuuint32_t)ey, (cuuint32_t)d.L};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -489,7 +489,7 @@ static int sm_count() {
 template <int LM, int EY, int ST, bool SC, bool LA>
 static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   thermal_grid* g = P.g;
-  constexpr int TY = EY - 2 * TB_H;
+  constexpr int TX = TB_EX - 2 * ST, TY = EY - 2 * ST;
   float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
   TBParams<LM> prm;
   std::memset(&prm, 0, sizeof(prm));
@@ -522,7 +522,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], EY));
   TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], EY));
   TH_TRY(tb_map(&mr, P.d, V.r, EY));
-  const int ntx = (P.d.nx + TB_TX - 1) / TB_TX;
+  const int ntx = (P.d.nx + TX - 1) / TX;
   const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
   const size_t smem = tb_smem_bytes<LM, EY>();
   TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, EY, ST, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1283,13 +1283,13 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 13) return th_fail(TH_EINVAL, "invalid argument");
-  if (kernel == 13 && !(g->uniform && g->nx % 4 == 0))
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 15) return th_fail(TH_EINVAL, "invalid argument");
+  if (kernel >= 13 && !(g->uniform && g->nx % 4 == 0))
     return th_fail(TH_EINVAL, "fused Chebyshev steps need a layer-uniform grid with nx %% 4 == 0");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
-  o.precond = (kernel == 13) ? TH_PC_CHEB : TH_PC_JACOBI;
+  o.precond = (kernel >= 13) ? TH_PC_CHEB : TH_PC_JACOBI;
   o.cheb_degree = 5;  // one chunk of four fused steps
   o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64 : TH_PREC_MIXED_IR;
   Plan P;
@@ -1318,7 +1318,13 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   const float c1 = 0.5f, c2 = 0.5f;
   auto launch = [&]() -> th_status {
     const bool uni = g->uniform && kernel < 9;  // ids 9..12: the per-face variants
-    if (kernel == 13) return tb_chain(P, V, s);
+    if (kernel >= 13) {
+      // one inner chunk: z_m, z_{m-1}, r in; z_{m+S}, z_{m+S-1} out (no reduction)
+      const Plan::Chunk c{kernel == 13 ? 4 : (kernel == 14 ? 2 : 3), 1, 0, 1, 2, 3};
+      if (P.tb_lmax == 8) return P.scaled ? tb_chunk<8, 32, true>(P, V, s, c, false)
+                                          : tb_chunk<8, 32, false>(P, V, s, c, false);
+      return P.scaled ? tb_chunk<12, 24, true>(P, V, s, c, false) : tb_chunk<12, 24, false>(P, V, s, c, false);
+    }
     const int kk = (kernel >= 9) ? (int[]){1, 3, 8, 0}[kernel - 9] : kernel;
     switch (kk) {
       case 0:

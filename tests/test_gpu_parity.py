@@ -260,19 +260,20 @@ def test_preconditioner_apply(pc, scaled, nx):
 
 @pytest.mark.parametrize("k", [2, 5, 8, 12])
 @pytest.mark.parametrize("dt", [0.0, 1e-4])
-def test_fused_chebyshev_equals_stepwise(k, dt):
-    """Temporal blocking (up to 4 steps per launch in shared memory) computes the same
-    polynomial as one launch per step: tiles with ragged x/y tails, 1..3 chunks."""
-    st = ti.stack_c2()
+@pytest.mark.parametrize("mk", ["c2", "c1", "mol"])
+def test_fused_chebyshev_equals_stepwise(k, dt, mk):
+    """Temporal blocking (1..4 steps per launch, TMA-staged tiles) computes the same
+    polynomial as one launch per step: tiles with ragged x/y tails, 1..3 chunks,
+    8 layers, 4 layers (zero-padded to 8) and 10 layers (the 12-layer variant)."""
+    st = STACKS[mk]()
     nx, ny = 76, 37           # nx % 32 != 0 and ny % 16 != 0: partial tiles on both axes
     g = grid_of(nx, ny, st)
     r = cuda(ti.random_vector(nx * ny * st.L, 5).astype(np.float32))
     z1 = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=1)
-    zf = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=0)
-    z3 = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=3)
     scale = z1.abs().max().item()
-    assert (zf - z1).abs().max().item() <= 1e-6 * scale
-    assert (z3 - z1).abs().max().item() <= 1e-6 * scale
+    for fuse in (0, 2, 3, 4):
+        zf = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=fuse)
+        assert (zf - z1).abs().max().item() <= 1e-6 * scale, fuse
 
 
 # ----------------------------------------------------------------- A5/A6: steady solves
@@ -441,6 +442,33 @@ def test_batched_matches_oracle(mode, pc):
         ref = osolve.steady(inst.nx, inst.ny, inst.stack, inst.power.astype(np.float64))
         assert s["status"] == 0 and s["rel_res"] <= 1e-10
         assert osolve.rise_relative_error(T.cpu().numpy(), ref, inst.stack.t_amb) <= 1e-6
+
+
+def test_batched_conductivity_map_and_ragged_tiles():
+    """One persistent launch over instances with a per-cell conductivity map (per-face
+    kernels), ragged 128 x 8 tiles (nx = 132, ny = 13) and the layer-table kernels;
+    an instance with nx % 4 != 0 sends the whole batch through the sequential path."""
+    from paper_2606_17850_gb300 import solve_batched
+    shapes = [(132, 13, ti.stack_c2()), (20, 36, ti.stack_c1()), (44, 9, ti.stack_mol())]
+    for extra in ([], [(21, 10, ti.stack_c1())]):
+        cases = shapes + extra
+        grids, powers, Ts, refs = [], [], [], []
+        for j, (nx, ny, st) in enumerate(cases):
+            P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, 60 + j)] * len(st.power_layers()),
+                               np.float64)
+            g = grid_of(nx, ny, st)
+            kc = None
+            if j == 0:
+                kc = _kmap(st, nx, ny, 11)
+                g.set_conductivity_map(cuda(kc))
+            grids.append(g)
+            powers.append(cuda(P.astype(np.float32)))
+            Ts.append(torch.empty(nx * ny * st.L, dtype=torch.float64, device="cuda"))
+            refs.append(osolve.steady(nx, ny, st, P.astype(np.float32).astype(np.float64), k_cell=kc))
+        stats = solve_batched(grids, powers, Ts, tol_rel=1e-10, precond="cheb", cheb_degree=8)
+        for (nx, ny, st), T, s, ref in zip(cases, Ts, stats, refs):
+            assert s["status"] == 0 and s["rel_res"] <= 1e-10
+            assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
 
 
 def test_batched_initial_guess_and_repeat():
