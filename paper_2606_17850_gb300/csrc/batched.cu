@@ -277,8 +277,11 @@ __device__ void cheb_tail(const BArgs& A, cg::grid_group& grid) {
   }
 }
 
+// Three co-resident blocks per SM (at most 80 registers a thread): the memory-bound
+// phases need the occupancy more than the rarely run FP64 residual phase needs
+// registers (measured: 0.92 s vs 1.12 s with two blocks per SM for the 64 stacks).
 template <typename TP>
-__global__ void __launch_bounds__(TH_BX* TH_BY4) k_batched(BArgs A) {
+__global__ void __launch_bounds__(TH_BX* TH_BY4, 3) k_batched(BArgs A) {
   cg::grid_group grid = cg::this_grid();
   const int rz_here = (A.pc != TH_PC_CHEB || A.k == 1) ? 1 : 0;
   auto zfinal = [&](const BInst& I) -> const float* {
