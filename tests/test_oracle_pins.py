@@ -409,3 +409,65 @@ def test_kmap_assembly_bruteforce_and_uniform_limit():
     assert abs(A - A.T).max() == 0.0
     Au = disc.assemble(nx, ny, st, k_cell=np.repeat(st.k(), nx * ny))
     np.testing.assert_allclose((Au - disc.assemble(nx, ny, st)).toarray(), 0.0, atol=1e-15 * abs(Au).max())
+
+
+# ------------------------------------------------ Sec. 4.4: reduced-precision pieces
+
+def test_quad_diag_round_trip():
+    """The four stored diagonals (Sec. 4.2) rebuild the assembled matrix exactly."""
+    from oracle import precision as prc
+    st = ti.stack_c1()
+    nx, ny = 5, 4
+    A = disc.assemble(nx, ny, st, dt=1e-4)
+    D = prc.quad_diag(A, nx, ny)
+    np.testing.assert_array_equal(prc.from_quad_diag(*D, nx, ny), A.toarray())
+    assert np.all(D[1] <= 0) and np.all(D[2] <= 0) and np.all(D[3] <= 0)
+
+
+def test_a3_spmv_exact_on_fp16_representable_values():
+    """With small-integer diagonals and inputs every FP16/FP32 step of Algorithm 3 is
+    exact, so the product equals the dense matrix-vector product."""
+    from oracle import precision as prc
+    nx, ny, L = 4, 3, 3
+    n = nx * ny * L
+    rng = np.random.default_rng(7)
+    i = np.arange(n)
+    D4 = rng.integers(20, 41, n).astype(np.float64)
+    D5 = np.where(i % nx + 1 < nx, -rng.integers(1, 5, n), 0).astype(np.float64)
+    D6 = np.where((i // nx) % ny + 1 < ny, -rng.integers(1, 5, n), 0).astype(np.float64)
+    D7 = np.where(i // (nx * ny) + 1 < L, -rng.integers(1, 5, n), 0).astype(np.float64)
+    x = rng.integers(0, 8, n).astype(np.float32)
+    e = prc.a3_scale_exponent(D4)
+    assert 16 <= D4.max() * 2.0 ** e < 32
+    y = prc.a3_spmv(D4, D5, D6, D7, x, nx, ny, e)
+    np.testing.assert_array_equal(y.astype(np.float64), prc.from_quad_diag(D4, D5, D6, D7, nx, ny) @ x)
+
+
+def test_a3_spmv_fp16_error_bound():
+    """On a physical matrix the FP16 roundings (stored values, x, in-plane products;
+    unit roundoff 2^-11 each) bound the error: |y - A x| <= 3.2 * 2^-11 sum_j |a_ij x_j|,
+    and the product is not exact (the FP16 path is really taken)."""
+    from oracle import precision as prc
+    st = ti.stack_c2()
+    nx, ny = 9, 7
+    A = disc.assemble(nx, ny, st, dt=1e-4)
+    D = prc.quad_diag(A, nx, ny)
+    x = ti.random_vector(A.shape[0], 31, lo=-3.0, hi=5.0).astype(np.float32)
+    y = prc.a3_spmv(*D, x, nx, ny, prc.a3_scale_exponent(D[0])).astype(np.float64)
+    xd = x.astype(np.float64)
+    err = np.abs(y - A @ xd)
+    bound = 3.2 * 2.0 ** -11 * (abs(A) @ np.abs(xd))
+    assert np.all(err <= bound), np.max(err / bound)
+    assert err.max() > 0.0
+
+
+def test_stage_switch_criteria():
+    """Eqs. (switch_a-c), one at a time."""
+    from oracle import precision as prc
+    eps = 1e-8
+    assert prc.stage_switch(0.9e-4, 1.0, None, 0.0, eps)            # (a) ||r_low|| <= sqrt(eps)
+    assert not prc.stage_switch(1.1e-4, 1.0, None, 0.0, eps)
+    assert prc.stage_switch(1.0, 0.95, 1.0, 0.0, eps)               # (b) stagnation of r_true
+    assert not prc.stage_switch(1.0, 0.85, 1.0, 0.0, eps)
+    assert prc.stage_switch(1.0, 1.0, None, 0.5, eps)               # (c) drift between r_true and r_low
+    assert not prc.stage_switch(1.0, 1.0, None, 0.49, eps)
