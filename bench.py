@@ -59,6 +59,10 @@ KERNEL_BYTES = {
     "residual_f64": 48,  # gx gy gz (24) + theta, theta_n (16) + P f32 (4) + r f32 (4)
     "stencil_f64": 40,   # gx gy gz (24) + x (8) + y (8)
     "cheb_f64": 64,      # gx gy gz (24) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)
+    # the paper's adaptive mixed precision (Sec. 4.4)
+    "ad_cheb_a3": 28,    # A3 in FP16 (8) + z_m, z_{m-1}, r, 1/diag (16) + z_{m+1} (4)
+    "ad_spmv_early": 32, # D4, gx gy gz FP32 (16) + p (8) + mu (8)
+    "ad_spmv_late": 48,  # D4, gx gy gz FP64 (32) + p (8) + mu (8)
 }
 DOMINANT = "cheb_tb4"
 
@@ -78,6 +82,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-stack batched section")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 2048x2048x10 adjoint section")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the trajectory with the paper's adaptive mixed-precision PCG")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
@@ -370,6 +376,26 @@ def main():
         result["speedup_mixed_vs_fp64"] = (ms64 / nsteps) / value
         result["accuracy"] = {"max_abs_diff_mixed_vs_fp64_K": err * rise,
                               "max_rel_diff_vs_rise": err}
+
+    # the paper's adaptive mixed-precision PCG (stage switch + hot restart) on the same trajectory
+    if not args.no_adaptive:
+        oad = dict(opts, precision="adaptive")
+        Tad = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
+        trajectory(oad, Tad, maps)  # warm-up (graph build)
+        barrier()
+        e0.record(stream)
+        sad = trajectory(oad, Tad, maps)
+        e1.record(stream)
+        barrier()
+        msad = e0.elapsed_time(e1)
+        rise = (Tad - st.t_amb).abs().max().item()
+        result["adaptive_gpu"] = {
+            "value": msad / nsteps, "unit": UNIT, "ms_per_trajectory": msad, "inner_it": sad["inner_it"],
+            "stage_switches": sad["stage_switches"], "final_rel_res": sad["rel_res"],
+            "max_abs_diff_vs_mixed_K": (Tad - T_mixed).abs().max().item(),
+            "note": "FP64 PCG, early stage FP64/32 SpMV, late stage FP64 SpMV (switch on Eqs. switch_a-c, hot "
+                    "restart), Chebyshev preconditioner in FP32 with the FP32/16 product of Algorithm 3"}
+        result["speedup_mixed_vs_adaptive"] = (msad / nsteps) / value
 
     # live per-kernel timings (CUDA events on the launching stream) -> roofline
     if not args.no_kernels:

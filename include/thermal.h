@@ -59,7 +59,12 @@ typedef enum th_status {
 typedef enum th_precision {
   TH_PREC_FP64 = 0,          /* plain FP64 PCG: FP64 coefficients, vectors, arithmetic   */
   TH_PREC_MIXED_IR = 1,      /* FP32 inner PCG + FP64 iterative refinement               */
-  TH_PREC_MIXED_IR_BF16 = 2  /* as MIXED_IR, preconditioner reads BF16 coefficients      */
+  TH_PREC_MIXED_IR_BF16 = 2, /* as MIXED_IR, preconditioner reads BF16 coefficients      */
+  TH_PREC_ADAPTIVE = 3       /* the paper's adaptive mixed-precision PCG (Sec. 4.4): FP64  */
+                             /* PCG whose SpMV reads FP32 coefficients (FP64 arithmetic)  */
+                             /* in an early stage and FP64 coefficients after the switch  */
+                             /* of Eqs. (switch_a-c) and a hot restart; the preconditioner */
+                             /* runs in FP32 with the FP32/16 product of Algorithm 3      */
 } th_precision;
 
 typedef enum th_precond {
@@ -93,7 +98,10 @@ typedef struct thermal_solve_opts {
                        /* start), 1 linear extrapolation 2 T_n - T_{n-1} inside a step loop (0) */
   int cheb_fuse;       /* Chebyshev steps per launch on layer-uniform grids (temporal blocking */
                        /* in shared memory): 0 auto (4), 1 one step per launch, 2..4 (0)      */
-  int reserved[5];
+  int ad_check;        /* ADAPTIVE: PCG iterations between true-residual evaluations of the   */
+                       /* switching criterion, rounded up to even; 0: 20 steady, 6 transient  */
+                       /* (the paper's 20 and 5 on the two-iteration loop body) (0)           */
+  int reserved[4];
 } thermal_solve_opts;
 
 typedef struct thermal_solve_stats {
@@ -107,7 +115,8 @@ typedef struct thermal_solve_stats {
   double lam_min;      /* spectral interval used by the Chebyshev preconditioner              */
   double lam_max;
   int steps;           /* time steps taken (transient calls)                                  */
-  int reserved[7];
+  int stage_switches;  /* ADAPTIVE: early-to-late switches (hot restarts), summed over steps  */
+  int reserved[6];
 } thermal_solve_stats;
 
 /* ------------------------------------------------------------------ misc */
@@ -180,7 +189,12 @@ th_status thermal_grid_faces(thermal_grid* g, double dt, double* gx, double* gy,
  * stored diagonals).  A is the steady matrix when dt <= 0, else the transient one.
  * precision TH_PREC_FP64: x, y are double and the FP64 coefficients are used;
  * TH_PREC_MIXED_IR: x, y are float, FP32 coefficients, FP32 arithmetic;
- * TH_PREC_MIXED_IR_BF16: x, y are float, BF16 coefficients, FP32 arithmetic.
+ * TH_PREC_MIXED_IR_BF16: x, y are float, BF16 coefficients, FP32 arithmetic;
+ * TH_PREC_ADAPTIVE: x, y are float, Algorithm 3's FP32/16 product (Sec. 4.4): the
+ *   Quad-Diag diagonals scaled by a power of two 2^e (max D4 2^e in [16, 32)) and
+ *   rounded to FP16; D4 and D7 promoted to FP32 and multiplied in FP32, D5 and D6
+ *   multiplied with FP16(x) in FP16, every product added to the FP32 result in the
+ *   order D4, D5 (x+1, x-1), D6 (y+1, y-1), D7 (z+1, z-1); y = 2^-e times the sum.
  * x, y: device, n_cells elements, must not overlap.  Asynchronous on `stream`.
  */
 th_status thermal_apply(thermal_grid* g, double dt, int precision, const void* x, void* y,
@@ -246,6 +260,9 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  *  13, 14, 15  four, two, three Chebyshev steps fused in one launch (temporal
  *      blocking; an inner chunk reading z_m, z_{m-1}, r and writing z_{m+S},
  *      z_{m+S-1}); layer-uniform grids with nx % 4 == 0, else TH_EINVAL
+ *  16  FP32 Chebyshev step with Algorithm 3's FP32/16 product (adaptive path)
+ *  17  adaptive path, early stage: FP64 mu = A p with FP32 coefficients + p^T mu
+ *  18  adaptive path, late stage: the same with FP64 coefficients
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

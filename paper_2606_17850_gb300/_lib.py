@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libthermal.so")
 TH_OK, TH_EINVAL, TH_ENOMEM, TH_ECUDA, TH_ENOCONV, TH_EBREAKDOWN, TH_ENONFINITE, TH_ESTATE = range(8)
 STATUS_NAMES = ["TH_OK", "TH_EINVAL", "TH_ENOMEM", "TH_ECUDA", "TH_ENOCONV", "TH_EBREAKDOWN",
                 "TH_ENONFINITE", "TH_ESTATE"]
-TH_PREC_FP64, TH_PREC_MIXED_IR, TH_PREC_MIXED_IR_BF16 = 0, 1, 2
+TH_PREC_FP64, TH_PREC_MIXED_IR, TH_PREC_MIXED_IR_BF16, TH_PREC_ADAPTIVE = 0, 1, 2, 3
 TH_PC_NONE, TH_PC_JACOBI, TH_PC_CHEB, TH_PC_ZLINE = 0, 1, 2, 3
 TH_F32, TH_F64 = 0, 1
 
@@ -36,7 +36,8 @@ class SolveOpts(C.Structure):
         ("batched_mode", C.c_int),
         ("guess", C.c_int),
         ("cheb_fuse", C.c_int),
-        ("reserved", C.c_int * 5),
+        ("ad_check", C.c_int),
+        ("reserved", C.c_int * 4),
     ]
 
 
@@ -52,7 +53,8 @@ class SolveStats(C.Structure):
         ("lam_min", C.c_double),
         ("lam_max", C.c_double),
         ("steps", C.c_int),
-        ("reserved", C.c_int * 7),
+        ("stage_switches", C.c_int),
+        ("reserved", C.c_int * 6),
     ]
 
     def as_dict(self):

@@ -13,7 +13,8 @@ import torch
 
 from . import _lib as L
 
-PRECISION = {"fp64": L.TH_PREC_FP64, "mixed": L.TH_PREC_MIXED_IR, "mixed_bf16": L.TH_PREC_MIXED_IR_BF16}
+PRECISION = {"fp64": L.TH_PREC_FP64, "mixed": L.TH_PREC_MIXED_IR, "mixed_bf16": L.TH_PREC_MIXED_IR_BF16,
+             "adaptive": L.TH_PREC_ADAPTIVE}
 PRECOND = {"none": L.TH_PC_NONE, "jacobi": L.TH_PC_JACOBI, "cheb": L.TH_PC_CHEB, "zline": L.TH_PC_ZLINE}
 
 
@@ -120,7 +121,8 @@ class ThermalGrid:
     KERNELS = {"stencil_f32": 0, "cheb_f32": 1, "cheb_bf16": 2, "spmv_dot_f32": 3, "update_f32": 4,
                "residual_f64": 5, "stencil_f64": 6, "cheb_f64": 7, "residual_df": 8,
                "cheb_f32_faces": 9, "spmv_dot_f32_faces": 10, "residual_df_faces": 11, "stencil_f32_faces": 12,
-               "cheb_tb4": 13, "cheb_tb2": 14, "cheb_tb3": 15}
+               "cheb_tb4": 13, "cheb_tb2": 14, "cheb_tb3": 15,
+               "ad_cheb_a3": 16, "ad_spmv_early": 17, "ad_spmv_late": 18}
 
     def kernel_time(self, kernel, reps=50, dt=0.0):
         """Average duration (ms) of one launch of a hot kernel on this grid (CUDA events)."""

@@ -89,6 +89,13 @@ struct Ctl {
   float rscale_f;          // 1/||r||
   float rnorm_hi, rnorm_lo;  // ||r|| as a double-float
   float pad_f;
+  // adaptive mixed precision (Sec. 4.4): stage 0 early (FP32-stored SpMV), 1 late (FP64)
+  int ad_stage;
+  int ad_switches;      // early-to-late switches, summed over systems
+  double ad_rs;         // power of two applied to r when it is rounded to FP32 for M^-1
+  double ad_zs;         // 1 / ad_rs: scale of the FP32 preconditioner output
+  double ad_rs_next;    // ad_rs for the next residual (from its norm)
+  double ad_rtrue_prev; // ||b - A x|| at the previous criterion evaluation (0: none)
 };
 
 template <typename T> __device__ __forceinline__ T ctl_alpha(const Ctl* c);
@@ -185,6 +192,64 @@ __device__ __forceinline__ void fin_residual(Ctl* ctl, double rr, double bb, int
   } else {
     ctl->inner_rel = 0.5 * ctl->tol_rel / rel;
   }
+}
+
+// power of two nearest below 1/v (1 for v <= 0): a scale that is exact in FP64
+__device__ __forceinline__ double pow2_inv(double v) {
+  if (!(v > 0.0) || !isfinite(v)) return 1.0;
+  int e;
+  frexp(v, &e);  // v = m 2^e, m in [0.5, 1)
+  return ldexp(1.0, 1 - e);
+}
+
+// Adaptive mixed precision: last-block decision on the true FP64 residual at the
+// start of a system (count_outer = 0) and at every hot restart (count_outer = 1).
+// The early stage runs until ||r|| <= sqrt(tol) ||b|| (Eq. switch_a) unless the
+// criterion kernel ends it first; every restart after it is in the late stage.
+__device__ __forceinline__ void fin_residual_ad(Ctl* ctl, double rr, double bb, int count_outer) {
+  fin_residual(ctl, rr, bb, 1, count_outer);
+  if (ctl->outer_done) return;
+  if (count_outer && ctl->ad_stage == 0) {  // hot restart into the late stage
+    ctl->ad_stage = 1;
+    ctl->ad_switches += 1;
+  }
+  const double rel = ctl->rel_res;
+  if (ctl->ad_stage == 0) {
+    const double want = sqrt(ctl->tol_rel) / rel;
+    if (want >= 1.0) {  // already at the late-stage level: switch without an early stage
+      ctl->ad_stage = 1;
+      ctl->ad_switches += 1;
+    } else {
+      ctl->inner_rel = want;
+    }
+  }
+  ctl->ad_rs = pow2_inv(sqrt(rr));
+  ctl->ad_zs = 1.0 / ctl->ad_rs;
+  ctl->ad_rs_next = ctl->ad_rs;
+  ctl->ad_rtrue_prev = 0.0;
+}
+
+// Adaptive: after the x/r update (or the start of a system after a restart).
+__device__ __forceinline__ void fin_update_ad(Ctl* ctl, double rr, bool init) {
+  fin_update(ctl, rr, 0.0, init, 0);
+  ctl->ad_rs_next = pow2_inv(sqrt(rr));
+}
+
+// Adaptive: Eqs. (switch_b) and (switch_c) on the true residual of the early stage.
+__device__ __forceinline__ void fin_check_ad(Ctl* ctl, double rt2, double d2) {
+  ctl->n_spmv += 1;
+  const double rt = sqrt(rt2);
+  const double prev = ctl->ad_rtrue_prev;
+  const bool b = prev > 0.0 && rt > 0.9 * prev;
+  const bool c = sqrt(d2) >= 0.5 * rt;
+  if (!isfinite(rt2)) {
+    ctl->status = 6;
+    ctl->done = 1;
+    ctl->outer_done = 1;
+  } else if (b || c) {
+    ctl->done = 1;  // ends the early stage: the outer loop restarts in the late stage
+  }
+  ctl->ad_rtrue_prev = rt;
 }
 
 // last-block helper: beta for the next search direction once rz_next is known

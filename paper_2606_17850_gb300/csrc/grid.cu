@@ -12,6 +12,7 @@
 
 #include "internal.h"
 #include "dfloat.cuh"
+#include "kernels_ad.cuh"
 
 // ------------------------------------------------------------------ errors
 
@@ -67,7 +68,7 @@ th_status validate_opts(const thermal_solve_opts* o) {
     return th_fail(TH_EINVAL, "inner_tol must lie in (0, 1)");
   if (o->max_outer < 1 || o->max_inner < 1 || o->max_iter < 1)
     return th_fail(TH_EINVAL, "iteration limits must be >= 1");
-  if (o->precision < TH_PREC_FP64 || o->precision > TH_PREC_MIXED_IR_BF16)
+  if (o->precision < TH_PREC_FP64 || o->precision > TH_PREC_ADAPTIVE)
     return th_fail(TH_EINVAL, "unknown precision %d", o->precision);
   if (o->precond < TH_PC_NONE || o->precond > TH_PC_ZLINE)
     return th_fail(TH_EINVAL, "unknown preconditioner %d", o->precond);
@@ -76,6 +77,9 @@ th_status validate_opts(const thermal_solve_opts* o) {
   if (o->precond == TH_PC_CHEB && (o->lanczos_steps < 2 || o->lanczos_steps > 1000))
     return th_fail(TH_EINVAL, "lanczos_steps must lie in [2, 1000]");
   if (o->cheb_fuse < 0 || o->cheb_fuse > 4) return th_fail(TH_EINVAL, "cheb_fuse must lie in [0, 4]");
+  if (o->ad_check < 0 || o->ad_check > 100000) return th_fail(TH_EINVAL, "ad_check must lie in [0, 100000]");
+  if (o->precision == TH_PREC_ADAPTIVE && o->precond == TH_PC_ZLINE)
+    return th_fail(TH_EINVAL, "the adaptive precision supports the none, Jacobi and Chebyshev preconditioners");
   return TH_OK;
 }
 
@@ -151,6 +155,30 @@ __global__ void k_setup_diag(Dims d, Faces64 f, const LayerTab* tab, float* invd
   invd64[c.i] = 1.0 / a;
   invd32[c.i] = (float)(1.0 / a);
   isqd32[c.i] = (float)(1.0 / sqrt(a));
+}
+
+// largest main diagonal entry (positive doubles order like their bit patterns)
+__global__ void k_diag_max(Dims d, Faces64 f, const LayerTab* tab, unsigned long long* out) {
+  const Cell c = cell_of(d);
+  double a = c.valid ? diag_at(f, tab, d, c) : 0.0;
+  a = warp_max(a);
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(a));
+}
+
+// Quad-Diag of Sec. 4.2 for the adaptive path: A3 = 2^e (D4, D5, D6, D7) rounded to
+// FP16 (D5..D7 = -g, zero where the neighbour is outside the grid) and D4 in FP32
+// and FP64.
+__global__ void k_setup_qd(Dims d, Faces64 f, const LayerTab* tab, double s, __half* q4, __half* q5, __half* q6,
+                           __half* q7, float* d32, double* d64) {
+  const Cell c = cell_of(d);
+  if (!c.valid) return;
+  const double a = diag_at(f, tab, d, c);
+  d64[c.i] = a;
+  d32[c.i] = (float)a;
+  q4[c.i] = __double2half(s * a);
+  q5[c.i] = __double2half(c.x + 1 < d.nx ? -s * f.gx[c.i] : 0.0);
+  q6[c.i] = __double2half(c.y + 1 < d.ny ? -s * f.gy[c.i] : 0.0);
+  q7[c.i] = __double2half(c.z + 1 < d.L ? -s * f.gz[c.i] : 0.0);
 }
 
 __global__ void k_diag_out(Dims d, Faces64 f, const LayerTab* tab, double* out) {
@@ -238,6 +266,7 @@ thermal_grid::~thermal_grid() {
   dfree(thm_hi); dfree(thm_lo); dfree(thm64);
   dfree(f16.gx); dfree(f16.gy); dfree(f16.gz);
   dfree(tab); dfree(invd32); dfree(invd64); dfree(isqd32); dfree(zl_c); dfree(zl_m);
+  dfree(qd4); dfree(qd5); dfree(qd6); dfree(qd7); dfree(diag32); dfree(diag64);
   for (auto& p : theta) dfree(p);
   dfree(theta_n); dfree(r64); dfree(mu64);
   for (auto& p : p64) dfree(p);
@@ -270,6 +299,7 @@ static th_status compute_faces(thermal_grid* g) {
   cudaFree(geo);
   if (e != cudaSuccess) return th_fail(TH_ECUDA, "face setup failed: %s", cudaGetErrorString(e));
   g->tab_valid = false;
+  g->qd_valid = false;
   g->zl_valid = false;
   g->lanczos_cache.clear();
   if (g->graphs) {  // captured Chebyshev coefficients depend on the faces
@@ -327,6 +357,41 @@ th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s) {
   g->tab_dt = key;
   g->tab_valid = true;
   g->zl_valid = false;
+  return TH_OK;
+}
+
+th_status grid_ensure_qd(thermal_grid* g, double dt, cudaStream_t s) {
+  TH_TRY(grid_ensure_tab(g, dt, s));
+  const double key = dt > 0.0 ? dt : 0.0;
+  if (g->qd_valid && g->qd_dt == key) return TH_OK;
+  if (!g->qd4) {
+    TH_TRY(dalloc(&g->qd4, g->n));
+    TH_TRY(dalloc(&g->qd5, g->n));
+    TH_TRY(dalloc(&g->qd6, g->n));
+    TH_TRY(dalloc(&g->qd7, g->n));
+    TH_TRY(dalloc(&g->diag32, g->n));
+    TH_TRY(dalloc(&g->diag64, g->n));
+  }
+  unsigned long long* mx = nullptr;
+  TH_TRY(dalloc(&mx, 1));
+  unsigned long long hmx = 0;
+  TH_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+  k_diag_max<<<grid_blocks(g), dim3(TH_BX, TH_BY), 0, s>>>(grid_dims(g), g->f64, g->tab, mx);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hmx, mx, sizeof(hmx), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(mx);
+  if (e != cudaSuccess) return th_fail(TH_ECUDA, "diagonal maximum failed: %s", cudaGetErrorString(e));
+  double dmax;
+  std::memcpy(&dmax, &hmx, sizeof(dmax));
+  if (!(dmax > 0.0) || !std::isfinite(dmax)) return th_fail(TH_EINVAL, "non-positive or non-finite diagonal");
+  // max(D4) 2^e in [16, 32): FP16 holds the diagonals with headroom for products
+  g->qd_e = 4 - (int)std::floor(std::log2(dmax));
+  k_setup_qd<<<grid_blocks(g), dim3(TH_BX, TH_BY), 0, s>>>(grid_dims(g), g->f64, g->tab, std::ldexp(1.0, g->qd_e),
+                                                            g->qd4, g->qd5, g->qd6, g->qd7, g->diag32, g->diag64);
+  TH_CHECK_LAUNCH();
+  g->qd_dt = key;
+  g->qd_valid = true;
   return TH_OK;
 }
 
@@ -503,6 +568,7 @@ extern "C" th_status thermal_grid_set_conductivity_map(thermal_grid* g, const do
   if (e != cudaSuccess) return th_fail(TH_ECUDA, "conductivity map setup failed: %s", cudaGetErrorString(e));
   g->uniform = false;
   g->tab_valid = false;
+  g->qd_valid = false;
   g->zl_valid = false;
   g->lanczos_cache.clear();
   if (g->graphs) {
@@ -579,6 +645,12 @@ extern "C" th_status thermal_apply(thermal_grid* g, double dt, int precision, co
       k_apply<float, float, float><<<gb, tb, 0, s>>>(d, g->f32.gx, g->f32.gy, g->f32.gz, g->tab,
                                                      (const float*)x, (float*)y);
       break;
+    case TH_PREC_ADAPTIVE: {
+      TH_TRY(grid_ensure_qd(g, dt, s));
+      const QD16 q{g->qd4, g->qd5, g->qd6, g->qd7};
+      k_apply_a3<<<gb, tb, 0, s>>>(d, q, std::ldexp(1.0f, -g->qd_e), (const float*)x, (float*)y);
+      break;
+    }
     case TH_PREC_MIXED_IR_BF16:
       if (solver_apply_f32(g, true, (const float*)x, (float*)y, s) == TH_OK) return TH_OK;
       k_apply<float, __nv_bfloat16, float><<<gb, tb, 0, s>>>(d, g->f16.gx, g->f16.gy, g->f16.gz, g->tab,

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdarg>
 #include <cstdint>
@@ -89,6 +90,15 @@ struct thermal_grid {
 
   std::map<LanczosKey, LanczosVal> lanczos_cache;
 
+  // adaptive mixed precision (Sec. 4.4): Quad-Diag A3 = 2^qd_e (D4..D7) in FP16 and
+  // the stored main diagonal D4 in FP32 / FP64, per dt (allocated on first use)
+  __half *qd4 = nullptr, *qd5 = nullptr, *qd6 = nullptr, *qd7 = nullptr;
+  float* diag32 = nullptr;
+  double* diag64 = nullptr;
+  int qd_e = 0;
+  double qd_dt = -1.0;
+  bool qd_valid = false;
+
   // workspace (allocated on first use)
   bool ws32 = false, ws64 = false;
   double *theta[2] = {nullptr, nullptr};
@@ -124,6 +134,7 @@ struct thermal_grid {
 th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s);
 th_status grid_ensure_workspace(thermal_grid* g, bool need64, cudaStream_t s);
 th_status grid_ensure_zline(thermal_grid* g, double dt, cudaStream_t s);
+th_status grid_ensure_qd(thermal_grid* g, double dt, cudaStream_t s);
 dim3 grid_blocks(const thermal_grid* g);
 Dims grid_dims(const thermal_grid* g);
 bool is_device_pointer(const void* p);

@@ -42,6 +42,7 @@ __global__ void k_step_begin(Ctl* c) {
   c->outer_it_step = 0;
   c->done = 0;
   c->rel_res = 1.0;
+  c->ad_stage = 0;
 }
 
 __global__ void k_step_end(Ctl* c) {
@@ -105,7 +106,7 @@ __global__ void k_theta_axpy(long long n, const Ctl* ctl, double* __restrict__ t
 // The last block takes the outer-loop decision on the true FP64 residual:
 // mode 0: iterative refinement (the FP32 inner solve must reduce r by inner_rel);
 // mode 1: plain FP64 PCG restarted from the true residual (reduce to 0.5 tol);
-// mode 2: statistics only.
+// mode 2: statistics only; mode 3: adaptive precision (stage and hot restart).
 template <typename TP, typename TR>
 __global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, const double* __restrict__ theta,
                            const TP* __restrict__ P, const TP* const* ptab, const double* __restrict__ theta_n,
@@ -130,7 +131,8 @@ __global__ void k_residual(Dims d, Ctl* ctl, Faces64 f, const LayerTab* tab, con
   }
   double tot[2];
   if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
-  fin_residual(ctl, tot[0], tot[1], mode, count_outer);
+  if (mode == 3) fin_residual_ad(ctl, tot[0], tot[1], count_outer);
+  else fin_residual(ctl, tot[0], tot[1], mode, count_outer);
 }
 
 // ---------------------------------------------------------------- double-float (mixed path)

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
 
 // Vectorised k_update (element-wise; one thread per 4 consecutive cells).
 template <bool INIT, int ZMODE>
-__global__ void __launch_bounds__(256)
+static __global__ void __launch_bounds__(256)
     k_update_v4(long long n4, Ctl* ctl, float* __restrict__ x, const float* __restrict__ p, float* __restrict__ r,
                 const float* __restrict__ mu, const float* __restrict__ invd, float* __restrict__ z, float zscale,
                 int scaled, int rz_here, int scale_r, double* partials, int stride, unsigned* counter) {
@@ -340,4 +340,52 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
   double tot[2];
   if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
   fin_residual(ctl, tot[0], tot[1], 0, count_outer);
+}
+
+// Element-wise double-float kernels of the mixed path, 4 cells per thread (n % 4 == 0,
+// 16-byte aligned arrays); the loop scalars are read once per thread.
+
+// theta += ||r|| d (see k_theta_axpy_df).
+static __global__ void __launch_bounds__(256)
+    k_theta_axpy_df_v4(long long n4, const Ctl* ctl, float* __restrict__ th_hi, float* __restrict__ th_lo,
+                       const float* __restrict__ d) {
+  if (ld_int(&ctl->outer_done)) return;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const long long i = 4 * q;
+  const df rn = df_make(__ldcg(&ctl->rnorm_hi), __ldcg(&ctl->rnorm_lo));
+  const float4 h = ld4(th_hi + i), l = ld4(th_lo + i), dv = ld4(d + i);
+  float oh[4], ol[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const df t = df_add(df_make(cmp(h, k), cmp(l, k)), df_mul_f(rn, cmp(dv, k)));
+    oh[k] = t.hi;
+    ol[k] = t.lo;
+  }
+  st4(th_hi + i, make_float4(oh[0], oh[1], oh[2], oh[3]));
+  st4(th_lo + i, make_float4(ol[0], ol[1], ol[2], ol[3]));
+}
+
+// Start of a step with the extrapolated guess (see k_step_extrap_df).
+static __global__ void __launch_bounds__(256)
+    k_step_extrap_df_v4(long long n4, float* th_hi, float* th_lo, float* thn_hi, float* thn_lo, float* thm_hi,
+                        float* thm_lo) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const long long i = 4 * q;
+  const float4 ch = ld4(th_hi + i), cl = ld4(th_lo + i), ph = ld4(thm_hi + i), pl = ld4(thm_lo + i);
+  float gh[4], gl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const df cur = df_make(cmp(ch, k), cmp(cl, k));
+    const df g = df_sub(df_add(cur, cur), df_make(cmp(ph, k), cmp(pl, k)));
+    gh[k] = g.hi;
+    gl[k] = g.lo;
+  }
+  st4(thn_hi + i, ch);
+  st4(thn_lo + i, cl);
+  st4(thm_hi + i, ch);
+  st4(thm_lo + i, cl);
+  st4(th_hi + i, make_float4(gh[0], gh[1], gh[2], gh[3]));
+  st4(th_lo + i, make_float4(gl[0], gl[1], gl[2], gl[3]));
 }

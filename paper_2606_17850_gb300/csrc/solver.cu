@@ -15,6 +15,7 @@
 #include "kernels.cuh"
 #include "kernels_v4.cuh"
 #include "kernels_tb.cuh"
+#include "kernels_ad.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -57,6 +58,12 @@ struct Plan {
   int zfin = -1;  // pool index of the preconditioned vector (-1: the per-step rule)
   bool v4 = false;
   int zc = 1;
+  // adaptive mixed precision (Sec. 4.4)
+  bool ad = false;
+  int ad_pairs = 10;  // iteration pairs between evaluations of the switching criterion
+  QD16 qd{};
+  float qd_sinv = 1.0f;
+  QDiag qdiag{};
   dim3 gb4, tb4;
   unsigned nbu4 = 1;
 };
@@ -200,6 +207,8 @@ __global__ void k_ctl_timing(Ctl* c) {
   *c = z;
 }
 
+__global__ void k_ctl_stage(Ctl* c, int stage) { c->ad_stage = stage; }
+
 // Picks how many layers one thread walks in the vectorised kernels: the whole
 // column keeps z-neighbours in registers, shorter chunks give more threads on
 // small grids.  Times a Chebyshev step for each candidate (CUDA events) once per grid.
@@ -309,7 +318,16 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
   P.pdtype = pdtype;
   P.transient = transient;
   TH_TRY(grid_ensure_tab(g, dt, s));
-  TH_TRY(grid_ensure_workspace(g, P.prec == TH_PREC_FP64, s));
+  P.ad = (P.prec == TH_PREC_ADAPTIVE);
+  TH_TRY(grid_ensure_workspace(g, P.prec == TH_PREC_FP64 || P.ad, s));
+  if (P.ad) {
+    TH_TRY(grid_ensure_qd(g, dt, s));
+    P.qd = QD16{g->qd4, g->qd5, g->qd6, g->qd7};
+    P.qd_sinv = std::ldexp(1.0f, -g->qd_e);
+    P.qdiag = QDiag{g->diag32, g->diag64};
+    const int chk = o->ad_check > 0 ? o->ad_check : (transient ? 6 : 20);
+    P.ad_pairs = std::max(1, (chk + 1) / 2);
+  }
   if (P.pc == TH_PC_ZLINE) TH_TRY(grid_ensure_zline(g, dt, s));
   P.v4 = (g->nx % 4 == 0);
   P.uni = g->uniform;
@@ -327,7 +345,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     cheb_coeffs(P.lmin, P.lmax, P.k, P.c1, P.c2, &P.inv_theta);
     P.pc_spmv = P.k - 1;
     const int fuse = o->cheb_fuse == 0 ? TB_H : o->cheb_fuse;
-    if (P.prec != TH_PREC_FP64 && P.v4 && P.uni && fuse > 1 && P.k > 1) {
+    if (P.prec != TH_PREC_FP64 && !P.ad && P.v4 && P.uni && fuse > 1 && P.k > 1) {
       // register columns: up to 8 layers with 32 x 32 threads, up to 12 with 32 x 24
       P.tb_lmax = g->L <= 8 ? 8 : (g->L <= 12 ? 12 : 0);
       if (P.tb_lmax > 0) {
@@ -710,6 +728,83 @@ static th_status enq_cond(cudaStream_t st, cudaGraphConditionalHandle h, const C
   return TH_OK;
 }
 
+// ------------------------------------------------------------------ enqueue: adaptive precision
+
+static const float* ad_zfinal(const Plan& P) {
+  thermal_grid* g = P.g;
+  if (P.pc == TH_PC_CHEB) return g->zc32[(P.k - 1) % 3];
+  if (P.pc == TH_PC_JACOBI) return g->zc32[0];
+  return g->r32;
+}
+
+// FP32 Chebyshev tail with the Algorithm 3 product (z_1 comes from the update)
+static th_status enq_ad_precond(const Plan& P, cudaStream_t st) {
+  thermal_grid* g = P.g;
+  if (P.pc != TH_PC_CHEB) return TH_OK;
+  for (int m = 1; m < P.k; ++m) {
+    const float* zprev = (m >= 2) ? g->zc32[(m - 2) % 3] : nullptr;
+    const float* zcur = g->zc32[(m - 1) % 3];
+    float* znext = g->zc32[m % 3];
+    const float c1 = (float)P.c1[m], c2 = (float)P.c2[m];
+    if (P.scaled)
+      k_ad_cheb<true><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, P.qd, P.qd_sinv, g->r32, zprev, zcur, znext, g->invd32, c1,
+                                             c2);
+    else
+      k_ad_cheb<false><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, P.qd, P.qd_sinv, g->r32, zprev, zcur, znext, g->invd32,
+                                              c1, c2);
+    TH_CHECK_LAUNCH();
+  }
+  return TH_OK;
+}
+
+template <bool INIT>
+static th_status enq_ad_update(const Plan& P, cudaStream_t st, int p_cur) {
+  thermal_grid* g = P.g;
+  const long long n = P.d.n;
+#define TH_ADU(ZM)                                                                                          \
+  k_ad_update<INIT, ZM><<<nb1(n), 256, 0, st>>>(n, g->ctl, g->theta[0], g->p64[p_cur], g->r64, g->mu64, g->r32, \
+                                                g->invd32, g->zc32[0], (float)P.inv_theta, P.scaled, g->partials,  \
+                                                g->partials_stride, g->counters)
+  switch (P.pc) {
+    case TH_PC_JACOBI: TH_ADU(1); break;
+    case TH_PC_CHEB: TH_ADU(2); break;
+    default: TH_ADU(0); break;
+  }
+#undef TH_ADU
+  TH_CHECK_LAUNCH();
+  TH_TRY(enq_ad_precond(P, st));
+  k_ad_rz<<<nb1(n), 256, 0, st>>>(n, g->ctl, g->r64, ad_zfinal(P), g->partials, g->partials_stride, g->counters);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+// one PCG iteration of the adaptive path: p = z + beta p, mu = A p, x/r update, z = M r, r^T z
+static th_status enq_ad_iteration(const Plan& P, cudaStream_t st, int parity) {
+  thermal_grid* g = P.g;
+  const long long n = P.d.n;
+  k_ad_pupdate<<<nb1(n), 256, 0, st>>>(n, g->ctl, ad_zfinal(P), g->p64[parity], g->p64[1 - parity]);
+  TH_CHECK_LAUNCH();
+  k_ad_spmv_dot<<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f32, g->f64, P.qdiag, g->p64[1 - parity], g->mu64,
+                                       g->partials, g->partials_stride, g->counters);
+  TH_CHECK_LAUNCH();
+  return enq_ad_update<false>(P, st, 1 - parity);
+}
+
+static th_status enq_ad_check(const Plan& P, cudaStream_t st) {
+  thermal_grid* g = P.g;
+  const double* thn = P.transient ? g->theta_n : nullptr;
+  if (P.pdtype == TH_F32)
+    k_ad_check<float><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64, g->tab, g->theta[0],
+                                             (const float* const*)g->dev_ptrs, thn, g->r64, g->partials,
+                                             g->partials_stride, g->counters);
+  else
+    k_ad_check<double><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64, g->tab, g->theta[0],
+                                              (const double* const*)g->dev_ptrs, thn, g->r64, g->partials,
+                                              g->partials_stride, g->counters);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
 // Pieces of a solve, shared by the polled and the graph form.
 struct Pieces {
   const Plan& P;
@@ -727,7 +822,10 @@ struct Pieces {
     return enq_iteration<float>(P, V, st, 1);
   }
   th_status outer_close(cudaStream_t st) {  // theta += ||r|| d ; r = b - A theta
-    k_theta_axpy_df<<<nb1(P.d.n), 256, 0, st>>>(P.d.n, P.g->ctl, P.g->th_hi, P.g->th_lo, P.g->d32);
+    if (P.v4)
+      k_theta_axpy_df_v4<<<P.nbu4, 256, 0, st>>>(P.d.n / 4, P.g->ctl, P.g->th_hi, P.g->th_lo, P.g->d32);
+    else
+      k_theta_axpy_df<<<nb1(P.d.n), 256, 0, st>>>(P.d.n, P.g->ctl, P.g->th_hi, P.g->th_lo, P.g->d32);
     TH_CHECK_LAUNCH();
     return enq_residual(P, st, 0, 1, false);
   }
@@ -744,20 +842,33 @@ struct Pieces {
     TH_TRY(enq_iteration<double>(P, V, st, 0));
     return enq_iteration<double>(P, V, st, 1);
   }
+  // adaptive path: FP64 PCG on theta; a restart recomputes r and p from their
+  // definitions (hot restart) and keeps theta
+  th_status ad_begin(cudaStream_t st) { return enq_residual(P, st, 3, 0, true); }
+  th_status ad_init(cudaStream_t st) { return enq_ad_update<true>(P, st, 0); }
+  th_status ad_body(cudaStream_t st) {  // ad_pairs iteration pairs, then the switching criterion
+    for (int c = 0; c < P.ad_pairs; ++c) {
+      TH_TRY(enq_ad_iteration(P, st, 0));
+      TH_TRY(enq_ad_iteration(P, st, 1));
+    }
+    return enq_ad_check(P, st);
+  }
+  th_status ad_close(cudaStream_t st) { return enq_residual(P, st, 3, 1, true); }
 };
 
 // theta set-up, theta_n <- theta and T output in the representation of the path
-// (FP64 for the plain FP64 path, double-float for the mixed path)
+// (FP64 for the plain FP64 and the adaptive path, double-float for the mixed path)
+static inline bool theta64(const Plan& P) { return P.prec == TH_PREC_FP64 || P.ad; }
 static th_status enq_prepare(const Plan& P, cudaStream_t st, const double* T, double toff, int mode) {
   thermal_grid* g = P.g;
   const long long n = P.d.n;
-  if (P.prec == TH_PREC_FP64)
+  if (theta64(P))
     k_prepare<<<nb1(n), 256, 0, st>>>(n, T, toff, mode, g->theta[0], g->theta_n);
   else
     k_prepare_df<<<nb1(n), 256, 0, st>>>(n, T, toff, mode, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo);
   TH_CHECK_LAUNCH();
   if (P.extrap) {  // no history yet: theta_{n-1} = theta_n (the first step starts from T_0)
-    if (P.prec == TH_PREC_FP64)
+    if (theta64(P))
       k_copy64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->thm64);
     else
       k_copy_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo);
@@ -768,7 +879,7 @@ static th_status enq_prepare(const Plan& P, cudaStream_t st, const double* T, do
 static th_status enq_finalize(const Plan& P, cudaStream_t st, double toff, double* T) {
   thermal_grid* g = P.g;
   const long long n = P.d.n;
-  if (P.prec == TH_PREC_FP64)
+  if (theta64(P))
     k_finalize<<<nb1(n), 256, 0, st>>>(n, g->theta[0], toff, T);
   else
     k_finalize_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, toff, T);
@@ -779,14 +890,19 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
   thermal_grid* g = P.g;
   const long long n = P.d.n;
   if (P.extrap) {
-    if (P.prec == TH_PREC_FP64)
+    if (theta64(P))
       k_step_extrap64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n, g->thm64);
     else
-      k_step_extrap_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo, g->thm_hi, g->thm_lo);
+      if (P.v4)
+        k_step_extrap_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo, g->thm_hi,
+                                                    g->thm_lo);
+      else
+        k_step_extrap_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo, g->thm_hi,
+                                                 g->thm_lo);
     TH_CHECK_LAUNCH();
     return TH_OK;
   }
-  if (P.prec == TH_PREC_FP64)
+  if (theta64(P))
     k_copy64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n);
   else
     k_copy_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo);
@@ -797,11 +913,11 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
 // ------------------------------------------------------------------ graph building
 
 struct GraphKey {
-  int kind, prec, pc, k, scaled, pdtype, lz, extrap;
+  int kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs;
   double dt;
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, dt) <
-           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.extrap, o.dt);
+    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, dt) <
+           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.extrap, o.fuse, o.ad_pairs, o.dt);
   }
 };
 struct GraphEntry {
@@ -870,6 +986,24 @@ static th_status emit_solve(const Plan& P, GraphCache* gc, int lvl) {
   Pieces pcs(P);
   Ctl* ctl = P.g->ctl;
   cudaStream_t s = gc->cs[lvl];
+  if (P.ad) {
+    TH_TRY(pcs.ad_begin(s));
+    cudaGraph_t bo;
+    cudaGraphConditionalHandle ho;
+    TH_TRY(begin_while(s, ctl, 1, &bo, &ho));
+    return capture_body(bo, gc->cs[lvl + 1], [&](cudaStream_t sb) -> th_status {
+      TH_TRY(pcs.ad_init(sb));
+      cudaGraph_t bi;
+      cudaGraphConditionalHandle hi;
+      TH_TRY(begin_while(sb, ctl, 0, &bi, &hi));
+      TH_TRY(capture_body(bi, gc->cs[lvl + 2], [&](cudaStream_t sc) -> th_status {
+        TH_TRY(pcs.ad_body(sc));
+        return enq_cond(sc, hi, ctl, 0);
+      }));
+      TH_TRY(pcs.ad_close(sb));
+      return enq_cond(sb, ho, ctl, 1);
+    });
+  }
   if (P.prec == TH_PREC_FP64) {
     TH_TRY(pcs.fp64_begin(s));
     cudaGraph_t bo;
@@ -911,7 +1045,7 @@ static CtlInit ctl_init(const thermal_solve_opts* o, int n_steps, int spm, int n
   ci.tol_rel = o->tol_rel;
   ci.inner_tol = o->inner_tol;
   ci.max_outer = o->max_outer;
-  ci.max_inner = o->precision == TH_PREC_FP64 ? o->max_iter : o->max_inner;
+  ci.max_inner = (o->precision == TH_PREC_FP64 || o->precision == TH_PREC_ADAPTIVE) ? o->max_iter : o->max_inner;
   ci.n_steps = n_steps;
   ci.steps_per_map = spm > 0 ? spm : 1;
   ci.n_maps = n_maps > 0 ? n_maps : 1;
@@ -982,6 +1116,21 @@ static th_status polled_solve(const Plan& P, cudaStream_t s) {
   thermal_grid* g = P.g;
   Pieces pcs(P);
   Ctl h;
+  if (P.ad) {
+    TH_TRY(pcs.ad_begin(s));
+    TH_TRY(poll(g, s, &h));
+    while (!h.outer_done) {
+      TH_TRY(pcs.ad_init(s));
+      TH_TRY(poll(g, s, &h));
+      while (!h.done) {
+        TH_TRY(pcs.ad_body(s));
+        TH_TRY(poll(g, s, &h));
+      }
+      TH_TRY(pcs.ad_close(s));
+      TH_TRY(poll(g, s, &h));
+    }
+    return TH_OK;
+  }
   if (P.prec == TH_PREC_FP64) {
     TH_TRY(pcs.fp64_begin(s));
     TH_TRY(poll(g, s, &h));
@@ -1084,6 +1233,7 @@ static void fill_stats(const Plan& P, const Ctl& h, float ms, thermal_solve_stat
   st->lam_min = P.lmin;
   st->lam_max = P.lmax;
   st->steps = h.steps_done;
+  st->stage_switches = h.ad_switches;
 }
 
 // kind: KIND_STEADY, KIND_STEP or KIND_RUN.  maps/n_maps: power maps; T: host or device.
@@ -1128,8 +1278,8 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   const CtlInit ci = ctl_init(o, kind == KIND_RUN ? n_steps : 1, spm, n_maps);
   TH_CUDA(cudaEventRecord(e0, s));
   if (o->use_graph) {
-    const GraphKey key{kind, P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.extrap ? 1 : 0,
-                       P.transient ? dt : 0.0};
+    const GraphKey key{kind,   P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.extrap ? 1 : 0,
+                       o->cheb_fuse, P.ad ? P.ad_pairs : 0, P.transient ? dt : 0.0};
     if (!g->graphs) {
       g->graphs = new GraphCache();
       for (auto& sx : g->graphs->cs) TH_CUDA(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
@@ -1283,15 +1433,15 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 15) return th_fail(TH_EINVAL, "invalid argument");
-  if (kernel >= 13 && !(g->uniform && g->nx % 4 == 0))
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 18) return th_fail(TH_EINVAL, "invalid argument");
+  if (kernel >= 13 && kernel <= 15 && !(g->uniform && g->nx % 4 == 0))
     return th_fail(TH_EINVAL, "fused Chebyshev steps need a layer-uniform grid with nx %% 4 == 0");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
-  o.precond = (kernel >= 13) ? TH_PC_CHEB : TH_PC_JACOBI;
+  o.precond = (kernel >= 13 && kernel <= 15) ? TH_PC_CHEB : TH_PC_JACOBI;
   o.cheb_degree = 5;  // one chunk of four fused steps
-  o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64 : TH_PREC_MIXED_IR;
+  o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64 : (kernel >= 16 ? TH_PREC_ADAPTIVE : TH_PREC_MIXED_IR);
   Plan P;
   TH_TRY(make_plan(g, dt, &o, TH_F32, dt > 0.0, P, s));
   TH_TRY(ensure_stage(g, sizeof(float) * (size_t)g->n));
@@ -1313,11 +1463,27 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   TH_CUDA(cudaMemcpyAsync((void*)g->dev_ptrs, pp, sizeof(void*), cudaMemcpyHostToDevice, s));
   k_ctl_timing<<<1, 1, 0, s>>>(g->ctl);
   TH_CHECK_LAUNCH();
+  if (kernel == 18) {  // late stage of the adaptive path: FP64 coefficients
+    k_ctl_stage<<<1, 1, 0, s>>>(g->ctl, 1);
+    TH_CHECK_LAUNCH();
+  }
   VecSet<float> V = vec32(g);
   VecSet<double> W = vec64(g);
   const float c1 = 0.5f, c2 = 0.5f;
   auto launch = [&]() -> th_status {
     const bool uni = g->uniform && kernel < 9;  // ids 9..12: the per-face variants
+    if (kernel == 16) {
+      k_ad_cheb<true><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, P.qd, P.qd_sinv, g->r32, g->zc32[0], g->zc32[1], g->zc32[2],
+                                            g->invd32, c1, c2);
+      TH_CHECK_LAUNCH();
+      return TH_OK;
+    }
+    if (kernel >= 17) {
+      k_ad_spmv_dot<<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f32, g->f64, P.qdiag, g->p64[0], g->mu64, g->partials,
+                                          g->partials_stride, g->counters);
+      TH_CHECK_LAUNCH();
+      return TH_OK;
+    }
     if (kernel >= 13) {
       // one inner chunk: z_m, z_{m-1}, r in; z_{m+S}, z_{m+S-1} out (no reduction)
       const Plan::Chunk c{kernel == 13 ? 4 : (kernel == 14 ? 2 : 3), 1, 0, 1, 2, 3};

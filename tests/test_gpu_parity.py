@@ -390,6 +390,71 @@ def test_run_transient_long_schedule(prec):
     assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
 
 
+# ------------------------------------- Sec. 4.4: the paper's adaptive mixed precision
+
+@pytest.mark.parametrize("nx,ny,mk,dt", [(37, 21, "c2", 1e-4), (36, 17, "mol", 0.0), (5, 3, "c1", 0.0)])
+def test_a3_product_matches_oracle(nx, ny, mk, dt):
+    """Algorithm 3 (FP16 A3, in-plane FP16 products, out-of-plane FP32) on the GPU
+    equals the oracle's step-by-step emulation; the two can differ only where the FP64
+    diagonal sums round to FP16 on opposite sides of a tie."""
+    from oracle import precision as prc
+    st = STACKS[mk]()
+    A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None).tocsr()
+    g = grid_of(nx, ny, st)
+    x = cuda(ti.random_vector(A.shape[0], 41, lo=-3.0, hi=5.0).astype(np.float32))
+    y = g.apply(x, dt, "adaptive").cpu().double().numpy()
+    D = prc.quad_diag(A, nx, ny)
+    xh = x.cpu().numpy()
+    y_ref = prc.a3_spmv(*D, xh, nx, ny, prc.a3_scale_exponent(D[0])).astype(np.float64)
+    err = np.abs(y - y_ref)
+    assert np.mean(err == 0.0) >= 0.99
+    assert np.all(err <= 2.0 ** -10 * (abs(A) @ np.abs(xh.astype(np.float64))))
+
+
+@pytest.mark.parametrize("pc,scaled", [("cheb", 1), ("cheb", 0), ("jacobi", 1), ("none", 1)])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_adaptive_steady_matches_oracle(pc, scaled, graph):
+    """FP64 PCG with the early FP64/32 SpMV, the FP32/16 Chebyshev preconditioner,
+    the stage switch and the hot restart reaches the exact solution."""
+    st = ti.stack_c2()
+    nx, ny = 30, 22
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (12, 13)], np.float64)
+    g = grid_of(nx, ny, st)
+    T, stats = g.solve_steady(cuda(P), precision="adaptive", precond=pc, cheb_degree=10, cheb_scaled=scaled,
+                              tol_rel=1e-10, use_graph=graph)
+    ref = osolve.steady(nx, ny, st, P)
+    assert stats["status"] == 0 and stats["rel_res"] <= 1e-10
+    assert stats["stage_switches"] == 1
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_adaptive_run_transient(graph):
+    st = ti.stack_c2()
+    nx, ny, dt = 36, 26, 1e-4
+    maps = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s + j) for j in (0, 1)], np.float32)
+            for s in (50, 52)]
+    n_steps, spm = 6, 2
+    g = grid_of(nx, ny, st)
+    T = cuda(np.full(nx * ny * st.L, st.t_amb))
+    T, stats = g.run_transient([cuda(m) for m in maps], spm, n_steps, dt, T, precision="adaptive", tol_rel=1e-10,
+                               cheb_degree=6, use_graph=graph)
+    sched = [maps[(s // spm) % 2].astype(np.float64) for s in range(n_steps)]
+    ref = osolve.transient(nx, ny, st, sched, dt, np.full(nx * ny * st.L, st.t_amb))[-1]
+    assert stats["steps"] == n_steps and stats["status"] == 0
+    assert 1 <= stats["stage_switches"] <= n_steps
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+def test_adaptive_rejects_zline():
+    from paper_2606_17850_gb300 import ThermalError
+    st = ti.stack_c1()
+    g = grid_of(8, 8, st)
+    with pytest.raises(ThermalError) as e:
+        g.solve_steady(cuda(np.ones(8 * 8 * st.L)), precision="adaptive", precond="zline")
+    assert e.value.status == 1
+
+
 # ----------------------------------------------------------------- A10: adjoint
 
 def test_lse_and_adjoint_gradient():
