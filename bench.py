@@ -330,10 +330,8 @@ def main():
         e1.record(stream)
         barrier()
     ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = t.item()
+    from paper_2606_17850_gb300.dist import max_over_ranks
+    ms_total = max_over_ranks(ms_total, device="cuda")
     ms_traj = ms_total / args.steps
     value = ms_traj / nsteps
     T_mixed = T.clone()
@@ -547,24 +545,30 @@ def kernel_table(grid, n, reps, peak, peak_kind):
     return kern
 
 
+# source files that define each profiled kernel: a committed DRAM-traffic figure is
+# used only while these files are unchanged
+KERNEL_SOURCES = {"cheb_tb4": ["kernels_tb.cuh"], "cheb_f32": ["kernels_v4.cuh"]}
+
+
 def traffic_from_profiles(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current sources."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's sources
+    are unchanged since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
     ent = d.get(kernel)
-    if not ent or ent.get("sources_sha") != sources_sha():
+    if not ent or ent.get("sources_sha") != sources_sha(kernel):
         return None
     return ent.get("dram_bytes_per_launch_full_size")
 
 
-def sources_sha():
+def sources_sha(kernel):
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_17850_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(KERNEL_SOURCES.get(kernel, [])):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
