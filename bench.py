@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--guess", type=int, default=1,
                     help="transient initial guess: 0 previous step (the paper's warm start), "
                          "1 linear extrapolation from the two previous steps")
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
+                    help="smallest residual reduction an FP32 inner solve is asked for")
     ap.add_argument("--fuse", type=int, default=0,
                     help="Chebyshev steps per launch (0 auto = 4, 1 one step per launch, 2..4)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-stack batched section")
@@ -302,7 +304,8 @@ def main():
     maps = [torch.from_numpy(m).cuda() for m in maps_h]
     T = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
     opts = dict(precision="mixed", precond="cheb", cheb_degree=args.degree, tol_rel=1e-8,
-                use_graph=0 if args.polled else 1, guess=args.guess, cheb_fuse=args.fuse)
+                use_graph=0 if args.polled else 1, guess=args.guess, cheb_fuse=args.fuse,
+                inner_tol=args.inner_tol)
 
     nsteps = args.time_steps
 
