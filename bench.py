@@ -73,11 +73,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--degree", type=int, default=12, help="Chebyshev degree k (SpMVs per application)")
+    ap.add_argument("--degree", type=int, default=20, help="Chebyshev degree k (SpMVs per application)")
     ap.add_argument("--guess", type=int, default=1,
                     help="transient initial guess: 0 previous step (the paper's warm start), "
                          "1 linear extrapolation from the two previous steps")
-    ap.add_argument("--inner-tol", type=float, default=1e-4,
+    ap.add_argument("--inner-tol", type=float, default=1e-5,
                     help="smallest residual reduction an FP32 inner solve is asked for")
     ap.add_argument("--fuse", type=int, default=0,
                     help="Chebyshev steps per launch (0 auto = 4, 1 one step per launch, 2..4)")

@@ -471,3 +471,79 @@ def test_stage_switch_criteria():
     assert not prc.stage_switch(1.0, 0.85, 1.0, 0.0, eps)
     assert prc.stage_switch(1.0, 1.0, None, 0.5, eps)               # (c) drift between r_true and r_low
     assert not prc.stage_switch(1.0, 1.0, None, 0.49, eps)
+
+
+# ------------------------------------------------ geometric multigrid (oracle)
+
+def test_multigrid_galerkin_is_summed_face_operator():
+    """P^T A P of the 2 x 2-column aggregation is the 7-point operator whose faces
+    are the sums of the fine faces crossing the aggregate boundary and whose
+    per-cell term is the sum of the fine sink/capacity terms (odd sizes included)."""
+    from oracle import multigrid as mg
+    st = ti.stack_c1()
+    for nx, ny in ((6, 4), (7, 5)):
+        L = st.L
+        A = disc.assemble(nx, ny, st, dt=1e-4).tocsr()
+        P = mg.prolongation(nx, ny, L)
+        Ac = (P.T @ A @ P).toarray()
+        nxc, nyc = mg.coarse_dims(nx, ny)
+        s_f = np.asarray(A.sum(axis=1)).ravel()           # row sums = sink + capacity terms
+        gx = -np.asarray([A[i, i + 1] if (i % nx) + 1 < nx else 0.0 for i in range(A.shape[0])])
+        gy = -np.asarray([A[i, i + nx] if ((i // nx) % ny) + 1 < ny else 0.0 for i in range(A.shape[0])])
+        gz = -np.asarray([A[i, i + nx * ny] if i // (nx * ny) + 1 < L else 0.0 for i in range(A.shape[0])])
+        nc = nxc * nyc * L
+        want = np.zeros((nc, nc))
+        cidx = lambda X, Y, z: X + nxc * (Y + nyc * z)
+        for z in range(L):
+            for y in range(ny):
+                for x in range(nx):
+                    i = x + nx * (y + ny * z)
+                    I = cidx(x // 2, y // 2, z)
+                    want[I, I] += s_f[i]
+                    for (dx_, dy_, dz_, g) in ((1, 0, 0, gx[i]), (0, 1, 0, gy[i]), (0, 0, 1, gz[i])):
+                        if g == 0.0:
+                            continue
+                        J = cidx((x + dx_) // 2, (y + dy_) // 2, z + dz_)
+                        if J != I:
+                            want[I, J] -= g; want[J, I] -= g; want[I, I] += g; want[J, J] += g
+        np.testing.assert_allclose(Ac, want, rtol=1e-12, atol=1e-15 * np.abs(want).max())
+
+
+def test_multigrid_vcycle_symmetric_and_exact_on_one_column():
+    from oracle import multigrid as mg
+    st = ti.stack_c2()
+    nx, ny, L = 9, 7, st.L
+    A = disc.assemble(nx, ny, st, dt=1e-4)
+    M = mg.preconditioner(A, nx, ny, L)
+    u, v = ti.random_vector(A.shape[0], 1), ti.random_vector(A.shape[0], 2)
+    a, b = u @ M(v), v @ M(u)
+    assert abs(a - b) <= 1e-12 * max(abs(a), abs(b))
+    assert u @ M(u) > 0
+    # the V-cycle as a stationary iteration contracts the error in the A-norm
+    anorm = lambda e: np.sqrt(e @ (A @ e))
+    for seed in (4, 5, 6):
+        e = ti.random_vector(A.shape[0], seed)
+        e2 = e - M(A @ e)
+        assert anorm(e2) < 0.7 * anorm(e)
+    # max(nx, ny) <= 4: a single (coarsest) level, solved exactly
+    A1 = disc.assemble(3, 2, st)
+    assert len(mg.hierarchy(A1, 3, 2, L)) == 1
+    b1 = ti.random_vector(A1.shape[0], 3)
+    x = mg.vcycle(mg.hierarchy(A1, 3, 2, L), L, b1)
+    assert np.all(np.abs(A1 @ x - b1) <= 1e-12 * (abs(A1) @ np.abs(x)))
+
+
+def test_multigrid_pcg_steady_iterations_and_solution():
+    """MG-preconditioned CG reaches the exact solution in far fewer iterations than
+    Jacobi on a steady stack (the case Chebyshev needs ~100 iterations for)."""
+    from oracle import multigrid as mg
+    inst = ti.c1(nx=32, ny=32)
+    st = inst.stack
+    A = disc.assemble(inst.nx, inst.ny, st)
+    b = disc.rhs_steady(inst.nx, inst.ny, st, inst.power.astype(np.float64))
+    ref = solve.solve_exact(A, b)
+    x_mg, it_mg, _, _ = krylov.pcg(krylov.CountingOp(A), b, mg.preconditioner(A, inst.nx, inst.ny, st.L),
+                                   tol_rel=1e-10)
+    x_j, it_j, _, _ = krylov.pcg(krylov.CountingOp(A), b, krylov.jacobi(A), tol_rel=1e-10)
+    assert solve.rise_relative_error(x_mg, ref, st.t_amb) <= 1e-8
+    assert it_mg * 5 < it_j, (it_mg, it_j)
