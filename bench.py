@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--no-ablation", action="store_true", help="skip the stencil-vs-CSR SpMV comparison")
+    ap.add_argument("--no-precond", action="store_true",
+                    help="skip the preconditioner comparison (Chebyshev vs multigrid, steady 512^2x8 and the "
+                         "transient trajectory)")
     ap.add_argument("--polled", action="store_true",
                     help="host-polled loop instead of the CUDA graph (same kernels; for per-kernel profiling)")
     ap.add_argument("--time-steps", type=int, default=N_STEPS,
@@ -426,6 +429,8 @@ def main():
                                  "T_100 back, through thermal_run_transient with pinned host buffers"}
     if not args.no_ablation:
         result["spmv_ablation"] = ablation_section(grid, inst.n, args.reps, result.get("kernels"), peak)
+    if not args.no_precond:
+        result["preconditioners"] = precond_section(args, opts, trajectory, maps, nsteps, st)
     if not args.no_batched:
         result["batched"] = batched_section(args)
     if not args.no_adjoint:
@@ -482,6 +487,34 @@ def ablation_section(grid, n, reps, kern, peak):
         "f32 (layer table)": out["csr_scalar_f32"]["ms"] / st["stencil_f32"]}
     out["note"] = ("same matrix (transient, dt=1e-4) in CSR with 32-bit indices; the paper reports 2.0-2.2x "
                    "for its diagonal-wise kernels over CSR on a different GPU")
+    return out
+
+
+def precond_section(args, opts, trajectory, maps, nsteps, st):
+    """Chebyshev (Lanczos bounds) against the geometric multigrid V-cycle: the steady
+    512 x 512 x 8 floorplan stack (FP32 PCG + FP64 refinement to 1e-8) and the
+    transient trajectory of the headline."""
+    import numpy as np
+    import torch
+    import thermal_inputs as ti
+    from paper_2606_17850_gb300 import ThermalGrid
+    out = {}
+    c2 = ti.c2(dtype=np.float32)
+    g2 = ThermalGrid.from_stack(c2.nx, c2.ny, c2.stack)
+    P2 = torch.from_numpy(c2.power).cuda()
+    for name, o in (("cheb30", dict(precond="cheb", cheb_degree=30)), ("cheb20", dict(precond="cheb", cheb_degree=20)),
+                    ("mg", dict(precond="mg")), ("jacobi", dict(precond="jacobi"))):
+        oo = dict(o, tol_rel=1e-8, inner_tol=args.inner_tol)
+        g2.solve_steady(P2, **oo)  # set-up (Lanczos / hierarchy, graph)
+        ms, (T, stt) = _event_ms(lambda: g2.solve_steady(P2, **oo), reps=2)
+        out[f"steady_512x512x8_{name}"] = {"ms": ms, "inner_it": stt["inner_it"], "outer_it": stt["outer_it"],
+                                            "rel_res": stt["rel_res"]}
+    omg = dict(opts, precond="mg")
+    Tm = torch.full((maps[0].numel(),), st.t_amb, dtype=torch.float64, device="cuda")
+    trajectory(omg, Tm, maps)
+    ms, stt = _event_ms(lambda: trajectory(omg, Tm, maps), reps=1)
+    out["transient_1024x1024x8_mg"] = {"ms_per_step": ms / nsteps, "inner_it": stt["inner_it"],
+                                       "outer_it": stt["outer_it"], "rel_res": stt["rel_res"]}
     return out
 
 

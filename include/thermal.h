@@ -72,7 +72,9 @@ typedef enum th_precond {
   TH_PC_JACOBI = 1,  /* M = diag(A) (Sec. 5.7)                                            */
   TH_PC_CHEB = 2,    /* Chebyshev polynomial of degree k (Algorithm "Chebyshev Polynomial  */
                      /* Preconditioning", Sec. 4.3) with Lanczos spectral bounds          */
-  TH_PC_ZLINE = 3    /* block Jacobi with one tridiagonal block per (x, y) column          */
+  TH_PC_ZLINE = 3,   /* block Jacobi with one tridiagonal block per (x, y) column          */
+  TH_PC_MG = 4       /* geometric multigrid V-cycle: x/y semi-coarsening, damped z-line    */
+                     /* Jacobi smoother, exact coarsest solve (FP32; MIXED_IR only)       */
 } th_precond;
 
 typedef enum th_dtype { TH_F32 = 0, TH_F64 = 1 } th_dtype;

@@ -15,7 +15,7 @@ TH_OK, TH_EINVAL, TH_ENOMEM, TH_ECUDA, TH_ENOCONV, TH_EBREAKDOWN, TH_ENONFINITE,
 STATUS_NAMES = ["TH_OK", "TH_EINVAL", "TH_ENOMEM", "TH_ECUDA", "TH_ENOCONV", "TH_EBREAKDOWN",
                 "TH_ENONFINITE", "TH_ESTATE"]
 TH_PREC_FP64, TH_PREC_MIXED_IR, TH_PREC_MIXED_IR_BF16, TH_PREC_ADAPTIVE = 0, 1, 2, 3
-TH_PC_NONE, TH_PC_JACOBI, TH_PC_CHEB, TH_PC_ZLINE = 0, 1, 2, 3
+TH_PC_NONE, TH_PC_JACOBI, TH_PC_CHEB, TH_PC_ZLINE, TH_PC_MG = 0, 1, 2, 3, 4
 TH_F32, TH_F64 = 0, 1
 
 

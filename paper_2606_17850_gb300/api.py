@@ -15,7 +15,8 @@ from . import _lib as L
 
 PRECISION = {"fp64": L.TH_PREC_FP64, "mixed": L.TH_PREC_MIXED_IR, "mixed_bf16": L.TH_PREC_MIXED_IR_BF16,
              "adaptive": L.TH_PREC_ADAPTIVE}
-PRECOND = {"none": L.TH_PC_NONE, "jacobi": L.TH_PC_JACOBI, "cheb": L.TH_PC_CHEB, "zline": L.TH_PC_ZLINE}
+PRECOND = {"none": L.TH_PC_NONE, "jacobi": L.TH_PC_JACOBI, "cheb": L.TH_PC_CHEB, "zline": L.TH_PC_ZLINE,
+           "mg": L.TH_PC_MG}
 
 
 def _ptr(t: Optional[torch.Tensor]):

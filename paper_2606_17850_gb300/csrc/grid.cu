@@ -70,7 +70,7 @@ th_status validate_opts(const thermal_solve_opts* o) {
     return th_fail(TH_EINVAL, "iteration limits must be >= 1");
   if (o->precision < TH_PREC_FP64 || o->precision > TH_PREC_ADAPTIVE)
     return th_fail(TH_EINVAL, "unknown precision %d", o->precision);
-  if (o->precond < TH_PC_NONE || o->precond > TH_PC_ZLINE)
+  if (o->precond < TH_PC_NONE || o->precond > TH_PC_MG)
     return th_fail(TH_EINVAL, "unknown preconditioner %d", o->precond);
   if (o->precond == TH_PC_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 1000))
     return th_fail(TH_EINVAL, "cheb_degree must lie in [1, 1000]");
@@ -78,8 +78,10 @@ th_status validate_opts(const thermal_solve_opts* o) {
     return th_fail(TH_EINVAL, "lanczos_steps must lie in [2, 1000]");
   if (o->cheb_fuse < 0 || o->cheb_fuse > 4) return th_fail(TH_EINVAL, "cheb_fuse must lie in [0, 4]");
   if (o->ad_check < 0 || o->ad_check > 100000) return th_fail(TH_EINVAL, "ad_check must lie in [0, 100000]");
-  if (o->precision == TH_PREC_ADAPTIVE && o->precond == TH_PC_ZLINE)
+  if (o->precision == TH_PREC_ADAPTIVE && (o->precond == TH_PC_ZLINE || o->precond == TH_PC_MG))
     return th_fail(TH_EINVAL, "the adaptive precision supports the none, Jacobi and Chebyshev preconditioners");
+  if (o->precond == TH_PC_MG && o->precision == TH_PREC_FP64)
+    return th_fail(TH_EINVAL, "the multigrid preconditioner runs in FP32: use a mixed precision");
   return TH_OK;
 }
 
@@ -267,6 +269,7 @@ thermal_grid::~thermal_grid() {
   dfree(f16.gx); dfree(f16.gy); dfree(f16.gz);
   dfree(tab); dfree(invd32); dfree(invd64); dfree(isqd32); dfree(zl_c); dfree(zl_m);
   dfree(qd4); dfree(qd5); dfree(qd6); dfree(qd7); dfree(diag32); dfree(diag64);
+  if (mg) mg_free(mg);
   for (auto& p : theta) dfree(p);
   dfree(theta_n); dfree(r64); dfree(mu64);
   for (auto& p : p64) dfree(p);
@@ -300,6 +303,7 @@ static th_status compute_faces(thermal_grid* g) {
   if (e != cudaSuccess) return th_fail(TH_ECUDA, "face setup failed: %s", cudaGetErrorString(e));
   g->tab_valid = false;
   g->qd_valid = false;
+  g->mg_valid = false;
   g->zl_valid = false;
   g->lanczos_cache.clear();
   if (g->graphs) {  // captured Chebyshev coefficients depend on the faces
@@ -569,6 +573,7 @@ extern "C" th_status thermal_grid_set_conductivity_map(thermal_grid* g, const do
   g->uniform = false;
   g->tab_valid = false;
   g->qd_valid = false;
+  g->mg_valid = false;
   g->zl_valid = false;
   g->lanczos_cache.clear();
   if (g->graphs) {

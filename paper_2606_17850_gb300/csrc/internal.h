@@ -99,6 +99,10 @@ struct thermal_grid {
   double qd_dt = -1.0;
   bool qd_valid = false;
 
+  // geometric multigrid hierarchy (multigrid.cu), per dt
+  struct MGHier* mg = nullptr;
+  bool mg_valid = false;
+
   // workspace (allocated on first use)
   bool ws32 = false, ws64 = false;
   double *theta[2] = {nullptr, nullptr};
@@ -135,6 +139,12 @@ th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s);
 th_status grid_ensure_workspace(thermal_grid* g, bool need64, cudaStream_t s);
 th_status grid_ensure_zline(thermal_grid* g, double dt, cudaStream_t s);
 th_status grid_ensure_qd(thermal_grid* g, double dt, cudaStream_t s);
+// multigrid.cu
+struct MGHier;
+void mg_free(MGHier* h);
+th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s);
+th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s);
+th_status mg_rz(thermal_grid* g, const float* r, const float* z, cudaStream_t s);
 dim3 grid_blocks(const thermal_grid* g);
 Dims grid_dims(const thermal_grid* g);
 bool is_device_pointer(const void* p);

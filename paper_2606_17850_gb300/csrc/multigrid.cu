@@ -1,0 +1,456 @@
+// Geometric multigrid preconditioner (one V-cycle per application), FP32.
+//
+// Not in the paper: the robust alternative to the Chebyshev preconditioner when
+// layers are in-plane dominated (Si, Cu) and vertically dominated (BEOL, TIM,
+// bonds) in the same stack.
+//
+// * Semi-coarsening in x and y only (every level keeps all layers): a coarse cell
+//   aggregates the 2 x 2 fine columns (2X..2X+1, 2Y..2Y+1) of its layer (fewer on an
+//   odd edge).  Piecewise-constant prolongation P, restriction P^T, Galerkin coarse
+//   operator P^T A P, which is again a 7-point operator: a coarse face sums the fine
+//   faces crossing the aggregate boundary, the coarse per-cell term sums the fine
+//   sink/capacity terms.  Levels are added while max(nx, ny) > 4.
+// * Smoother: damped z-line Jacobi, x <- x + omega T^-1 (b - A x), T the tridiagonal
+//   block of A over each (x, y) column (Thomas factors precomputed per level), one
+//   sweep before and one after the coarse correction; omega = 0.8.
+// * Coarsest level (at most 4 x 4 columns): exact solve with a dense inverse
+//   computed once on the host in FP64.
+// The cycle starts from zero on every level and pre/post sweeps match, so M^-1 is
+// symmetric, as PCG requires.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr float MG_OMEGA = 0.8f;
+constexpr int MG_COARSEST = 4;
+
+__device__ __forceinline__ long long idx3(int nx, int ny, int x, int y, int z) {
+  return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+}
+
+// per-cell sink + capacity term of the finest level from the layer table
+__global__ void k_mg_s0(Dims d, const LayerTab* tab, float* __restrict__ s) {
+  const Cell c = cell_of(d);
+  if (!c.valid) return;
+  s[c.i] = __ldg(&tab->s32[c.z]);
+}
+
+// Galerkin coarse operator of the 2 x 2-column aggregation (one thread per coarse cell)
+__global__ void k_mg_coarsen(int nxf, int nyf, int nxc, int nyc, int L, const float* __restrict__ gxf,
+                             const float* __restrict__ gyf, const float* __restrict__ gzf,
+                             const float* __restrict__ sf, float* __restrict__ gxc, float* __restrict__ gyc,
+                             float* __restrict__ gzc, float* __restrict__ sc) {
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (X >= nxc || Y >= nyc) return;
+  const int x0 = 2 * X, y0 = 2 * Y;
+  const bool hx = x0 + 1 < nxf, hy = y0 + 1 < nyf;  // second fine column / row exists
+  float s = 0.f, gz = 0.f, gx = 0.f, gy = 0.f;
+  for (int b = 0; b < (hy ? 2 : 1); ++b)
+    for (int a = 0; a < (hx ? 2 : 1); ++a) {
+      const long long i = idx3(nxf, nyf, x0 + a, y0 + b, z);
+      s += sf[i];
+      gz += gzf[i];
+    }
+  if (hx) {  // faces between fine x0+1 and x0+2, i.e. between aggregates X and X+1
+    gx = gxf[idx3(nxf, nyf, x0 + 1, y0, z)];
+    if (hy) gx += gxf[idx3(nxf, nyf, x0 + 1, y0 + 1, z)];
+  }
+  if (hy) {
+    gy = gyf[idx3(nxf, nyf, x0, y0 + 1, z)];
+    if (hx) gy += gyf[idx3(nxf, nyf, x0 + 1, y0 + 1, z)];
+  }
+  const long long ic = idx3(nxc, nyc, X, Y, z);
+  sc[ic] = s;
+  gzc[ic] = gz;
+  gxc[ic] = (X + 1 < nxc) ? gx : 0.f;
+  gyc[ic] = (Y + 1 < nyc) ? gy : 0.f;
+}
+
+// Thomas factors of every column's tridiagonal block T: b_z = A_zz, a_z = -gz_{z-1},
+// c_z = -gz_z; m_z = 1 / (b_z - a_z c'_{z-1}), c'_z = c_z m_z; stored m_z and
+// w_z = gz_z m_z (= -c'_z).
+__global__ void k_mg_zfactors(int nx, int ny, int L, const float* __restrict__ gx, const float* __restrict__ gy,
+                              const float* __restrict__ gz, const float* __restrict__ s, float* __restrict__ m,
+                              float* __restrict__ w) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const long long pxy = (long long)nx * ny;
+  double wprev = 0.0;  // -c'_{z-1}
+  for (int z = 0; z < L; ++z) {
+    const long long i = idx3(nx, ny, x, y, z);
+    double b = s[i];
+    if (x + 1 < nx) b += gx[i];
+    if (x > 0) b += gx[i - 1];
+    if (y + 1 < ny) b += gy[i];
+    if (y > 0) b += gy[i - nx];
+    if (z + 1 < L) b += gz[i];
+    const double gb = (z > 0) ? (double)gz[i - pxy] : 0.0;
+    if (z > 0) b += gb;
+    const double mz = 1.0 / (b - gb * wprev);  // a_z c'_{z-1} = (-gb)(-wprev)
+    const double wz = (z + 1 < L) ? (double)gz[i] * mz : 0.0;
+    m[i] = (float)mz;
+    w[i] = (float)wz;
+    wprev = wz;
+  }
+}
+
+struct MGDev {  // one level, by value into kernels
+  int nx, ny, L;
+  const float *gx, *gy, *gz, *s, *m, *w;
+};
+
+// x_out = x + omega T^-1 (b - A x) per column, x = x_in (+ P x_c: the prolongated
+// coarse correction, read on the fly) or 0 (x_in == nullptr).  One thread per
+// column; the column (LMAX >= L layers) stays in registers.
+template <int LMAX>
+__global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, const float* __restrict__ b,
+                                                   const float* __restrict__ xin, const float* __restrict__ xc,
+                                                   int nxc, int nyc, float* __restrict__ xout, float omega) {
+  if (ld_int(&ctl->done)) return;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= v.nx || y >= v.ny) return;
+  const int L = v.L;
+  const long long pxy = (long long)v.nx * v.ny;
+  const long long pxyc = (long long)nxc * nyc;
+  auto val = [&](int xx, int yy, int z) -> float {
+    if (!xin) return 0.f;
+    float t = xin[idx3(v.nx, v.ny, xx, yy, z)];
+    if (xc) t += xc[(xx >> 1) + (long long)nxc * (yy >> 1) + pxyc * z];
+    return t;
+  };
+  float xv[LMAX], dp[LMAX];
+  // current iterate of the column
+#pragma unroll
+  for (int z = 0; z < LMAX; ++z) xv[z] = (z < L) ? val(x, y, z) : 0.f;
+  // forward sweep: residual and Thomas elimination
+  float dprev = 0.f;
+#pragma unroll
+  for (int z = 0; z < LMAX; ++z) {
+    if (z >= L) break;
+    const long long i = idx3(v.nx, v.ny, x, y, z);
+    float res = b[i];
+    if (xin) {
+      const float xi = xv[z];
+      float a = v.s[i] * xi;
+      if (x + 1 < v.nx) a += v.gx[i] * (xi - val(x + 1, y, z));
+      if (x > 0) a += v.gx[i - 1] * (xi - val(x - 1, y, z));
+      if (y + 1 < v.ny) a += v.gy[i] * (xi - val(x, y + 1, z));
+      if (y > 0) a += v.gy[i - v.nx] * (xi - val(x, y - 1, z));
+      if (z + 1 < L) a += v.gz[i] * (xi - xv[z + 1 < LMAX ? z + 1 : z]);
+      if (z > 0) a += v.gz[i - pxy] * (xi - xv[z > 0 ? z - 1 : 0]);
+      res -= a;
+    }
+    const float gb = (z > 0) ? v.gz[i - pxy] : 0.f;
+    dprev = (res + gb * dprev) * v.m[i];
+    dp[z] = dprev;
+  }
+  // back substitution and the damped update
+  float dn = 0.f;
+#pragma unroll
+  for (int zz = LMAX - 1; zz >= 0; --zz) {
+    if (zz >= L) continue;
+    const int z = zz;
+    const long long i = idx3(v.nx, v.ny, x, y, z);
+    const float dz = dp[z] + v.w[i] * dn;
+    dn = dz;
+    xout[i] = xv[z] + omega * dz;
+  }
+}
+
+// b_c = P^T (b - A x): one thread per coarse column, summing the residuals of the
+// aggregate's fine cells.
+__global__ void __launch_bounds__(256) k_mg_restrict(const Ctl* ctl, MGDev v, const float* __restrict__ b,
+                                                     const float* __restrict__ x, int nxc, int nyc,
+                                                     float* __restrict__ bc) {
+  if (ld_int(&ctl->done)) return;
+  const int X = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (X >= nxc || Y >= nyc) return;
+  const long long pxy = (long long)v.nx * v.ny;
+  const int x0 = 2 * X, y0 = 2 * Y;
+  const int na = (x0 + 1 < v.nx) ? 2 : 1, nb = (y0 + 1 < v.ny) ? 2 : 1;
+  for (int z = 0; z < v.L; ++z) {
+    float sum = 0.f;
+    for (int bb = 0; bb < nb; ++bb)
+      for (int aa = 0; aa < na; ++aa) {
+        const int xx = x0 + aa, yy = y0 + bb;
+        const long long i = idx3(v.nx, v.ny, xx, yy, z);
+        const float xi = x[i];
+        float a = v.s[i] * xi;
+        if (xx + 1 < v.nx) a += v.gx[i] * (xi - x[i + 1]);
+        if (xx > 0) a += v.gx[i - 1] * (xi - x[i - 1]);
+        if (yy + 1 < v.ny) a += v.gy[i] * (xi - x[i + v.nx]);
+        if (yy > 0) a += v.gy[i - v.nx] * (xi - x[i - v.nx]);
+        if (z + 1 < v.L) a += v.gz[i] * (xi - x[i + pxy]);
+        if (z > 0) a += v.gz[i - pxy] * (xi - x[i - pxy]);
+        sum += b[i] - a;
+      }
+    bc[idx3(nxc, nyc, X, Y, z)] = sum;
+  }
+}
+
+// coarsest level: x = C b with the dense inverse C (n x n, FP32), one CTA, a warp per row
+__global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, const float* __restrict__ C,
+                                                     const float* __restrict__ b, float* __restrict__ x) {
+  if (ld_int(&ctl->done)) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = warp; row < n; row += nw) {
+    float acc = 0.f;
+    for (int j = lane; j < n; j += 32) acc += C[(long long)row * n + j] * b[j];
+    acc = warp_sum(acc);
+    if (lane == 0) x[row] = acc;
+  }
+}
+
+// r^T z with FP32 products and FP64 sums, then beta (the preconditioner's dot product)
+__global__ void k_mg_rz(long long n, Ctl* ctl, const float* __restrict__ r, const float* __restrict__ z,
+                        double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float v[1] = {0.f};
+  if (i < n) v[0] = r[i] * z[i];
+  double tot[1];
+  if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
+}
+
+dim3 col_grid(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8, 1); }
+
+}  // namespace
+
+struct MGLevelH {
+  int nx = 0, ny = 0;
+  long long n = 0;
+  const float *gx = nullptr, *gy = nullptr, *gz = nullptr;  // level 0: the grid's FP32 faces
+  float *own_gx = nullptr, *own_gy = nullptr, *own_gz = nullptr;
+  float *s = nullptr, *m = nullptr, *w = nullptr;
+  float *x = nullptr, *xt = nullptr, *b = nullptr;
+};
+
+struct MGHier {
+  double dt = -1.0;
+  std::vector<MGLevelH> lv;
+  float* cinv = nullptr;  // dense inverse of the coarsest operator
+  int nc = 0;
+  ~MGHier() {
+    for (auto& l : lv) {
+      for (float* p : {l.own_gx, l.own_gy, l.own_gz, l.s, l.m, l.w, l.x, l.xt, l.b})
+        if (p) cudaFree(p);
+    }
+    if (cinv) cudaFree(cinv);
+  }
+};
+
+void mg_free(MGHier* h) { delete h; }
+
+static th_status mg_alloc(float** p, long long n) {
+  if (cudaMalloc((void**)p, sizeof(float) * (size_t)std::max(n, 1LL)) != cudaSuccess) {
+    cudaGetLastError();
+    return th_fail(TH_ENOMEM, "multigrid level allocation failed");
+  }
+  return TH_OK;
+}
+
+static MGDev dev_of(const MGLevelH& l, int L) { return MGDev{l.nx, l.ny, L, l.gx, l.gy, l.gz, l.s, l.m, l.w}; }
+
+// Dense symmetric positive definite inverse by Cholesky (host, FP64).
+static bool spd_inverse(std::vector<double>& A, int n) {
+  // A = R^T R in place (upper R)
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)k * n + j] * A[(size_t)k * n + j];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    A[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)j * n + i];
+      for (int k = 0; k < j; ++k) t -= A[(size_t)k * n + j] * A[(size_t)k * n + i];
+      A[(size_t)j * n + i] = t / d;
+    }
+  }
+  // inverse columns: solve R^T R x = e_c
+  std::vector<double> inv((size_t)n * n), y(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= A[(size_t)k * n + i] * y[k];
+      y[i] = t / A[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= A[(size_t)i * n + k] * inv[(size_t)k * n + c];
+      inv[(size_t)i * n + c] = t / A[(size_t)i * n + i];
+    }
+  }
+  A.swap(inv);
+  return true;
+}
+
+th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s) {
+  TH_TRY(grid_ensure_tab(g, dt, s));
+  const double key = dt > 0.0 ? dt : 0.0;
+  if (g->mg && g->mg_valid && g->mg->dt == key) return TH_OK;
+  if (g->L > 32) return th_fail(TH_EINVAL, "multigrid supports at most 32 layers");
+  if (!g->mg) {
+    MGHier* h = new MGHier();
+    int nx = g->nx, ny = g->ny;
+    while (true) {
+      MGLevelH l;
+      l.nx = nx;
+      l.ny = ny;
+      l.n = (long long)nx * ny * g->L;
+      h->lv.push_back(l);
+      if (std::max(nx, ny) <= MG_COARSEST) break;
+      nx = (nx + 1) / 2;
+      ny = (ny + 1) / 2;
+    }
+    g->mg = h;
+    for (size_t k = 0; k < h->lv.size(); ++k) {
+      MGLevelH& l = h->lv[k];
+      TH_TRY(mg_alloc(&l.s, l.n));
+      TH_TRY(mg_alloc(&l.m, l.n));
+      TH_TRY(mg_alloc(&l.w, l.n));
+      TH_TRY(mg_alloc(&l.xt, l.n));
+      if (k == 0) {
+        l.gx = g->f32.gx;
+        l.gy = g->f32.gy;
+        l.gz = g->f32.gz;
+      } else {
+        TH_TRY(mg_alloc(&l.own_gx, l.n));
+        TH_TRY(mg_alloc(&l.own_gy, l.n));
+        TH_TRY(mg_alloc(&l.own_gz, l.n));
+        l.gx = l.own_gx;
+        l.gy = l.own_gy;
+        l.gz = l.own_gz;
+        TH_TRY(mg_alloc(&l.x, l.n));
+        TH_TRY(mg_alloc(&l.b, l.n));
+      }
+    }
+  }
+  MGHier* h = g->mg;
+  const int L = g->L;
+  k_mg_s0<<<grid_blocks(g), dim3(TH_BX, TH_BY), 0, s>>>(grid_dims(g), g->tab, h->lv[0].s);
+  TH_CHECK_LAUNCH();
+  for (size_t k = 0; k + 1 < h->lv.size(); ++k) {
+    const MGLevelH& f = h->lv[k];
+    MGLevelH& c = h->lv[k + 1];
+    const dim3 gr((c.nx + 31) / 32, (c.ny + 7) / 8, L);
+    k_mg_coarsen<<<gr, dim3(32, 8), 0, s>>>(f.nx, f.ny, c.nx, c.ny, L, f.gx, f.gy, f.gz, f.s, c.own_gx, c.own_gy,
+                                            c.own_gz, c.s);
+    TH_CHECK_LAUNCH();
+  }
+  for (auto& l : h->lv) {
+    k_mg_zfactors<<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(l.nx, l.ny, L, l.gx, l.gy, l.gz, l.s, l.m, l.w);
+    TH_CHECK_LAUNCH();
+  }
+  // dense inverse of the coarsest operator (at most 4 x 4 columns x L layers)
+  const MGLevelH& c = h->lv.back();
+  const int nc = (int)c.n;
+  std::vector<float> hx(c.n), hy(c.n), hz(c.n), hs(c.n);
+  TH_CUDA(cudaMemcpyAsync(hx.data(), c.gx, sizeof(float) * c.n, cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(hy.data(), c.gy, sizeof(float) * c.n, cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(hz.data(), c.gz, sizeof(float) * c.n, cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaMemcpyAsync(hs.data(), c.s, sizeof(float) * c.n, cudaMemcpyDeviceToHost, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> A((size_t)nc * nc, 0.0);
+  auto couple = [&](long long i, long long j, double gval) {
+    A[(size_t)i * nc + j] -= gval;
+    A[(size_t)j * nc + i] -= gval;
+    A[(size_t)i * nc + i] += gval;
+    A[(size_t)j * nc + j] += gval;
+  };
+  for (int z = 0; z < L; ++z)
+    for (int y = 0; y < c.ny; ++y)
+      for (int x = 0; x < c.nx; ++x) {
+        const long long i = (long long)x + (long long)c.nx * (y + (long long)c.ny * z);
+        A[(size_t)i * nc + i] += hs[i];
+        if (x + 1 < c.nx) couple(i, i + 1, hx[i]);
+        if (y + 1 < c.ny) couple(i, i + c.nx, hy[i]);
+        if (z + 1 < L) couple(i, i + (long long)c.nx * c.ny, hz[i]);
+      }
+  if (!spd_inverse(A, nc)) return th_fail(TH_ENOCONV, "coarsest multigrid operator is not positive definite");
+  std::vector<float> Af(A.begin(), A.end());
+  if (h->cinv && h->nc != nc) {
+    cudaFree(h->cinv);
+    h->cinv = nullptr;
+  }
+  if (!h->cinv) TH_TRY(mg_alloc(&h->cinv, (long long)nc * nc));
+  h->nc = nc;
+  TH_CUDA(cudaMemcpyAsync(h->cinv, Af.data(), sizeof(float) * Af.size(), cudaMemcpyHostToDevice, s));
+  TH_CUDA(cudaStreamSynchronize(s));
+  h->dt = key;
+  g->mg_valid = true;
+  return TH_OK;
+}
+
+template <int LMAX>
+static th_status smooth(thermal_grid* g, const MGLevelH& l, const float* b, const float* xin, const float* xc,
+                        int nxc, int nyc, float* xout, cudaStream_t s) {
+  k_mg_smooth<LMAX><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), b, xin, xc, nxc, nyc, xout,
+                                                                  MG_OMEGA);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+static th_status smooth_any(thermal_grid* g, const MGLevelH& l, const float* b, const float* xin, const float* xc,
+                            int nxc, int nyc, float* xout, cudaStream_t s) {
+  if (g->L <= 8) return smooth<8>(g, l, b, xin, xc, nxc, nyc, xout, s);
+  if (g->L <= 16) return smooth<16>(g, l, b, xin, xc, nxc, nyc, xout, s);
+  return smooth<32>(g, l, b, xin, xc, nxc, nyc, xout, s);
+}
+
+// z = M^-1 r: one V-cycle (see the file comment).  Every level's pre-smoothed
+// iterate is in x (level 0: xt); the post-smoothed one goes to xt (level 0: z).
+th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
+  MGHier* h = g->mg;
+  if (!h || !g->mg_valid) return th_fail(TH_ESTATE, "multigrid hierarchy not built");
+  const int nl = (int)h->lv.size();
+  if (nl == 1) {
+    k_mg_coarsest<<<1, 256, 0, s>>>(g->ctl, h->nc, h->cinv, r, z);
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  }
+  std::vector<const float*> B(nl);
+  std::vector<float*> X(nl);
+  B[0] = r;
+  X[0] = h->lv[0].xt;
+  for (int k = 1; k < nl; ++k) {
+    B[k] = h->lv[k].b;
+    X[k] = h->lv[k].x;
+  }
+  for (int k = 0; k + 1 < nl; ++k) {  // down: pre-smooth from zero, restrict the residual
+    const MGLevelH& l = h->lv[k];
+    const MGLevelH& c = h->lv[k + 1];
+    TH_TRY(smooth_any(g, l, B[k], nullptr, nullptr, 1, 1, X[k], s));
+    k_mg_restrict<<<col_grid(c.nx, c.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), B[k], X[k], c.nx, c.ny,
+                                                                h->lv[k + 1].b);
+    TH_CHECK_LAUNCH();
+  }
+  k_mg_coarsest<<<1, 256, 0, s>>>(g->ctl, h->nc, h->cinv, B[nl - 1], X[nl - 1]);
+  TH_CHECK_LAUNCH();
+  for (int k = nl - 2; k >= 0; --k) {  // up: coarse correction (prolongated on the fly) + post-smooth
+    const MGLevelH& l = h->lv[k];
+    const MGLevelH& c = h->lv[k + 1];
+    float* out = (k == 0) ? z : h->lv[k].xt;
+    TH_TRY(smooth_any(g, l, B[k], X[k], X[k + 1], c.nx, c.ny, out, s));
+    X[k] = out;
+  }
+  return TH_OK;
+}
+
+th_status mg_rz(thermal_grid* g, const float* r, const float* z, cudaStream_t s) {
+  const long long n = g->n;
+  k_mg_rz<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, g->ctl, r, z, g->partials, g->partials_stride,
+                                                      g->counters);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}

@@ -329,6 +329,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     P.ad_pairs = std::max(1, (chk + 1) / 2);
   }
   if (P.pc == TH_PC_ZLINE) TH_TRY(grid_ensure_zline(g, dt, s));
+  if (P.pc == TH_PC_MG) TH_TRY(grid_ensure_mg(g, dt, s));
   P.v4 = (g->nx % 4 == 0);
   P.uni = g->uniform;
   if (P.v4) {
@@ -642,6 +643,13 @@ static th_status enq_precond_tail(const Plan& P, const VecSet<TV>& V, cudaStream
         return enq_cheb_tail<TV, __nv_bfloat16>(P, V, g->f16.gx, g->f16.gy, g->f16.gz, st);
       return enq_cheb_tail<TV, float>(P, V, g->f32.gx, g->f32.gy, g->f32.gz, st);
     }
+  }
+  if (P.pc == TH_PC_MG) {
+    if constexpr (sizeof(TV) == 4) {
+      TH_TRY(mg_vcycle(g, V.r, V.zc[0], st));
+      return mg_rz(g, V.r, V.zc[0], st);
+    }
+    return th_fail(TH_EINVAL, "the multigrid preconditioner runs in FP32");
   }
   if (P.pc == TH_PC_ZLINE) {
     k_zline<TV><<<P.gcol, P.tb, 0, st>>>(P.d, g->ctl, g->f32.gz, g->zl_m, g->zl_c, V.r, V.zc[0], g->partials,

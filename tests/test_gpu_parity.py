@@ -390,6 +390,56 @@ def test_run_transient_long_schedule(prec):
     assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
 
 
+# ----------------------------------------------------- geometric multigrid (not in the paper)
+
+@pytest.mark.parametrize("nx,ny,mk,dt", [(37, 21, "c2", 1e-4), (37, 21, "c2", 0.0), (9, 30, "mol", 0.0),
+                                         (3, 2, "c1", 0.0), (64, 64, "c1", 1e-4)])
+def test_mg_vcycle_matches_oracle(nx, ny, mk, dt):
+    """One V-cycle (aggregation semi-coarsening, damped z-line Jacobi, exact coarsest
+    solve) in FP32 on the GPU against the oracle's FP64 V-cycle, on odd sizes, a
+    single-level grid and a grid with six levels."""
+    from oracle import multigrid as mg
+    st = STACKS[mk]()
+    A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None).tocsr()
+    g = grid_of(nx, ny, st)
+    r = ti.random_vector(A.shape[0], 17).astype(np.float32)
+    z = g.precond(cuda(r), dt, precond="mg").cpu().double().numpy()
+    z_ref = mg.vcycle(mg.hierarchy(A, nx, ny, st.L), st.L, r.astype(np.float64))
+    assert np.max(np.abs(z - z_ref)) <= 2e-5 * np.max(np.abs(z_ref))
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_mg_steady_solve(graph):
+    st = ti.stack_c2()
+    nx, ny = 70, 45
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (14, 15)], np.float64)
+    g = grid_of(nx, ny, st)
+    T, stats = g.solve_steady(cuda(P), precond="mg", tol_rel=1e-10, use_graph=graph)
+    _, sj = g.solve_steady(cuda(P), precond="jacobi", tol_rel=1e-10, use_graph=graph)
+    ref = osolve.steady(nx, ny, st, P)
+    assert stats["status"] == 0 and stats["rel_res"] <= 1e-10
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+    assert stats["inner_it"] * 5 < sj["inner_it"], (stats["inner_it"], sj["inner_it"])
+
+
+def test_mg_transient_schedule_and_invalid_precision():
+    from paper_2606_17850_gb300 import ThermalError
+    st = ti.stack_c2()
+    nx, ny, dt = 40, 26, 1e-4
+    maps = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s + j) for j in (0, 1)], np.float32)
+            for s in (60, 62)]
+    g = grid_of(nx, ny, st)
+    T = cuda(np.full(nx * ny * st.L, st.t_amb))
+    T, stats = g.run_transient([cuda(m) for m in maps], 2, 5, dt, T, precond="mg", tol_rel=1e-10)
+    sched = [maps[(s // 2) % 2].astype(np.float64) for s in range(5)]
+    ref = osolve.transient(nx, ny, st, sched, dt, np.full(nx * ny * st.L, st.t_amb))[-1]
+    assert stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+    with pytest.raises(ThermalError) as e:
+        g.solve_steady(cuda(maps[0]), precision="fp64", precond="mg")
+    assert e.value.status == 1
+
+
 # ------------------------------------- Sec. 4.4: the paper's adaptive mixed precision
 
 @pytest.mark.parametrize("nx,ny,mk,dt", [(37, 21, "c2", 1e-4), (36, 17, "mol", 0.0), (5, 3, "c1", 0.0)])
