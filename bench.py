@@ -63,6 +63,9 @@ KERNEL_BYTES = {
     "ad_cheb_a3": 28,    # A3 in FP16 (8) + z_m, z_{m-1}, r, 1/diag (16) + z_{m+1} (4)
     "ad_spmv_early": 32, # D4, gx gy gz FP32 (16) + p (8) + mu (8)
     "ad_spmv_late": 48,  # D4, gx gy gz FP64 (32) + p (8) + mu (8)
+    # one multigrid V-cycle; level 0: two smoothing sweeps (b, x, gx gy gz, s, m, w: 32 read
+    # + 4 written each) and the restriction (x, b, faces, s: 24); coarser levels add 1/3
+    "mg_vcycle": 124,
 }
 DOMINANT = "cheb_tb4"
 

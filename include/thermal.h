@@ -265,6 +265,7 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  *  16  FP32 Chebyshev step with Algorithm 3's FP32/16 product (adaptive path)
  *  17  adaptive path, early stage: FP64 mu = A p with FP32 coefficients + p^T mu
  *  18  adaptive path, late stage: the same with FP64 coefficients
+ *  19  one multigrid V-cycle (all levels; several launches)
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

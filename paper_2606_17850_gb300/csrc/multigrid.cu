@@ -165,35 +165,41 @@ __global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, cons
   }
 }
 
-// b_c = P^T (b - A x): one thread per coarse column, summing the residuals of the
-// aggregate's fine cells.
+// b_c = P^T (b - A x): one thread per fine column computes its residual layer by
+// layer; the x pair of an aggregate (adjacent lanes) is summed with a shuffle, the
+// y pair (adjacent block rows) through shared memory.  Block (32, 8): every
+// aggregate lies inside one block.
 __global__ void __launch_bounds__(256) k_mg_restrict(const Ctl* ctl, MGDev v, const float* __restrict__ b,
                                                      const float* __restrict__ x, int nxc, int nyc,
                                                      float* __restrict__ bc) {
   if (ld_int(&ctl->done)) return;
-  const int X = blockIdx.x * blockDim.x + threadIdx.x;
-  const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (X >= nxc || Y >= nyc) return;
+  __shared__ float rowsum[8][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int xx = blockIdx.x * 32 + tx, yy = blockIdx.y * 8 + ty;
+  const bool in = xx < v.nx && yy < v.ny;
   const long long pxy = (long long)v.nx * v.ny;
-  const int x0 = 2 * X, y0 = 2 * Y;
-  const int na = (x0 + 1 < v.nx) ? 2 : 1, nb = (y0 + 1 < v.ny) ? 2 : 1;
   for (int z = 0; z < v.L; ++z) {
-    float sum = 0.f;
-    for (int bb = 0; bb < nb; ++bb)
-      for (int aa = 0; aa < na; ++aa) {
-        const int xx = x0 + aa, yy = y0 + bb;
-        const long long i = idx3(v.nx, v.ny, xx, yy, z);
-        const float xi = x[i];
-        float a = v.s[i] * xi;
-        if (xx + 1 < v.nx) a += v.gx[i] * (xi - x[i + 1]);
-        if (xx > 0) a += v.gx[i - 1] * (xi - x[i - 1]);
-        if (yy + 1 < v.ny) a += v.gy[i] * (xi - x[i + v.nx]);
-        if (yy > 0) a += v.gy[i - v.nx] * (xi - x[i - v.nx]);
-        if (z + 1 < v.L) a += v.gz[i] * (xi - x[i + pxy]);
-        if (z > 0) a += v.gz[i - pxy] * (xi - x[i - pxy]);
-        sum += b[i] - a;
-      }
-    bc[idx3(nxc, nyc, X, Y, z)] = sum;
+    float r = 0.f;
+    if (in) {
+      const long long i = idx3(v.nx, v.ny, xx, yy, z);
+      const float xi = x[i];
+      float a = v.s[i] * xi;
+      if (xx + 1 < v.nx) a += v.gx[i] * (xi - x[i + 1]);
+      if (xx > 0) a += v.gx[i - 1] * (xi - x[i - 1]);
+      if (yy + 1 < v.ny) a += v.gy[i] * (xi - x[i + v.nx]);
+      if (yy > 0) a += v.gy[i - v.nx] * (xi - x[i - v.nx]);
+      if (z + 1 < v.L) a += v.gz[i] * (xi - x[i + pxy]);
+      if (z > 0) a += v.gz[i - pxy] * (xi - x[i - pxy]);
+      r = b[i] - a;
+    }
+    r += __shfl_xor_sync(0xffffffffu, r, 1);  // x pair (2X, 2X+1); 0 from a column outside the grid
+    rowsum[ty][tx] = r;
+    __syncthreads();
+    if (((tx | ty) & 1) == 0) {
+      const int X = xx >> 1, Y = yy >> 1;
+      if (X < nxc && Y < nyc) bc[idx3(nxc, nyc, X, Y, z)] = rowsum[ty][tx] + rowsum[ty + 1][tx];
+    }
+    __syncthreads();
   }
 }
 
@@ -431,7 +437,7 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
     const MGLevelH& l = h->lv[k];
     const MGLevelH& c = h->lv[k + 1];
     TH_TRY(smooth_any(g, l, B[k], nullptr, nullptr, 1, 1, X[k], s));
-    k_mg_restrict<<<col_grid(c.nx, c.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), B[k], X[k], c.nx, c.ny,
+    k_mg_restrict<<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), B[k], X[k], c.nx, c.ny,
                                                                 h->lv[k + 1].b);
     TH_CHECK_LAUNCH();
   }

@@ -1441,15 +1441,16 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 18) return th_fail(TH_EINVAL, "invalid argument");
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 19) return th_fail(TH_EINVAL, "invalid argument");
   if (kernel >= 13 && kernel <= 15 && !(g->uniform && g->nx % 4 == 0))
     return th_fail(TH_EINVAL, "fused Chebyshev steps need a layer-uniform grid with nx %% 4 == 0");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
-  o.precond = (kernel >= 13 && kernel <= 15) ? TH_PC_CHEB : TH_PC_JACOBI;
+  o.precond = (kernel >= 13 && kernel <= 15) ? TH_PC_CHEB : (kernel == 19 ? TH_PC_MG : TH_PC_JACOBI);
   o.cheb_degree = 5;  // one chunk of four fused steps
-  o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64 : (kernel >= 16 ? TH_PREC_ADAPTIVE : TH_PREC_MIXED_IR);
+  o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64
+                : ((kernel >= 16 && kernel <= 18) ? TH_PREC_ADAPTIVE : TH_PREC_MIXED_IR);
   Plan P;
   TH_TRY(make_plan(g, dt, &o, TH_F32, dt > 0.0, P, s));
   TH_TRY(ensure_stage(g, sizeof(float) * (size_t)g->n));
@@ -1480,6 +1481,7 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   const float c1 = 0.5f, c2 = 0.5f;
   auto launch = [&]() -> th_status {
     const bool uni = g->uniform && kernel < 9;  // ids 9..12: the per-face variants
+    if (kernel == 19) return mg_vcycle(g, g->r32, g->zc32[0], s);
     if (kernel == 16) {
       k_ad_cheb<true><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, P.qd, P.qd_sinv, g->r32, g->zc32[0], g->zc32[1], g->zc32[2],
                                             g->invd32, c1, c2);
