@@ -246,6 +246,9 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
+    # the oracle as it stands, on one host thread (numpy/BLAS threads pinned before import)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     import numpy as np
     from oracle import discretisation as disc, krylov
     inst, maps = workload_arrays()
@@ -262,7 +265,7 @@ def run_reference(args):
         if s >= args.warmup:
             step_ms.append(dt_ms)
     v = sum(step_ms) / len(step_ms)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    cores = 1
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -46,6 +46,21 @@ struct TBParams {
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
 };
 
+// FIRST chunk: the CG update (Algorithm 1's AXPYs) fused in front of the first
+// Chebyshev steps.  Staged boxes: r_k (slot 0) and mu_k = A p_k (slot 1, not at the
+// start of an inner solve); every grown-tile column forms r_{k+1} = r_k - alpha mu_k
+// (or r scaled to unit norm at the start), z_1 = D^-1 r_{k+1} / theta in registers,
+// and the interior writes r_{k+1} to a second buffer (other tiles still stage r_k
+// as their halo) and x += alpha p (x = 0 at the start).
+struct TBFirst {
+  float* r_out;     // r_{k+1} (interior)
+  float* x;         // inner-solve iterate d (interior)
+  const float* p;   // search direction p_k
+  float inv_theta;  // 1 / theta of the Chebyshev recurrence
+  int init;         // start of an inner solve (no alpha, x = 0)
+  int scale_r;      // at the start: r <- r * rscale (unit norm)
+};
+
 __device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void tb_mbar_init(unsigned long long* bar, unsigned count) {
@@ -103,13 +118,17 @@ constexpr size_t tb_smem_bytes() {
 // (EY - 2 STEPS) columns.  Layers L..LMAX-1 (when the stack has fewer than LMAX
 // layers) are carried as zeros: their coefficients and inverse diagonal are 0, so
 // they stay 0 and the step loop needs no per-layer guard.
-template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST>
+template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST, bool FIRST = false>
 __global__ void __launch_bounds__(TB_EX * EY, 1)
     k_cheb_tb(Dims d, int ntx, int ntiles, int has_prev, Ctl* ctl,
               const __grid_constant__ CUtensorMap m_cur, const __grid_constant__ CUtensorMap m_prev,
               const __grid_constant__ CUtensorMap m_r, float* __restrict__ out_cur, float* __restrict__ out_prev,
-              const __grid_constant__ TBParams<LMAX> P, double* partials, int stride, unsigned* counter) {
-  if (ld_int(&ctl->done)) return;
+              const __grid_constant__ TBParams<LMAX> P, TBFirst F, double* partials, int stride, unsigned* counter) {
+  if (FIRST && F.init) {
+    if (ld_int(&ctl->outer_done)) return;
+  } else if (ld_int(&ctl->done)) {
+    return;
+  }
   constexpr int H = STEPS;
   constexpr int TX = TB_EX - 2 * H, TY = EY - 2 * H;  // interior of a tile
   constexpr int PL = EY * TB_EX;  // floats per layer plane
@@ -123,7 +142,10 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
   const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
-  const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
+  // FIRST: r_k and (unless at the start) mu_k; otherwise z_m, z_{m-1} (if any), r
+  const unsigned tx_bytes = box_bytes * (FIRST ? (F.init ? 1u : 2u) : (has_prev ? 3u : 2u));
+  const float alpha = (FIRST && !F.init) ? ctl_alpha<float>(ctl) : 0.f;
+  const float rs = (FIRST && F.init && F.scale_r) ? __ldcg(&ctl->rscale_f) : 1.f;
 
   if (tid == 0) {
     tb_mbar_init(bar, 1);
@@ -136,12 +158,16 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     const int xa = ((t % ntx) * TX - H) & ~3, y0 = (t / ntx) * TY - H;
     tb_mbar_expect(bar, tx_bytes);
     tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
-    if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
-    tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
+    if (FIRST) {
+      if (!F.init) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+    } else {
+      if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+      tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
+    }
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
 
-  float part[1] = {0.f};
+  float part[2] = {0.f, 0.f};  // r^T r (FIRST), r^T z (LAST) over interior cells
   unsigned parity = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const bool timed_out = !tb_mbar_wait(bar, parity);
@@ -164,10 +190,18 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
       const bool on = z < L;
-      cur[z] = on ? stage[z * SL + st] : 0.f;
-      prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
-      rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
       inv[z] = P.invd[nxf + 3 * nyf][z];
+      if (FIRST) {
+        const float r0 = on ? stage[z * SL + st] : 0.f;
+        const float rn = F.init ? r0 * rs : r0 - alpha * (on ? stage[(LMAX + z) * SL + st] : 0.f);
+        rr[z] = rn;
+        cur[z] = (SCALED ? rn * inv[z] : rn) * F.inv_theta;  // z_1
+        prv[z] = 0.f;                                          // z_0
+      } else {
+        cur[z] = on ? stage[z * SL + st] : 0.f;
+        prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
+        rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
+      }
     }
     __syncthreads();  // staging buffer consumed by every thread
     const int tn = t + gridDim.x;
@@ -219,14 +253,23 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
           const long long i = base + d.pxy * z;
           out_cur[i] = cur[z];
           if (out_prev) out_prev[i] = prv[z];
-          if (LAST) part[0] += rr[z] * cur[z];
+          if (FIRST) {
+            F.r_out[i] = rr[z];
+            F.x[i] = F.init ? 0.f : F.x[i] + alpha * F.p[i];
+            part[0] += rr[z] * rr[z];
+          }
+          if (LAST) part[1] += rr[z] * cur[z];
         }
       }
     }
   }
-  if (!LAST) return;
-  double tot[1];
-  if (!grid_reduce<float, 1>(part, partials, stride, counter, tot)) return;
-  ctl->rz_next = tot[0];
-  ctl_set_beta(ctl);
+  if (!LAST && !FIRST) return;
+  double tot[2];
+  if (!grid_reduce<float, 2>(part, partials, stride, counter, tot)) return;
+  if (FIRST) {
+    fin_update(ctl, tot[0], tot[1], F.init != 0, LAST ? 1 : 0);
+  } else {
+    ctl->rz_next = tot[1];
+    ctl_set_beta(ctl);
+  }
 }
