@@ -347,14 +347,16 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     cheb_coeffs(P.lmin, P.lmax, P.k, P.c1, P.c2, &P.inv_theta);
     P.pc_spmv = P.k - 1;
     const int fuse = o->cheb_fuse == 0 ? TB_H : o->cheb_fuse;
-    if (P.prec != TH_PREC_FP64 && !P.ad && P.v4 && P.uni && fuse > 1 && P.k > 1) {
+    // fused chunks exist for the Jacobi-scaled form (the default); the unscaled
+    // polynomial of the paper runs one step per launch
+    if (P.prec != TH_PREC_FP64 && !P.ad && P.v4 && P.uni && P.scaled && fuse > 1 && P.k > 1) {
       // register columns: up to 8 layers with 32 x 32 threads, up to 12 with 32 x 24
       P.tb_lmax = g->L <= 8 ? 8 : (g->L <= 12 ? 12 : 0);
       if (P.tb_lmax > 0) {
         P.fused = true;
-        // the first chunk forms z_1 itself from the update it fuses (Jacobi-scaled form);
-        // mu (pool slot 3) is one of its inputs, so its outputs take slots 0 and 1
-        P.fuse_update = P.scaled != 0;
+        // the first chunk forms z_1 itself from the update it fuses; mu (pool slot 3) is
+        // one of its inputs, so its outputs take slots 0 and 1
+        P.fuse_update = true;
         int cur = P.fuse_update ? -1 : 0, prev = -1, m = 1, left = P.k - 1;
         while (left > 0) {
           const int st = std::min(fuse, left);
@@ -589,15 +591,13 @@ static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st
   }
 }
 
-template <int LM, int EY, bool SC>
+template <int LM, int EY>
 static th_status tb_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last,
                           const TBUpd* u = nullptr) {
-  if constexpr (SC) {  // the fused update exists for the Jacobi-scaled form only
-    if (u) return last ? tb_steps<LM, EY, SC, true, true>(P, V, st, c, u) : tb_steps<LM, EY, SC, false, true>(P, V, st, c, u);
-  }
-  if (u) return th_fail(TH_ESTATE, "fused update without Jacobi scaling");
-  return last ? tb_steps<LM, EY, SC, true, false>(P, V, st, c, nullptr)
-              : tb_steps<LM, EY, SC, false, false>(P, V, st, c, nullptr);
+  if (u) return last ? tb_steps<LM, EY, true, true, true>(P, V, st, c, u)
+                     : tb_steps<LM, EY, true, false, true>(P, V, st, c, u);
+  return last ? tb_steps<LM, EY, true, true, false>(P, V, st, c, nullptr)
+              : tb_steps<LM, EY, true, false, false>(P, V, st, c, nullptr);
 }
 
 // The chunk chain of one preconditioner application; with a fused update the first
@@ -607,13 +607,8 @@ static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st
     const bool last = (ci + 1 == P.chunks.size());
     const Plan::Chunk& c = P.chunks[ci];
     const TBUpd* uc = (ci == 0) ? u : nullptr;
-    if (P.tb_lmax == 8) {
-      if (P.scaled) TH_TRY((tb_chunk<8, 32, true>(P, V, st, c, last, uc)));
-      else TH_TRY((tb_chunk<8, 32, false>(P, V, st, c, last, uc)));
-    } else {
-      if (P.scaled) TH_TRY((tb_chunk<12, 24, true>(P, V, st, c, last, uc)));
-      else TH_TRY((tb_chunk<12, 24, false>(P, V, st, c, last, uc)));
-    }
+    if (P.tb_lmax == 8) TH_TRY((tb_chunk<8, 32>(P, V, st, c, last, uc)));
+    else TH_TRY((tb_chunk<12, 24>(P, V, st, c, last, uc)));
   }
   return TH_OK;
 }
@@ -1557,9 +1552,8 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
     if (kernel >= 13) {
       // one inner chunk: z_m, z_{m-1}, r in; z_{m+S}, z_{m+S-1} out (no reduction)
       const Plan::Chunk c{kernel == 13 ? 4 : (kernel == 14 ? 2 : 3), 1, 0, 1, 2, 3};
-      if (P.tb_lmax == 8) return P.scaled ? tb_chunk<8, 32, true>(P, V, s, c, false)
-                                          : tb_chunk<8, 32, false>(P, V, s, c, false);
-      return P.scaled ? tb_chunk<12, 24, true>(P, V, s, c, false) : tb_chunk<12, 24, false>(P, V, s, c, false);
+      if (P.tb_lmax == 8) return tb_chunk<8, 32>(P, V, s, c, false);
+      return tb_chunk<12, 24>(P, V, s, c, false);
     }
     const int kk = (kernel >= 9) ? (int[]){1, 3, 8, 0}[kernel - 9] : kernel;
     switch (kk) {
