@@ -63,6 +63,14 @@ struct TBFirst {
 
 __device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// 4-byte asynchronous global -> shared copy (completes at tb_cp_wait)
+__device__ __forceinline__ void tb_cp4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tb_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void tb_cp_wait() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void tb_mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tb_smem(bar)), "r"(count) : "memory");
 }
@@ -209,6 +217,22 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(tn);
     }
+    // FIRST with four steps: the interior's x and p are fetched into the unused third
+    // staging slot now and consumed after the steps (the copy latency hides behind them)
+    constexpr bool XP_ASYNC = FIRST && STEPS == 4;
+    static_assert(!XP_ASYNC || 2 * LMAX * TX * TY <= LMAX * SL, "x, p staging exceeds the free slot");
+    const bool interior_col = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
+    const int itid = (ex - H) + TX * (ey - H);
+    float* xs = stage + 2 * LMAX * SL;  // [LMAX][TY][TX] x, then [LMAX][TY][TX] p
+    if (XP_ASYNC && !F.init && interior_col) {
+      const long long base = (long long)gx + (long long)d.nx * gy;
+#pragma unroll
+      for (int z = 0; z < LMAX; ++z)
+        if (z < L) {
+          tb_cp4(xs + z * TX * TY + itid, F.x + base + d.pxy * z);
+          tb_cp4(xs + (LMAX + z) * TX * TY + itid, F.p + base + d.pxy * z);
+        }
+    }
     // neighbour offsets inside a plane; a missing neighbour reads the cell itself
     const int oR = tid + ((gx + 1 < d.nx) ? 1 : 0), oL = tid - ((gx > 0) ? 1 : 0);
     const int oU = tid + ((gy + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gy > 0) ? TB_EX : 0);
@@ -255,7 +279,16 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
           if (out_prev) out_prev[i] = prv[z];
           if (FIRST) {
             F.r_out[i] = rr[z];
-            F.x[i] = F.init ? 0.f : F.x[i] + alpha * F.p[i];
+            float xn = 0.f;
+            if (!F.init) {
+              if (XP_ASYNC) {
+                if (z == 0) tb_cp_wait();
+                xn = xs[z * TX * TY + itid] + alpha * xs[(LMAX + z) * TX * TY + itid];
+              } else {
+                xn = F.x[i] + alpha * F.p[i];
+              }
+            }
+            F.x[i] = xn;
             part[0] += rr[z] * rr[z];
           }
           if (LAST) part[1] += rr[z] * cur[z];
