@@ -274,7 +274,7 @@ thermal_grid::~thermal_grid() {
   dfree(theta_n); dfree(r64); dfree(mu64);
   for (auto& p : p64) dfree(p);
   for (auto& p : zc64) dfree(p);
-  dfree(r32); dfree(r32b); dfree(d32); dfree(mu32);
+  dfree(r32); dfree(d32); dfree(mu32);
   for (auto& p : p32) dfree(p);
   for (auto& p : zc32) dfree(p);
   dfree(partials); dfree(counters); dfree(ctl); dfree(lz);
@@ -419,7 +419,6 @@ th_status grid_ensure_workspace(thermal_grid* g, bool need64, cudaStream_t s) {
     for (auto& p : g->theta) TH_TRY(dalloc(&p, n));
     TH_TRY(dalloc(&g->theta_n, n));
     TH_TRY(dalloc(&g->r32, n));
-    TH_TRY(dalloc(&g->r32b, n));
     TH_TRY(dalloc(&g->d32, n));
     TH_TRY(dalloc(&g->mu32, n));
     for (auto& p : g->p32) TH_TRY(dalloc(&p, n));

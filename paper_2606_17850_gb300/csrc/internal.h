@@ -109,7 +109,6 @@ struct thermal_grid {
   double *theta_n = nullptr;
   double *r64 = nullptr, *p64[2] = {nullptr, nullptr}, *mu64 = nullptr, *zc64[3] = {nullptr, nullptr, nullptr};
   float *r32 = nullptr, *d32 = nullptr, *p32[2] = {nullptr, nullptr}, *mu32 = nullptr;
-  float* r32b = nullptr;  // second FP32 residual buffer (CG update fused into the Chebyshev chain)
   float *zc32[3] = {nullptr, nullptr, nullptr};
   // mixed path: theta and theta_n as double-float (hi, lo) pairs
   float *th_hi = nullptr, *th_lo = nullptr, *thn_hi = nullptr, *thn_lo = nullptr;

@@ -46,30 +46,7 @@ struct TBParams {
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
 };
 
-// FIRST chunk: the CG update (Algorithm 1's AXPYs) fused in front of the first
-// Chebyshev steps.  Staged boxes: r_k (slot 0) and mu_k = A p_k (slot 1, not at the
-// start of an inner solve); every grown-tile column forms r_{k+1} = r_k - alpha mu_k
-// (or r scaled to unit norm at the start), z_1 = D^-1 r_{k+1} / theta in registers,
-// and the interior writes r_{k+1} to a second buffer (other tiles still stage r_k
-// as their halo) and x += alpha p (x = 0 at the start).
-struct TBFirst {
-  float* r_out;     // r_{k+1} (interior)
-  float* x;         // inner-solve iterate d (interior)
-  const float* p;   // search direction p_k
-  float inv_theta;  // 1 / theta of the Chebyshev recurrence
-  int init;         // start of an inner solve (no alpha, x = 0)
-  int scale_r;      // at the start: r <- r * rscale (unit norm)
-};
-
 __device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-// 4-byte asynchronous global -> shared copy (completes at tb_cp_wait)
-__device__ __forceinline__ void tb_cp4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tb_smem(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void tb_cp_wait() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
-}
 
 __device__ __forceinline__ void tb_mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tb_smem(bar)), "r"(count) : "memory");
@@ -126,17 +103,13 @@ constexpr size_t tb_smem_bytes() {
 // (EY - 2 STEPS) columns.  Layers L..LMAX-1 (when the stack has fewer than LMAX
 // layers) are carried as zeros: their coefficients and inverse diagonal are 0, so
 // they stay 0 and the step loop needs no per-layer guard.
-template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST, bool FIRST = false>
+template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST>
 __global__ void __launch_bounds__(TB_EX * EY, 1)
     k_cheb_tb(Dims d, int ntx, int ntiles, int has_prev, Ctl* ctl,
               const __grid_constant__ CUtensorMap m_cur, const __grid_constant__ CUtensorMap m_prev,
               const __grid_constant__ CUtensorMap m_r, float* __restrict__ out_cur, float* __restrict__ out_prev,
-              const __grid_constant__ TBParams<LMAX> P, TBFirst F, double* partials, int stride, unsigned* counter) {
-  if (FIRST && F.init) {
-    if (ld_int(&ctl->outer_done)) return;
-  } else if (ld_int(&ctl->done)) {
-    return;
-  }
+              const __grid_constant__ TBParams<LMAX> P, double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
   constexpr int H = STEPS;
   constexpr int TX = TB_EX - 2 * H, TY = EY - 2 * H;  // interior of a tile
   constexpr int PL = EY * TB_EX;  // floats per layer plane
@@ -150,10 +123,7 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
   const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
-  // FIRST: r_k and (unless at the start) mu_k; otherwise z_m, z_{m-1} (if any), r
-  const unsigned tx_bytes = box_bytes * (FIRST ? (F.init ? 1u : 2u) : (has_prev ? 3u : 2u));
-  const float alpha = (FIRST && !F.init) ? ctl_alpha<float>(ctl) : 0.f;
-  const float rs = (FIRST && F.init && F.scale_r) ? __ldcg(&ctl->rscale_f) : 1.f;
+  const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
 
   if (tid == 0) {
     tb_mbar_init(bar, 1);
@@ -166,16 +136,12 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     const int xa = ((t % ntx) * TX - H) & ~3, y0 = (t / ntx) * TY - H;
     tb_mbar_expect(bar, tx_bytes);
     tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
-    if (FIRST) {
-      if (!F.init) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
-    } else {
-      if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
-      tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
-    }
+    if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+    tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
 
-  float part[2] = {0.f, 0.f};  // r^T r (FIRST), r^T z (LAST) over interior cells
+  float part[1] = {0.f};
   unsigned parity = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const bool timed_out = !tb_mbar_wait(bar, parity);
@@ -198,40 +164,16 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
       const bool on = z < L;
+      cur[z] = on ? stage[z * SL + st] : 0.f;
+      prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
+      rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
       inv[z] = P.invd[nxf + 3 * nyf][z];
-      if (FIRST) {
-        const float r0 = on ? stage[z * SL + st] : 0.f;
-        const float rn = F.init ? r0 * rs : r0 - alpha * (on ? stage[(LMAX + z) * SL + st] : 0.f);
-        rr[z] = rn;
-        cur[z] = (SCALED ? rn * inv[z] : rn) * F.inv_theta;  // z_1
-        prv[z] = 0.f;                                          // z_0
-      } else {
-        cur[z] = on ? stage[z * SL + st] : 0.f;
-        prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
-        rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
-      }
     }
     __syncthreads();  // staging buffer consumed by every thread
     const int tn = t + gridDim.x;
     if (tid == 0 && tn < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(tn);
-    }
-    // FIRST with four steps: the interior's x and p are fetched into the unused third
-    // staging slot now and consumed after the steps (the copy latency hides behind them)
-    constexpr bool XP_ASYNC = FIRST && STEPS == 4;
-    static_assert(!XP_ASYNC || 2 * LMAX * TX * TY <= LMAX * SL, "x, p staging exceeds the free slot");
-    const bool interior_col = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
-    const int itid = (ex - H) + TX * (ey - H);
-    float* xs = stage + 2 * LMAX * SL;  // [LMAX][TY][TX] x, then [LMAX][TY][TX] p
-    if (XP_ASYNC && !F.init && interior_col) {
-      const long long base = (long long)gx + (long long)d.nx * gy;
-#pragma unroll
-      for (int z = 0; z < LMAX; ++z)
-        if (z < L) {
-          tb_cp4(xs + z * TX * TY + itid, F.x + base + d.pxy * z);
-          tb_cp4(xs + (LMAX + z) * TX * TY + itid, F.p + base + d.pxy * z);
-        }
     }
     // neighbour offsets inside a plane; a missing neighbour reads the cell itself
     const int oR = tid + ((gx + 1 < d.nx) ? 1 : 0), oL = tid - ((gx > 0) ? 1 : 0);
@@ -277,32 +219,14 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
           const long long i = base + d.pxy * z;
           out_cur[i] = cur[z];
           if (out_prev) out_prev[i] = prv[z];
-          if (FIRST) {
-            F.r_out[i] = rr[z];
-            float xn = 0.f;
-            if (!F.init) {
-              if (XP_ASYNC) {
-                if (z == 0) tb_cp_wait();
-                xn = xs[z * TX * TY + itid] + alpha * xs[(LMAX + z) * TX * TY + itid];
-              } else {
-                xn = F.x[i] + alpha * F.p[i];
-              }
-            }
-            F.x[i] = xn;
-            part[0] += rr[z] * rr[z];
-          }
-          if (LAST) part[1] += rr[z] * cur[z];
+          if (LAST) part[0] += rr[z] * cur[z];
         }
       }
     }
   }
-  if (!LAST && !FIRST) return;
-  double tot[2];
-  if (!grid_reduce<float, 2>(part, partials, stride, counter, tot)) return;
-  if (FIRST) {
-    fin_update(ctl, tot[0], tot[1], F.init != 0, LAST ? 1 : 0);
-  } else {
-    ctl->rz_next = tot[1];
-    ctl_set_beta(ctl);
-  }
+  if (!LAST) return;
+  double tot[1];
+  if (!grid_reduce<float, 1>(part, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
 }

@@ -53,7 +53,6 @@ struct Plan {
   // pool of four FP32 buffers {zc0, zc1, zc2, mu} (indices 0..3)
   struct Chunk { int steps, m0, in_cur, in_prev, out_cur, out_prev; };
   bool fused = false;  // temporal blocking active
-  bool fuse_update = false;  // the CG update runs inside the first chunk (r ping-pongs between r32, r32b)
   int tb_lmax = 8;  // layer capacity of the fused kernel (8: 32 x 32 tiles, 12: 32 x 24)
   std::vector<Chunk> chunks;
   int zfin = -1;  // pool index of the preconditioned vector (-1: the per-step rule)
@@ -354,15 +353,12 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
       P.tb_lmax = g->L <= 8 ? 8 : (g->L <= 12 ? 12 : 0);
       if (P.tb_lmax > 0) {
         P.fused = true;
-        // the first chunk forms z_1 itself from the update it fuses; mu (pool slot 3) is
-        // one of its inputs, so its outputs take slots 0 and 1
-        P.fuse_update = true;
-        int cur = P.fuse_update ? -1 : 0, prev = -1, m = 1, left = P.k - 1;
+        int cur = 0, prev = -1, m = 1, left = P.k - 1;
         while (left > 0) {
           const int st = std::min(fuse, left);
           int oc = -1, op = -1;
           for (int b = 0; b < 4 && (oc < 0 || op < 0); ++b) {
-            if (b == cur || b == prev || (cur < 0 && b == 3)) continue;
+            if (b == cur || b == prev) continue;
             if (oc < 0) oc = b; else op = b;
           }
           const bool last = (left == st);
@@ -511,17 +507,8 @@ static int sm_count() {
   return n[dev];
 }
 
-// fused-update arguments of a FIRST chunk: r_k in, r_{k+1} out, p_k, start flags
-struct TBUpd {
-  const float* r_in = nullptr;
-  float* r_out = nullptr;
-  const float* p = nullptr;
-  int init = 0, scale_r = 0;
-};
-
-template <int LM, int EY, int ST, bool SC, bool LA, bool FI = false>
-static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c,
-                           const TBUpd* u = nullptr) {
+template <int LM, int EY, int ST, bool SC, bool LA>
+static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   thermal_grid* g = P.g;
   constexpr int TX = TB_EX - 2 * ST, TY = EY - 2 * ST;
   float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
@@ -553,78 +540,48 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
       }
   }
   CUtensorMap mc, mp, mr;
-  TBFirst F{};
-  if (FI) {  // staged r_k and mu_k
-    TH_TRY(tb_map(&mc, P.d, u->r_in, EY));
-    TH_TRY(tb_map(&mp, P.d, V.mu, EY));
-    mr = mc;
-    F = TBFirst{u->r_out, V.x, u->p, (float)P.inv_theta, u->init, u->scale_r};
-  } else {
-    TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], EY));
-    TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], EY));
-    TH_TRY(tb_map(&mr, P.d, V.r, EY));
-  }
+  TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], EY));
+  TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], EY));
+  TH_TRY(tb_map(&mr, P.d, V.r, EY));
   const int ntx = (P.d.nx + TX - 1) / TX;
   const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
   const size_t smem = tb_smem_bytes<LM, EY>();
-  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, EY, ST, SC, LA, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, EY, ST, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   const int nblk = std::min(ntiles, sm_count());
   if (nblk > g->partials_stride) return th_fail(TH_ESTATE, "partials buffer smaller than the temporal-blocking grid");
-  k_cheb_tb<LM, EY, ST, SC, LA, FI><<<nblk, dim3(TB_EX, EY), smem, st>>>(
+  k_cheb_tb<LM, EY, ST, SC, LA><<<nblk, dim3(TB_EX, EY), smem, st>>>(
       P.d, ntx, ntiles, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, pool[c.out_cur],
-      c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, F, g->partials, g->partials_stride, g->counters);
+      c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
 
-// chunk dispatch on (steps, last chunk, first chunk with the fused update)
-template <int LM, int EY, bool SC, bool LA, bool FI>
-static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c,
-                          const TBUpd* u) {
+// chunk dispatch on (steps, last chunk)
+template <int LM, int EY, bool SC, bool LA>
+static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   switch (c.steps) {
-    case 1: return tb_launch<LM, EY, 1, SC, LA, FI>(P, V, st, c, u);
-    case 2: return tb_launch<LM, EY, 2, SC, LA, FI>(P, V, st, c, u);
-    case 3: return tb_launch<LM, EY, 3, SC, LA, FI>(P, V, st, c, u);
-    case 4: return tb_launch<LM, EY, 4, SC, LA, FI>(P, V, st, c, u);
+    case 1: return tb_launch<LM, EY, 1, SC, LA>(P, V, st, c);
+    case 2: return tb_launch<LM, EY, 2, SC, LA>(P, V, st, c);
+    case 3: return tb_launch<LM, EY, 3, SC, LA>(P, V, st, c);
+    case 4: return tb_launch<LM, EY, 4, SC, LA>(P, V, st, c);
     default: return th_fail(TH_ESTATE, "temporal-blocking chunk with %d steps", c.steps);
   }
 }
 
 template <int LM, int EY>
-static th_status tb_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last,
-                          const TBUpd* u = nullptr) {
-  if (u) return last ? tb_steps<LM, EY, true, true, true>(P, V, st, c, u)
-                     : tb_steps<LM, EY, true, false, true>(P, V, st, c, u);
-  return last ? tb_steps<LM, EY, true, true, false>(P, V, st, c, nullptr)
-              : tb_steps<LM, EY, true, false, false>(P, V, st, c, nullptr);
+static th_status tb_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last) {
+  return last ? tb_steps<LM, EY, true, true>(P, V, st, c) : tb_steps<LM, EY, true, false>(P, V, st, c);
 }
 
-// The chunk chain of one preconditioner application; with a fused update the first
-// chunk takes u (and V.r is r_{k+1} for the later chunks).
-static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st, const TBUpd* u = nullptr) {
+static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st) {
   for (size_t ci = 0; ci < P.chunks.size(); ++ci) {
     const bool last = (ci + 1 == P.chunks.size());
     const Plan::Chunk& c = P.chunks[ci];
-    const TBUpd* uc = (ci == 0) ? u : nullptr;
-    if (P.tb_lmax == 8) TH_TRY((tb_chunk<8, 32>(P, V, st, c, last, uc)));
-    else TH_TRY((tb_chunk<12, 24>(P, V, st, c, last, uc)));
+    if (P.tb_lmax == 8) TH_TRY((tb_chunk<8, 32>(P, V, st, c, last)));
+    else TH_TRY((tb_chunk<12, 24>(P, V, st, c, last)));
   }
   return TH_OK;
-}
-
-// CG update fused into the first chunk: r_in -> r_out, then the rest of the chain on r_out
-static th_status tb_update_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st, int init, int scale_r,
-                                 const float* r_in, float* r_out, const float* p) {
-  TBUpd u;
-  u.r_in = r_in;
-  u.r_out = r_out;
-  u.p = p;
-  u.init = init;
-  u.scale_r = scale_r;
-  VecSet<float> W = V;
-  W.r = r_out;
-  return tb_chain(P, W, st, &u);
 }
 
 template <typename TV, typename TC>
@@ -632,10 +589,7 @@ static th_status enq_cheb_tail(const Plan& P, const VecSet<TV>& V, const TC* gx,
                                cudaStream_t st) {
   thermal_grid* g = P.g;
   if constexpr (sizeof(TV) == 4) {
-    if (P.fused) {
-      if (P.fuse_update) return th_fail(TH_ESTATE, "fused Chebyshev chain needs its fused update");
-      return tb_chain(P, V, st);
-    }
+    if (P.fused) return tb_chain(P, V, st);
   }
   for (int m = 1; m < P.k; ++m) {
     const TV* zprev = (m >= 2) ? V.zc[(m - 2) % 3] : nullptr;
@@ -722,13 +676,6 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
                                                     g->partials_stride, g->counters);
   }
   TH_CHECK_LAUNCH();
-  if constexpr (sizeof(TV) == 4) {
-    if (P.fuse_update) {  // r ping-pongs: r32b -> r32 (parity 0), r32 -> r32b (parity 1)
-      float* ra = P.g->r32b;
-      float* rb = P.g->r32;
-      return tb_update_chain(P, V, st, 0, 0, parity == 0 ? ra : rb, parity == 0 ? rb : ra, V.p[1 - parity]);
-    }
-  }
   TH_TRY((enq_update<TV, false>(P, V, st, 1 - parity, 1, 0)));
   return enq_precond_tail<TV>(P, V, st);
 }
@@ -871,7 +818,6 @@ struct Pieces {
   // mixed: scale r, x = 0, z_0 = M r
   th_status inner_init(cudaStream_t st) {
     VecSet<float> V = vec32(P.g);
-    if (P.fuse_update) return tb_update_chain(P, V, st, 1, 1, P.g->r32, P.g->r32b, nullptr);
     TH_TRY((enq_update<float, true>(P, V, st, 0, 1, 1)));
     return enq_precond_tail<float>(P, V, st);
   }
@@ -1479,12 +1425,8 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
   const size_t bytes = sizeof(float) * (size_t)g->n;
   TH_CUDA(cudaMemcpyAsync(g->r32, r, bytes, cudaMemcpyDeviceToDevice, s));
   VecSet<float> V = vec32(g);
-  if (P.fuse_update) {
-    TH_TRY(tb_update_chain(P, V, s, 1, 0, g->r32, g->r32b, nullptr));
-  } else {
-    TH_TRY((enq_update<float, true>(P, V, s, 0, 1, 0)));
-    TH_TRY(enq_precond_tail<float>(P, V, s));
-  }
+  TH_TRY((enq_update<float, true>(P, V, s, 0, 1, 0)));
+  TH_TRY(enq_precond_tail<float>(P, V, s));
   TH_CUDA(cudaMemcpyAsync(z, z_final(P, V), bytes, cudaMemcpyDeviceToDevice, s));
   TH_CUDA(cudaStreamSynchronize(s));
   return TH_OK;
