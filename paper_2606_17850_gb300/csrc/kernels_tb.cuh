@@ -92,16 +92,11 @@ __device__ __forceinline__ void tb_tma_3d(float* dst, const CUtensorMap* map, in
       : "memory");
 }
 
-// floats of slack before and after the planes: every thread of the grown tile
-// updates every step, so the edge rows and columns read one row or one element
-// past the plane
-#define TB_GUARD 64
-
 // dynamic shared memory of one CTA: staging (3 boxes) + two planes + mbarrier,
 // plus room to align the staging boxes to 128 bytes
 template <int LMAX, int EY>
 constexpr size_t tb_smem_bytes() {
-  return ((size_t)3 * LMAX * EY * TB_BW + (size_t)2 * LMAX * EY * TB_EX + 2 * TB_GUARD) * sizeof(float) + 16 + 128;
+  return ((size_t)3 * LMAX * EY * TB_BW + (size_t)2 * LMAX * EY * TB_EX) * sizeof(float) + 16 + 128;
 }
 
 // STEPS steps with a halo of STEPS cells: the interior is (32 - 2 STEPS) x
@@ -122,8 +117,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   extern __shared__ __align__(128) float tb_dyn[];
   float* tb_sm = tb_dyn + (((128u - (tb_smem(tb_dyn) & 127u)) & 127u) >> 2);  // 128-byte aligned
   float* stage = tb_sm;                    // [3][LMAX][EY][TB_BW]: z_m, z_{m-1}, r
-  float* plane = tb_sm + 3 * LMAX * SL + TB_GUARD;  // [2][LMAX][EY][TB_EX], guarded on both sides
-  unsigned long long* bar = (unsigned long long*)(plane + 2 * LMAX * PL + TB_GUARD);
+  float* plane = tb_sm + 3 * LMAX * SL;    // [2][LMAX][EY][TB_EX]
+  unsigned long long* bar = (unsigned long long*)(plane + 2 * LMAX * PL);
   const int L = d.L;
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
@@ -189,11 +184,9 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
 #pragma unroll
       for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = cur[z];
       __syncthreads();
-      // Every column of the grown tile updates (no divergence, no merges): columns
-      // outside the shrinking valid region compute values no valid column reads
-      // (the region loses one cell per step on each side, and a cell on the domain
-      // boundary reads itself in place of its missing neighbour).
-      {
+      // rows outside the shrinking valid region skip the step as whole warps
+      const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
+      if (upd) {
         float below = 0.f;  // z_m of the layer below (before its update)
 #pragma unroll
         for (int z = 0; z < LMAX; ++z) {
