@@ -77,9 +77,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=20, help="Chebyshev degree k (SpMVs per application)")
-    ap.add_argument("--guess", type=int, default=1,
+    ap.add_argument("--guess", type=int, default=2,
                     help="transient initial guess: 0 previous step (the paper's warm start), "
-                         "1 linear extrapolation from the two previous steps")
+                         "1 linear extrapolation from the two previous steps, 2 quadratic from three")
     ap.add_argument("--inner-tol", type=float, default=1e-5,
                     help="smallest residual reduction an FP32 inner solve is asked for")
     ap.add_argument("--fuse", type=int, default=0,
@@ -190,14 +190,15 @@ def workload_arrays():
     return inst, maps
 
 
-def config_dict(degree, polled=False, guess=1, fuse=0):
+def config_dict(degree, polled=False, guess=2, fuse=0):
     return {"workload": "transient backward Euler, 1024x1024x8 layers (8,388,608 DOF), 2 Si dies + TIM + Cu, "
                         "dt=1e-4 s, 100 steps from 45 C, 4 floorplans switched every 25 steps",
             "nx": NX, "ny": NY, "layers": 8, "dof": NX * NY * 8, "time_steps_per_bench_step": N_STEPS,
             "tol_rel": 1e-8, "precision": "FP32 PCG + FP64 iterative refinement",
             "preconditioner": f"Chebyshev degree {degree} on the Jacobi-scaled operator (Lanczos bounds), "
                               f"up to {fuse or 4} steps per launch (temporal blocking)",
-            "initial_guess": ("linear extrapolation 2 T_n - T_(n-1)" if guess else "previous step T_n"),
+            "initial_guess": {0: "previous step T_n", 1: "linear extrapolation 2 T_n - T_(n-1)",
+                              2: "quadratic extrapolation 3 T_n - 3 T_(n-1) + T_(n-2)"}[guess],
             "loop": ("host-polled launch chunks (profiling mode)" if polled else
                      "CUDA graph, conditional WHILE nodes (no host sync inside the 100 steps)"),
             "l2": "inputs larger than L2 (about 1 GB resident vs 129 MB L2); no flush"}

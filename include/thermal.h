@@ -97,7 +97,9 @@ typedef struct thermal_solve_opts {
   int batched_mode;    /* thermal_solve_batched: 0 one persistent launch when possible, 1 one */
                        /* instance after another through the single-grid solver (0)          */
   int guess;           /* transient initial guess: 0 the previous step T_n (the paper's warm  */
-                       /* start), 1 linear extrapolation 2 T_n - T_{n-1} inside a step loop (0) */
+                       /* start); inside a step loop 1 linear extrapolation 2 T_n - T_{n-1},  */
+                       /* 2 quadratic 3 T_n - 3 T_{n-1} + T_{n-2} (mixed path with nx % 4 == 0; */
+                       /* linear elsewhere); lower orders while the history is short (0)     */
   int cheb_fuse;       /* Chebyshev steps per launch on layer-uniform grids (temporal blocking */
                        /* in shared memory): 0 auto (4), 1 one step per launch, 2..4 (0)      */
   int ad_check;        /* ADAPTIVE: PCG iterations between true-residual evaluations of the   */

@@ -114,6 +114,7 @@ struct thermal_grid {
   float *th_hi = nullptr, *th_lo = nullptr, *thn_hi = nullptr, *thn_lo = nullptr;
   // theta_{n-1} for the extrapolated transient guess (allocated on first use)
   float *thm_hi = nullptr, *thm_lo = nullptr;
+  float *thm2_hi = nullptr, *thm2_lo = nullptr;  // theta_{n-2} (quadratic extrapolation)
   double* thm64 = nullptr;
   double* partials = nullptr;   // reduction partials
   int partials_stride = 0;

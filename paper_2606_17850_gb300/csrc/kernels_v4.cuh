@@ -389,3 +389,39 @@ static __global__ void __launch_bounds__(256)
   st4(th_hi + i, make_float4(gh[0], gh[1], gh[2], gh[3]));
   st4(th_lo + i, make_float4(gl[0], gl[1], gl[2], gl[3]));
 }
+
+// Start of a step with the quadratic extrapolated guess: theta <- 3 theta_n -
+// 3 theta_{n-1} + theta_{n-2} (2 theta_n - theta_{n-1} on the second step, theta_n on
+// the first), history shifted; theta holds the previous step's solution on entry.
+static __global__ void __launch_bounds__(256)
+    k_step_extrap2_df_v4(long long n4, const Ctl* ctl, float* th_hi, float* th_lo, float* thn_hi, float* thn_lo,
+                         float* thm_hi, float* thm_lo, float* thm2_hi, float* thm2_lo) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n4) return;
+  const int step = ld_int(&ctl->step);
+  const long long i = 4 * q;
+  const float4 ch = ld4(th_hi + i), cl = ld4(th_lo + i), ph = ld4(thm_hi + i), pl = ld4(thm_lo + i);
+  const float4 qh = ld4(thm2_hi + i), ql = ld4(thm2_lo + i);
+  float gh[4], gl[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const df cur = df_make(cmp(ch, k), cmp(cl, k));
+    const df prev = df_make(cmp(ph, k), cmp(pl, k));
+    df g = cur;
+    if (step == 1) g = df_sub(df_add(cur, cur), prev);
+    if (step >= 2) {
+      const df prev2 = df_make(cmp(qh, k), cmp(ql, k));
+      g = df_add(df_mul_f(df_sub(cur, prev), 3.0f), prev2);
+    }
+    gh[k] = g.hi;
+    gl[k] = g.lo;
+  }
+  st4(thn_hi + i, ch);
+  st4(thn_lo + i, cl);
+  st4(thm2_hi + i, ph);
+  st4(thm2_lo + i, pl);
+  st4(thm_hi + i, ch);
+  st4(thm_lo + i, cl);
+  st4(th_hi + i, make_float4(gh[0], gh[1], gh[2], gh[3]));
+  st4(th_lo + i, make_float4(gl[0], gl[1], gl[2], gl[3]));
+}

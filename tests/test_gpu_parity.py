@@ -352,7 +352,7 @@ def test_transient_step(prec, nx):
     assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
 
 
-@pytest.mark.parametrize("guess", [0, 1])
+@pytest.mark.parametrize("guess", [0, 1, 2])
 @pytest.mark.parametrize("graph", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_run_transient_schedule(graph, prec, guess):
