@@ -19,6 +19,7 @@
 // symmetric, as PCG requires.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -106,17 +107,48 @@ struct MGDev {  // one level, by value into kernels
   const float *gx, *gy, *gz, *s, *m, *w;
 };
 
+// Finest level of a grid with one conductivity per layer: the coefficients and the
+// Thomas factors depend only on the layer and on which in-plane neighbours exist
+// (case nxf + 3 nyf, nxf/nyf = number of x/y neighbours), so they come from this
+// table (kernel parameters) instead of per-cell arrays.
+template <int LMAX>
+struct MGUni {
+  float s[LMAX], gx[LMAX], gy[LMAX], gz[LMAX];  // gz: face to the layer above (0 on top)
+  float m[9][LMAX], w[9][LMAX];
+};
+
+// coefficient access of one cell (layer z, in-plane case c) for either source
+template <int LMAX, bool UNI>
+struct MGC {
+  const MGDev& v;
+  const MGUni<LMAX>& U;
+  __device__ __forceinline__ float s(long long i, int z) const { return UNI ? U.s[z] : v.s[i]; }
+  __device__ __forceinline__ float gxr(long long i, int z) const { return UNI ? U.gx[z] : v.gx[i]; }
+  __device__ __forceinline__ float gxl(long long i, int z) const { return UNI ? U.gx[z] : v.gx[i - 1]; }
+  __device__ __forceinline__ float gyu(long long i, int z) const { return UNI ? U.gy[z] : v.gy[i]; }
+  __device__ __forceinline__ float gyd(long long i, int z) const { return UNI ? U.gy[z] : v.gy[i - v.nx]; }
+  __device__ __forceinline__ float gza(long long i, int z) const { return UNI ? U.gz[z] : v.gz[i]; }
+  __device__ __forceinline__ float gzb(long long i, int z, long long pxy) const {
+    return UNI ? U.gz[z > 0 ? z - 1 : 0] : v.gz[i - pxy];
+  }
+  __device__ __forceinline__ float m(long long i, int z, int c) const { return UNI ? U.m[c][z] : v.m[i]; }
+  __device__ __forceinline__ float w(long long i, int z, int c) const { return UNI ? U.w[c][z] : v.w[i]; }
+};
+
 // x_out = x + omega T^-1 (b - A x) per column, x = x_in (+ P x_c: the prolongated
 // coarse correction, read on the fly) or 0 (x_in == nullptr).  One thread per
 // column; the column (LMAX >= L layers) stays in registers.
-template <int LMAX>
-__global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, const float* __restrict__ b,
-                                                   const float* __restrict__ xin, const float* __restrict__ xc,
-                                                   int nxc, int nyc, float* __restrict__ xout, float omega) {
+template <int LMAX, bool UNI>
+__global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, const __grid_constant__ MGUni<LMAX> U,
+                                                   const float* __restrict__ b, const float* __restrict__ xin,
+                                                   const float* __restrict__ xc, int nxc, int nyc,
+                                                   float* __restrict__ xout, float omega) {
   if (ld_int(&ctl->done)) return;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= v.nx || y >= v.ny) return;
+  const MGC<LMAX, UNI> C{v, U};
+  const int cs = (x + 1 < v.nx) + (x > 0) + 3 * ((y + 1 < v.ny) + (y > 0));
   const int L = v.L;
   const long long pxy = (long long)v.nx * v.ny;
   const long long pxyc = (long long)nxc * nyc;
@@ -139,17 +171,17 @@ __global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, cons
     float res = b[i];
     if (xin) {
       const float xi = xv[z];
-      float a = v.s[i] * xi;
-      if (x + 1 < v.nx) a += v.gx[i] * (xi - val(x + 1, y, z));
-      if (x > 0) a += v.gx[i - 1] * (xi - val(x - 1, y, z));
-      if (y + 1 < v.ny) a += v.gy[i] * (xi - val(x, y + 1, z));
-      if (y > 0) a += v.gy[i - v.nx] * (xi - val(x, y - 1, z));
-      if (z + 1 < L) a += v.gz[i] * (xi - xv[z + 1 < LMAX ? z + 1 : z]);
-      if (z > 0) a += v.gz[i - pxy] * (xi - xv[z > 0 ? z - 1 : 0]);
+      float a = C.s(i, z) * xi;
+      if (x + 1 < v.nx) a += C.gxr(i, z) * (xi - val(x + 1, y, z));
+      if (x > 0) a += C.gxl(i, z) * (xi - val(x - 1, y, z));
+      if (y + 1 < v.ny) a += C.gyu(i, z) * (xi - val(x, y + 1, z));
+      if (y > 0) a += C.gyd(i, z) * (xi - val(x, y - 1, z));
+      if (z + 1 < L) a += C.gza(i, z) * (xi - xv[z + 1 < LMAX ? z + 1 : z]);
+      if (z > 0) a += C.gzb(i, z, pxy) * (xi - xv[z > 0 ? z - 1 : 0]);
       res -= a;
     }
-    const float gb = (z > 0) ? v.gz[i - pxy] : 0.f;
-    dprev = (res + gb * dprev) * v.m[i];
+    const float gb = (z > 0) ? C.gzb(i, z, pxy) : 0.f;
+    dprev = (res + gb * dprev) * C.m(i, z, cs);
     dp[z] = dprev;
   }
   // back substitution and the damped update
@@ -159,7 +191,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, cons
     if (zz >= L) continue;
     const int z = zz;
     const long long i = idx3(v.nx, v.ny, x, y, z);
-    const float dz = dp[z] + v.w[i] * dn;
+    const float dz = dp[z] + C.w(i, z, cs) * dn;
     dn = dz;
     xout[i] = xv[z] + omega * dz;
   }
@@ -169,27 +201,31 @@ __global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, cons
 // layer; the x pair of an aggregate (adjacent lanes) is summed with a shuffle, the
 // y pair (adjacent block rows) through shared memory.  Block (32, 8): every
 // aggregate lies inside one block.
-__global__ void __launch_bounds__(256) k_mg_restrict(const Ctl* ctl, MGDev v, const float* __restrict__ b,
-                                                     const float* __restrict__ x, int nxc, int nyc,
-                                                     float* __restrict__ bc) {
+template <int LMAX, bool UNI>
+__global__ void __launch_bounds__(256) k_mg_restrict(const Ctl* ctl, MGDev v, const __grid_constant__ MGUni<LMAX> U,
+                                                     const float* __restrict__ b, const float* __restrict__ x,
+                                                     int nxc, int nyc, float* __restrict__ bc) {
   if (ld_int(&ctl->done)) return;
+  const MGC<LMAX, UNI> C{v, U};
   __shared__ float rowsum[8][32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int xx = blockIdx.x * 32 + tx, yy = blockIdx.y * 8 + ty;
   const bool in = xx < v.nx && yy < v.ny;
   const long long pxy = (long long)v.nx * v.ny;
-  for (int z = 0; z < v.L; ++z) {
+#pragma unroll
+  for (int z = 0; z < LMAX; ++z) {
+    if (z >= v.L) break;
     float r = 0.f;
     if (in) {
       const long long i = idx3(v.nx, v.ny, xx, yy, z);
       const float xi = x[i];
-      float a = v.s[i] * xi;
-      if (xx + 1 < v.nx) a += v.gx[i] * (xi - x[i + 1]);
-      if (xx > 0) a += v.gx[i - 1] * (xi - x[i - 1]);
-      if (yy + 1 < v.ny) a += v.gy[i] * (xi - x[i + v.nx]);
-      if (yy > 0) a += v.gy[i - v.nx] * (xi - x[i - v.nx]);
-      if (z + 1 < v.L) a += v.gz[i] * (xi - x[i + pxy]);
-      if (z > 0) a += v.gz[i - pxy] * (xi - x[i - pxy]);
+      float a = C.s(i, z) * xi;
+      if (xx + 1 < v.nx) a += C.gxr(i, z) * (xi - x[i + 1]);
+      if (xx > 0) a += C.gxl(i, z) * (xi - x[i - 1]);
+      if (yy + 1 < v.ny) a += C.gyu(i, z) * (xi - x[i + v.nx]);
+      if (yy > 0) a += C.gyd(i, z) * (xi - x[i - v.nx]);
+      if (z + 1 < v.L) a += C.gza(i, z) * (xi - x[i + pxy]);
+      if (z > 0) a += C.gzb(i, z, pxy) * (xi - x[i - pxy]);
       r = b[i] - a;
     }
     r += __shfl_xor_sync(0xffffffffu, r, 1);  // x pair (2X, 2X+1); 0 from a column outside the grid
@@ -245,6 +281,8 @@ struct MGLevelH {
 struct MGHier {
   double dt = -1.0;
   std::vector<MGLevelH> lv;
+  bool uni = false;   // finest level from the layer table
+  MGUni<32> tab{};    // its coefficients and Thomas factors (first L layers used)
   float* cinv = nullptr;  // dense inverse of the coarsest operator
   int nc = 0;
   ~MGHier() {
@@ -358,6 +396,36 @@ th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s) {
     k_mg_zfactors<<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(l.nx, l.ny, L, l.gx, l.gy, l.gz, l.s, l.m, l.w);
     TH_CHECK_LAUNCH();
   }
+  // finest level of a layer-uniform grid: coefficients and Thomas factors per case
+  h->uni = g->uniform;
+  if (h->uni) {
+    const LayerTab& T = g->tab_host;
+    std::memset(&h->tab, 0, sizeof(h->tab));
+    for (int z = 0; z < L; ++z) {
+      h->tab.s[z] = T.s32[z];
+      h->tab.gx[z] = T.gxl[z];
+      h->tab.gy[z] = T.gyl[z];
+      h->tab.gz[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
+    }
+    for (int nyf = 0; nyf < 3; ++nyf)
+      for (int nxf = 0; nxf < 3; ++nxf) {
+        const int c = nxf + 3 * nyf;
+        double wprev = 0.0;
+        for (int z = 0; z < L; ++z) {  // the order of k_mg_zfactors: s, x faces, y faces, z faces
+          double b = h->tab.s[z];
+          for (int q = 0; q < nxf; ++q) b += h->tab.gx[z];
+          for (int q = 0; q < nyf; ++q) b += h->tab.gy[z];
+          if (z + 1 < L) b += h->tab.gz[z];
+          const double gb = (z > 0) ? (double)h->tab.gz[z - 1] : 0.0;
+          if (z > 0) b += gb;
+          const double mz = 1.0 / (b - gb * wprev);
+          const double wz = (z + 1 < L) ? (double)h->tab.gz[z] * mz : 0.0;
+          h->tab.m[c][z] = (float)mz;
+          h->tab.w[c][z] = (float)wz;
+          wprev = wz;
+        }
+      }
+  }
   // dense inverse of the coarsest operator (at most 4 x 4 columns x L layers)
   const MGLevelH& c = h->lv.back();
   const int nc = (int)c.n;
@@ -399,19 +467,65 @@ th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s) {
 }
 
 template <int LMAX>
-static th_status smooth(thermal_grid* g, const MGLevelH& l, const float* b, const float* xin, const float* xc,
-                        int nxc, int nyc, float* xout, cudaStream_t s) {
-  k_mg_smooth<LMAX><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), b, xin, xc, nxc, nyc, xout,
-                                                                  MG_OMEGA);
+static MGUni<LMAX> uni_of(const MGHier* h) {
+  MGUni<LMAX> u;
+  std::memset(&u, 0, sizeof(u));
+  for (int z = 0; z < LMAX; ++z) {
+    u.s[z] = h->tab.s[z];
+    u.gx[z] = h->tab.gx[z];
+    u.gy[z] = h->tab.gy[z];
+    u.gz[z] = h->tab.gz[z];
+    for (int c = 0; c < 9; ++c) {
+      u.m[c][z] = h->tab.m[c][z];
+      u.w[c][z] = h->tab.w[c][z];
+    }
+  }
+  return u;
+}
+
+template <int LMAX>
+static th_status smooth(thermal_grid* g, int k, const float* b, const float* xin, const float* xc, int nxc, int nyc,
+                        float* xout, cudaStream_t s) {
+  const MGHier* h = g->mg;
+  const MGLevelH& l = h->lv[k];
+  const MGUni<LMAX> U = uni_of<LMAX>(h);
+  if (k == 0 && h->uni)
+    k_mg_smooth<LMAX, true><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, xin, xc, nxc,
+                                                                        nyc, xout, MG_OMEGA);
+  else
+    k_mg_smooth<LMAX, false><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, xin, xc,
+                                                                         nxc, nyc, xout, MG_OMEGA);
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
 
-static th_status smooth_any(thermal_grid* g, const MGLevelH& l, const float* b, const float* xin, const float* xc,
-                            int nxc, int nyc, float* xout, cudaStream_t s) {
-  if (g->L <= 8) return smooth<8>(g, l, b, xin, xc, nxc, nyc, xout, s);
-  if (g->L <= 16) return smooth<16>(g, l, b, xin, xc, nxc, nyc, xout, s);
-  return smooth<32>(g, l, b, xin, xc, nxc, nyc, xout, s);
+template <int LMAX>
+static th_status restrict_(thermal_grid* g, int k, const float* b, const float* x, float* bc, cudaStream_t s) {
+  const MGHier* h = g->mg;
+  const MGLevelH& l = h->lv[k];
+  const MGLevelH& c = h->lv[k + 1];
+  const MGUni<LMAX> U = uni_of<LMAX>(h);
+  if (k == 0 && h->uni)
+    k_mg_restrict<LMAX, true><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, x, c.nx,
+                                                                          c.ny, bc);
+  else
+    k_mg_restrict<LMAX, false><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, x, c.nx,
+                                                                           c.ny, bc);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+static th_status smooth_any(thermal_grid* g, int k, const float* b, const float* xin, const float* xc, int nxc,
+                            int nyc, float* xout, cudaStream_t s) {
+  if (g->L <= 8) return smooth<8>(g, k, b, xin, xc, nxc, nyc, xout, s);
+  if (g->L <= 16) return smooth<16>(g, k, b, xin, xc, nxc, nyc, xout, s);
+  return smooth<32>(g, k, b, xin, xc, nxc, nyc, xout, s);
+}
+
+static th_status restrict_any(thermal_grid* g, int k, const float* b, const float* x, float* bc, cudaStream_t s) {
+  if (g->L <= 8) return restrict_<8>(g, k, b, x, bc, s);
+  if (g->L <= 16) return restrict_<16>(g, k, b, x, bc, s);
+  return restrict_<32>(g, k, b, x, bc, s);
 }
 
 // z = M^-1 r: one V-cycle (see the file comment).  Every level's pre-smoothed
@@ -436,10 +550,8 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
   for (int k = 0; k + 1 < nl; ++k) {  // down: pre-smooth from zero, restrict the residual
     const MGLevelH& l = h->lv[k];
     const MGLevelH& c = h->lv[k + 1];
-    TH_TRY(smooth_any(g, l, B[k], nullptr, nullptr, 1, 1, X[k], s));
-    k_mg_restrict<<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), B[k], X[k], c.nx, c.ny,
-                                                                h->lv[k + 1].b);
-    TH_CHECK_LAUNCH();
+    TH_TRY(smooth_any(g, k, B[k], nullptr, nullptr, 1, 1, X[k], s));
+    TH_TRY(restrict_any(g, k, B[k], X[k], h->lv[k + 1].b, s));
   }
   k_mg_coarsest<<<1, 256, 0, s>>>(g->ctl, h->nc, h->cinv, B[nl - 1], X[nl - 1]);
   TH_CHECK_LAUNCH();
@@ -447,7 +559,7 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
     const MGLevelH& l = h->lv[k];
     const MGLevelH& c = h->lv[k + 1];
     float* out = (k == 0) ? z : h->lv[k].xt;
-    TH_TRY(smooth_any(g, l, B[k], X[k], X[k + 1], c.nx, c.ny, out, s));
+    TH_TRY(smooth_any(g, k, B[k], X[k], X[k + 1], c.nx, c.ny, out, s));
     X[k] = out;
   }
   return TH_OK;
