@@ -44,7 +44,6 @@ struct TBParams {
   float gx[LMAX], gy[LMAX];     // in-plane face conductances per layer
   float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
-  float inv_theta;              // 1 / theta: z_1 = D^-1 r / theta for a chain's first chunk
 };
 
 __device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -124,9 +123,7 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
   const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
-  // has_prev: 0 z_m staged, no z_{m-1}; 1 both staged; 2 first chunk of a chain, z_1
-  // formed from r (only r staged)
-  const unsigned tx_bytes = box_bytes * (has_prev == 2 ? 1u : (has_prev ? 3u : 2u));
+  const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
 
   if (tid == 0) {
     tb_mbar_init(bar, 1);
@@ -138,8 +135,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   auto issue = [&](int t) {
     const int xa = ((t % ntx) * TX - H) & ~3, y0 = (t / ntx) * TY - H;
     tb_mbar_expect(bar, tx_bytes);
-    if (has_prev != 2) tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
-    if (has_prev == 1) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+    tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
+    if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
     tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
   };
   if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
@@ -167,15 +164,10 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
       const bool on = z < L;
+      cur[z] = on ? stage[z * SL + st] : 0.f;
+      prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
       rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
       inv[z] = P.invd[nxf + 3 * nyf][z];
-      if (has_prev == 2) {
-        cur[z] = (SCALED ? rr[z] * inv[z] : rr[z]) * P.inv_theta;  // z_1
-        prv[z] = 0.f;                                               // z_0
-      } else {
-        cur[z] = on ? stage[z * SL + st] : 0.f;
-        prv[z] = (on && has_prev == 1) ? stage[(LMAX + z) * SL + st] : 0.f;
-      }
     }
     __syncthreads();  // staging buffer consumed by every thread
     const int tn = t + gridDim.x;

@@ -354,8 +354,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
       P.tb_lmax = g->L <= 8 ? 8 : (g->L <= 12 ? 12 : 0);
       if (P.tb_lmax > 0) {
         P.fused = true;
-        // the first chunk forms z_1 = D^-1 r / theta itself (pool index -2: from r)
-        int cur = -2, prev = -1, m = 1, left = P.k - 1;
+        int cur = 0, prev = -1, m = 1, left = P.k - 1;
         while (left > 0) {
           const int st = std::min(fuse, left);
           int oc = -1, op = -1;
@@ -438,10 +437,7 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
       switch (P.pc) {
         case TH_PC_NONE: TH_UPD4(0); break;
         case TH_PC_JACOBI: TH_UPD4(1); break;
-        case TH_PC_CHEB:
-          if (P.fused) TH_UPD4(3);  // the first fused chunk forms z_1 from r
-          else TH_UPD4(2);
-          break;
+        case TH_PC_CHEB: TH_UPD4(2); break;
         default: TH_UPD4(3); break;
       }
 #undef TH_UPD4
@@ -544,17 +540,10 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
         prm.invd[nxf + 3 * nyf][z] = 1.0f / dg;
       }
   }
-  prm.inv_theta = (float)P.inv_theta;
   CUtensorMap mc, mp, mr;
+  TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], EY));
+  TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], EY));
   TH_TRY(tb_map(&mr, P.d, V.r, EY));
-  const int mode = (c.in_cur == -2) ? 2 : (c.in_prev >= 0 ? 1 : 0);
-  if (mode == 2) {
-    mc = mr;
-    mp = mr;
-  } else {
-    TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], EY));
-    TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], EY));
-  }
   const int ntx = (P.d.nx + TX - 1) / TX;
   const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
   const size_t smem = tb_smem_bytes<LM, EY>();
@@ -563,7 +552,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   const int nblk = std::min(ntiles, sm_count());
   if (nblk > g->partials_stride) return th_fail(TH_ESTATE, "partials buffer smaller than the temporal-blocking grid");
   k_cheb_tb<LM, EY, ST, SC, LA><<<nblk, dim3(TB_EX, EY), smem, st>>>(
-      P.d, ntx, ntiles, mode, g->ctl, mc, mp, mr, pool[c.out_cur],
+      P.d, ntx, ntiles, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, pool[c.out_cur],
       c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
