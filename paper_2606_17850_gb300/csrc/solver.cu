@@ -1070,7 +1070,6 @@ static th_status build_graph(const Plan& P, int kind, const CtlInit& ci, GraphEn
   }
   GraphCache* gc = g->graphs;
   Ctl* ctl = g->ctl;
-  const long long n = P.d.n;
   cudaGraph_t G = nullptr;
   TH_CUDA(cudaGraphCreate(&G, 0));
   th_status st = capture_body(G, gc->cs[0], [&](cudaStream_t s0) -> th_status {
@@ -1317,7 +1316,6 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
     }
     TH_CUDA(cudaGraphLaunch(it->second.exec, s));
   } else {
-    const long long n = P.d.n;
     k_ctl_reset<<<1, 1, 0, s>>>(g->ctl, ci);
     TH_CHECK_LAUNCH();
     const int prep = (kind == KIND_STEP) ? 2 : 1;
