@@ -239,6 +239,171 @@ __global__ void __launch_bounds__(256) k_mg_restrict(const Ctl* ctl, MGDev v, co
   }
 }
 
+// ---------------------------------------------------------------- finest level, vectorised
+// Layer-uniform grids with nx % 4 == 0 and at most 8 layers: a thread owns 4
+// consecutive columns (x0 .. x0+3, x0 % 4 == 0) and moves them with 16-byte loads;
+// the two aggregates they belong to (x0/2, x0/2+1) are one 8-byte load of the
+// coarse correction.  Same arithmetic as k_mg_smooth / k_mg_restrict.
+
+__device__ __forceinline__ float4 mg_ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float2 mg_ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float mg_c4(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// the 4 columns' iterate (x_in + P x_c) at row yy, layer z, and the scalar neighbours
+struct MGRow4 {
+  const float* xin;
+  const float* xc;
+  int nx, nxc;
+  long long pxy, pxyc;
+  __device__ __forceinline__ float4 row(int x0, int yy, int z) const {
+    if (!xin) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 t = mg_ld4(xin + (long long)x0 + (long long)nx * yy + pxy * z);
+    if (xc) {
+      const float2 c = mg_ld2(xc + (x0 >> 1) + (long long)nxc * (yy >> 1) + pxyc * z);
+      t.x += c.x; t.y += c.x; t.z += c.y; t.w += c.y;
+    }
+    return t;
+  }
+  __device__ __forceinline__ float one(int xx, int yy, int z) const {
+    if (!xin) return 0.f;
+    float t = xin[(long long)xx + (long long)nx * yy + pxy * z];
+    if (xc) t += xc[(xx >> 1) + (long long)nxc * (yy >> 1) + pxyc * z];
+    return t;
+  }
+};
+
+__global__ void __launch_bounds__(256, 2) k_mg_smooth4(const Ctl* ctl, int nx, int ny, int L,
+                                                       const __grid_constant__ MGUni<8> U,
+                                                       const float* __restrict__ b, const float* __restrict__ xin,
+                                                       const float* __restrict__ xc, int nxc, int nyc,
+                                                       float* __restrict__ xout, float omega) {
+  if (ld_int(&ctl->done)) return;
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x0 >= nx || y >= ny) return;
+  const long long pxy = (long long)nx * ny;
+  const MGRow4 X{xin, xc, nx, nxc, pxy, (long long)nxc * nyc};
+  const bool hasL = x0 > 0, hasR = x0 + 4 < nx, hasD = y > 0, hasU = y + 1 < ny;
+  const int nyf = (int)hasU + (int)hasD;
+  // boundary case of each of the 4 columns (only the outer two can miss an x neighbour)
+  const int cs0 = (1 + (int)hasL) + 3 * nyf, cs3 = (1 + (int)hasR) + 3 * nyf, csm = 2 + 3 * nyf;
+  float xv[4][8], dp[4][8];
+  float4 xb = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 xcur = X.row(x0, y, 0);
+  float dprev[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int z = 0; z < 8; ++z) {
+    if (z >= L) break;
+    const long long i = (long long)x0 + (long long)nx * y + pxy * z;
+    const float4 xa = (xin && z + 1 < L) ? X.row(x0, y, z + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 bv = mg_ld4(b + i);
+    float4 xu = xcur, xd = xcur;
+    float xl = xcur.x, xr = xcur.w;
+    if (xin) {
+      if (hasU) xu = X.row(x0, y + 1, z);
+      if (hasD) xd = X.row(x0, y - 1, z);
+      if (hasL) xl = X.one(x0 - 1, y, z);
+      if (hasR) xr = X.one(x0 + 4, y, z);
+    }
+    const float gx = U.gx[z], gy = U.gy[z], ga = U.gz[z], gbz = z > 0 ? U.gz[z > 0 ? z - 1 : 0] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float xi = mg_c4(xcur, k);
+      xv[k][z] = xi;
+      float res = mg_c4(bv, k);
+      if (xin) {
+        const float right = (k == 3) ? xr : mg_c4(xcur, k + 1);
+        const float left = (k == 0) ? xl : mg_c4(xcur, k - 1);
+        float a = U.s[z] * xi;
+        if (k < 3 || hasR) a += gx * (xi - right);
+        if (k > 0 || hasL) a += gx * (xi - left);
+        if (hasU) a += gy * (xi - mg_c4(xu, k));
+        if (hasD) a += gy * (xi - mg_c4(xd, k));
+        if (z + 1 < L) a += ga * (xi - mg_c4(xa, k));
+        if (z > 0) a += gbz * (xi - mg_c4(xb, k));
+        res -= a;
+      }
+      const int c = (k == 0) ? cs0 : ((k == 3) ? cs3 : csm);
+      dprev[k] = (res + gbz * dprev[k]) * U.m[c][z];
+      dp[k][z] = dprev[k];
+    }
+    xb = xcur;
+    xcur = xa;
+  }
+  float dn[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int zz = 7; zz >= 0; --zz) {
+    if (zz >= L) continue;
+    float o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = (k == 0) ? cs0 : ((k == 3) ? cs3 : csm);
+      const float d = dp[k][zz] + U.w[c][zz] * dn[k];
+      dn[k] = d;
+      o[k] = xv[k][zz] + omega * d;
+    }
+    *reinterpret_cast<float4*>(xout + (long long)x0 + (long long)nx * y + pxy * zz) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+}
+
+// b_c = P^T (b - A x) on the vectorised finest level: 4 fine columns give 2 aggregate
+// partial sums per layer; the y pair is summed through shared memory.  Block (32, 8).
+__global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, int ny, int L,
+                                                      const __grid_constant__ MGUni<8> U,
+                                                      const float* __restrict__ b, const float* __restrict__ x,
+                                                      int nxc, int nyc, float* __restrict__ bc) {
+  if (ld_int(&ctl->done)) return;
+  __shared__ float2 rowsum[8][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = 4 * (blockIdx.x * 32 + tx), y = blockIdx.y * 8 + ty;
+  const bool in = x0 < nx && y < ny;
+  const long long pxy = (long long)nx * ny;
+  const bool hasL = x0 > 0, hasR = x0 + 4 < nx, hasD = y > 0, hasU = y + 1 < ny;
+#pragma unroll
+  for (int z = 0; z < 8; ++z) {
+    if (z >= L) break;
+    float2 r2 = make_float2(0.f, 0.f);
+    if (in) {
+      const long long i = (long long)x0 + (long long)nx * y + pxy * z;
+      const float4 xc = mg_ld4(x + i), bv = mg_ld4(b + i);
+      const float4 xu = hasU ? mg_ld4(x + i + nx) : xc, xd = hasD ? mg_ld4(x + i - nx) : xc;
+      const float4 xa = (z + 1 < L) ? mg_ld4(x + i + pxy) : xc;
+      const float4 xbv = (z > 0) ? mg_ld4(x + i - pxy) : xc;
+      const float xl = hasL ? x[i - 1] : xc.x, xr = hasR ? x[i + 4] : xc.w;
+      const float gx = U.gx[z], gy = U.gy[z], ga = U.gz[z], gbz = z > 0 ? U.gz[z > 0 ? z - 1 : 0] : 0.f;
+      float r[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float xi = mg_c4(xc, k);
+        const float right = (k == 3) ? xr : mg_c4(xc, k + 1);
+        const float left = (k == 0) ? xl : mg_c4(xc, k - 1);
+        float a = U.s[z] * xi;
+        a += gx * (xi - right);  // a missing neighbour is the cell itself: difference 0
+        a += gx * (xi - left);
+        a += gy * (xi - mg_c4(xu, k));
+        a += gy * (xi - mg_c4(xd, k));
+        a += ga * (xi - mg_c4(xa, k));
+        a += gbz * (xi - mg_c4(xbv, k));
+        r[k] = mg_c4(bv, k) - a;
+      }
+      r2 = make_float2(r[0] + r[1], r[2] + r[3]);
+    }
+    rowsum[ty][tx] = r2;
+    __syncthreads();
+    if ((ty & 1) == 0) {
+      const int X0 = x0 >> 1, Y = y >> 1;
+      if (X0 < nxc && Y < nyc) {
+        const float2 a = rowsum[ty][tx], c = rowsum[ty + 1][tx];
+        *reinterpret_cast<float2*>(bc + X0 + (long long)nxc * Y + (long long)nxc * nyc * z) =
+            make_float2(a.x + c.x, a.y + c.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // coarsest level: x = C b with the dense inverse C (n x n, FP32), one CTA, a warp per row
 __global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, const float* __restrict__ C,
                                                      const float* __restrict__ b, float* __restrict__ x) {
@@ -483,12 +648,24 @@ static MGUni<LMAX> uni_of(const MGHier* h) {
   return u;
 }
 
+// the vectorised finest-level kernels apply (layer table, nx % 4 == 0, <= 8 layers)
+static bool mg_v4(const thermal_grid* g, int k) { return k == 0 && g->mg->uni && g->nx % 4 == 0 && g->L <= 8; }
+
 template <int LMAX>
 static th_status smooth(thermal_grid* g, int k, const float* b, const float* xin, const float* xc, int nxc, int nyc,
                         float* xout, cudaStream_t s) {
   const MGHier* h = g->mg;
   const MGLevelH& l = h->lv[k];
   const MGUni<LMAX> U = uni_of<LMAX>(h);
+  if constexpr (LMAX == 8) {
+    if (mg_v4(g, k)) {
+      k_mg_smooth4<<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U, b,
+                                                                                     xin, xc, nxc, nyc, xout,
+                                                                                     MG_OMEGA);
+      TH_CHECK_LAUNCH();
+      return TH_OK;
+    }
+  }
   if (k == 0 && h->uni)
     k_mg_smooth<LMAX, true><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, xin, xc, nxc,
                                                                         nyc, xout, MG_OMEGA);
@@ -505,6 +682,14 @@ static th_status restrict_(thermal_grid* g, int k, const float* b, const float* 
   const MGLevelH& l = h->lv[k];
   const MGLevelH& c = h->lv[k + 1];
   const MGUni<LMAX> U = uni_of<LMAX>(h);
+  if constexpr (LMAX == 8) {
+    if (mg_v4(g, k)) {
+      k_mg_restrict4<<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U,
+                                                                                       b, x, c.nx, c.ny, bc);
+      TH_CHECK_LAUNCH();
+      return TH_OK;
+    }
+  }
   if (k == 0 && h->uni)
     k_mg_restrict<LMAX, true><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, x, c.nx,
                                                                           c.ny, bc);
