@@ -11,7 +11,7 @@ bonds) at once.  One V-cycle is M^{-1} r:
   aggregates the 2 x 2 fine columns (2X, 2X+1) x (2Y, 2Y+1) of its layer (one or two
   on an odd edge); prolongation P is piecewise constant over the aggregate,
   restriction R = P^T, and the coarse operator is the Galerkin product P^T A P.
-  Levels are added while max(nx, ny) > 4.
+  Levels are added while max(nx, ny) > 8.
 * Smoother: damped z-line Jacobi, x <- x + omega T^{-1} (b - A x), T = the
   tridiagonal block of A over each (x, y) column (diagonal and vertical couplings),
   omega = 0.8, nu sweeps before and nu after the coarse correction.
@@ -31,7 +31,7 @@ import scipy.sparse as sp
 from . import krylov
 
 OMEGA = 0.8
-COARSEST = 4
+COARSEST = 8
 
 
 def coarse_dims(nx, ny):

@@ -9,11 +9,11 @@
 //   odd edge).  Piecewise-constant prolongation P, restriction P^T, Galerkin coarse
 //   operator P^T A P, which is again a 7-point operator: a coarse face sums the fine
 //   faces crossing the aggregate boundary, the coarse per-cell term sums the fine
-//   sink/capacity terms.  Levels are added while max(nx, ny) > 4.
+//   sink/capacity terms.  Levels are added while max(nx, ny) > 8.
 // * Smoother: damped z-line Jacobi, x <- x + omega T^-1 (b - A x), T the tridiagonal
 //   block of A over each (x, y) column (Thomas factors precomputed per level), one
 //   sweep before and one after the coarse correction; omega = 0.8.
-// * Coarsest level (at most 4 x 4 columns): exact solve with a dense inverse
+// * Coarsest level (at most 8 x 8 columns): exact solve with a dense inverse
 //   computed once on the host in FP64.
 // The cycle starts from zero on every level and pre/post sweeps match, so M^-1 is
 // symmetric, as PCG requires.
@@ -27,7 +27,7 @@
 namespace {
 
 constexpr float MG_OMEGA = 0.8f;
-constexpr int MG_COARSEST = 4;
+constexpr int MG_COARSEST = 8;
 
 __device__ __forceinline__ long long idx3(int nx, int ny, int x, int y, int z) {
   return (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
@@ -404,12 +404,22 @@ __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, in
   }
 }
 
-// coarsest level: x = C b with the dense inverse C (n x n, FP32), one CTA, a warp per row
+// x_l += P x_{l+1}: the piecewise-constant coarse correction, one thread per fine cell
+__global__ void __launch_bounds__(256) k_mg_prolong(const Ctl* ctl, int nx, int ny, int L, float* __restrict__ x,
+                                                    const float* __restrict__ xc, int nxc, int nyc) {
+  if (ld_int(&ctl->done)) return;
+  const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (xx >= nx || yy >= ny || z >= L) return;
+  x[idx3(nx, ny, xx, yy, z)] += xc[idx3(nxc, nyc, xx >> 1, yy >> 1, z)];
+}
+
+// coarsest level: x = C b with the dense inverse C (n x n, FP32), a warp per row
 __global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, const float* __restrict__ C,
                                                      const float* __restrict__ b, float* __restrict__ x) {
   if (ld_int(&ctl->done)) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int row = warp; row < n; row += nw) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int warp = blockIdx.x * nw + (threadIdx.x >> 5);
+  for (int row = warp; row < n; row += nw * gridDim.x) {
     float acc = 0.f;
     for (int j = lane; j < n; j += 32) acc += C[(long long)row * n + j] * b[j];
     acc = warp_sum(acc);
@@ -720,7 +730,7 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
   if (!h || !g->mg_valid) return th_fail(TH_ESTATE, "multigrid hierarchy not built");
   const int nl = (int)h->lv.size();
   if (nl == 1) {
-    k_mg_coarsest<<<1, 256, 0, s>>>(g->ctl, h->nc, h->cinv, r, z);
+    k_mg_coarsest<<<(h->nc + 7) / 8, 256, 0, s>>>(g->ctl, h->nc, h->cinv, r, z);
     TH_CHECK_LAUNCH();
     return TH_OK;
   }
@@ -738,13 +748,16 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
     TH_TRY(smooth_any(g, k, B[k], nullptr, nullptr, 1, 1, X[k], s));
     TH_TRY(restrict_any(g, k, B[k], X[k], h->lv[k + 1].b, s));
   }
-  k_mg_coarsest<<<1, 256, 0, s>>>(g->ctl, h->nc, h->cinv, B[nl - 1], X[nl - 1]);
+  k_mg_coarsest<<<(h->nc + 7) / 8, 256, 0, s>>>(g->ctl, h->nc, h->cinv, B[nl - 1], X[nl - 1]);
   TH_CHECK_LAUNCH();
-  for (int k = nl - 2; k >= 0; --k) {  // up: coarse correction (prolongated on the fly) + post-smooth
+  for (int k = nl - 2; k >= 0; --k) {  // up: coarse correction, then post-smooth
     const MGLevelH& l = h->lv[k];
     const MGLevelH& c = h->lv[k + 1];
+    k_mg_prolong<<<dim3((l.nx + 31) / 32, (l.ny + 7) / 8, g->L), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, X[k],
+                                                                                     X[k + 1], c.nx, c.ny);
+    TH_CHECK_LAUNCH();
     float* out = (k == 0) ? z : h->lv[k].xt;
-    TH_TRY(smooth_any(g, k, B[k], X[k], X[k + 1], c.nx, c.ny, out, s));
+    TH_TRY(smooth_any(g, k, B[k], X[k], nullptr, 1, 1, out, s));
     X[k] = out;
   }
   return TH_OK;
