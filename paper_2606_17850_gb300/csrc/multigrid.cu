@@ -404,15 +404,6 @@ __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, in
   }
 }
 
-// x_l += P x_{l+1}: the piecewise-constant coarse correction, one thread per fine cell
-__global__ void __launch_bounds__(256) k_mg_prolong(const Ctl* ctl, int nx, int ny, int L, float* __restrict__ x,
-                                                    const float* __restrict__ xc, int nxc, int nyc) {
-  if (ld_int(&ctl->done)) return;
-  const int xx = blockIdx.x * blockDim.x + threadIdx.x, yy = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-  if (xx >= nx || yy >= ny || z >= L) return;
-  x[idx3(nx, ny, xx, yy, z)] += xc[idx3(nxc, nyc, xx >> 1, yy >> 1, z)];
-}
-
 // coarsest level: x = C b with the dense inverse C (n x n, FP32), a warp per row
 __global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, const float* __restrict__ C,
                                                      const float* __restrict__ b, float* __restrict__ x) {
@@ -750,14 +741,10 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
   }
   k_mg_coarsest<<<(h->nc + 7) / 8, 256, 0, s>>>(g->ctl, h->nc, h->cinv, B[nl - 1], X[nl - 1]);
   TH_CHECK_LAUNCH();
-  for (int k = nl - 2; k >= 0; --k) {  // up: coarse correction, then post-smooth
-    const MGLevelH& l = h->lv[k];
+  for (int k = nl - 2; k >= 0; --k) {  // up: coarse correction (prolongated on the fly) + post-smooth
     const MGLevelH& c = h->lv[k + 1];
-    k_mg_prolong<<<dim3((l.nx + 31) / 32, (l.ny + 7) / 8, g->L), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, X[k],
-                                                                                     X[k + 1], c.nx, c.ny);
-    TH_CHECK_LAUNCH();
     float* out = (k == 0) ? z : h->lv[k].xt;
-    TH_TRY(smooth_any(g, k, B[k], X[k], nullptr, 1, 1, out, s));
+    TH_TRY(smooth_any(g, k, B[k], X[k], X[k + 1], c.nx, c.ny, out, s));
     X[k] = out;
   }
   return TH_OK;
