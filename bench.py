@@ -57,8 +57,8 @@ KERNEL_BYTES = {
     "cheb_bf16": 22,     # gx gy gz bf16 (6) + 16
     # plain FP64 path
     "residual_f64": 48,  # gx gy gz (24) + theta, theta_n (16) + P f32 (4) + r f32 (4)
-    "stencil_f64": 40,   # gx gy gz (24) + x (8) + y (8)
-    "cheb_f64": 64,      # gx gy gz (24) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)
+    "stencil_f64": 48,   # gx gy gz, diagonal (32) + x (8) + y (8)
+    "cheb_f64": 72,      # gx gy gz, diagonal (32) + z_m, z_{m-1}, r, 1/diag (32) + z_{m+1} (8)
     # the paper's adaptive mixed precision (Sec. 4.4)
     "ad_cheb_a3": 28,    # A3 in FP16 (8) + z_m, z_{m-1}, r, 1/diag (16) + z_{m+1} (4)
     "ad_spmv_early": 32, # D4, gx gy gz FP32 (16) + p (8) + mu (8)

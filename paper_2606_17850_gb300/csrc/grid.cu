@@ -270,6 +270,7 @@ thermal_grid::~thermal_grid() {
   dfree(tab); dfree(invd32); dfree(invd64); dfree(isqd32); dfree(zl_c); dfree(zl_m);
   dfree(qd4); dfree(qd5); dfree(qd6); dfree(qd7); dfree(diag32); dfree(diag64);
   if (mg) mg_free(mg);
+  dfree(dg64);
   for (auto& p : theta) dfree(p);
   dfree(theta_n); dfree(r64); dfree(mu64);
   for (auto& p : p64) dfree(p);
@@ -304,6 +305,7 @@ static th_status compute_faces(thermal_grid* g) {
   g->tab_valid = false;
   g->qd_valid = false;
   g->mg_valid = false;
+  g->dg64_valid = false;
   g->zl_valid = false;
   g->lanczos_cache.clear();
   if (g->graphs) {  // captured Chebyshev coefficients depend on the faces
@@ -396,6 +398,18 @@ th_status grid_ensure_qd(thermal_grid* g, double dt, cudaStream_t s) {
   TH_CHECK_LAUNCH();
   g->qd_dt = key;
   g->qd_valid = true;
+  return TH_OK;
+}
+
+th_status grid_ensure_dg64(thermal_grid* g, double dt, cudaStream_t s) {
+  TH_TRY(grid_ensure_tab(g, dt, s));
+  const double key = dt > 0.0 ? dt : 0.0;
+  if (g->dg64_valid && g->dg64_dt == key) return TH_OK;
+  if (!g->dg64) TH_TRY(dalloc(&g->dg64, g->n));
+  k_diag_out<<<grid_blocks(g), dim3(TH_BX, TH_BY), 0, s>>>(grid_dims(g), g->f64, g->tab, g->dg64);
+  TH_CHECK_LAUNCH();
+  g->dg64_dt = key;
+  g->dg64_valid = true;
   return TH_OK;
 }
 
@@ -574,6 +588,7 @@ extern "C" th_status thermal_grid_set_conductivity_map(thermal_grid* g, const do
   g->tab_valid = false;
   g->qd_valid = false;
   g->mg_valid = false;
+  g->dg64_valid = false;
   g->zl_valid = false;
   g->lanczos_cache.clear();
   if (g->graphs) {

@@ -99,6 +99,11 @@ struct thermal_grid {
   double qd_dt = -1.0;
   bool qd_valid = false;
 
+  // main diagonal in FP64 for the plain FP64 path's expanded-form kernels, per dt
+  double* dg64 = nullptr;
+  double dg64_dt = -1.0;
+  bool dg64_valid = false;
+
   // geometric multigrid hierarchy (multigrid.cu), per dt
   struct MGHier* mg = nullptr;
   bool mg_valid = false;
@@ -140,6 +145,7 @@ th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s);
 th_status grid_ensure_workspace(thermal_grid* g, bool need64, cudaStream_t s);
 th_status grid_ensure_zline(thermal_grid* g, double dt, cudaStream_t s);
 th_status grid_ensure_qd(thermal_grid* g, double dt, cudaStream_t s);
+th_status grid_ensure_dg64(thermal_grid* g, double dt, cudaStream_t s);
 // multigrid.cu
 struct MGHier;
 void mg_free(MGHier* h);

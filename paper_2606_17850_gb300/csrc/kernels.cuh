@@ -378,6 +378,83 @@ __global__ void k_cheb(Dims d, Ctl* ctl, const TC* __restrict__ gx, const TC* __
   ctl_set_beta(ctl);
 }
 
+// ---------------------------------------------------------------- plain FP64 path, expanded form
+// y_i = D_i v_i - sum_j g_ij v_j with the stored main diagonal D (FP64): one DMUL and
+// up to six DFMA per cell, against 13 FP64 operations for the difference form.
+// GB300 retires FP64 at about 1/64 of its FP32 rate, so the FP64 pipe, not HBM,
+// bounds these kernels and the operation count decides their time.
+template <typename F>
+__device__ __forceinline__ double row64x(const Faces64& f, const double* __restrict__ dg, const Dims& d,
+                                         const Cell& c, double vi, F val) {
+  double a = dg[c.i] * vi;
+  if (c.x + 1 < d.nx) a -= f.gx[c.i] * val(c.i + 1);
+  if (c.x > 0) a -= f.gx[c.i - 1] * val(c.i - 1);
+  if (c.y + 1 < d.ny) a -= f.gy[c.i] * val(c.i + d.nx);
+  if (c.y > 0) a -= f.gy[c.i - d.nx] * val(c.i - d.nx);
+  if (c.z + 1 < d.L) a -= f.gz[c.i] * val(c.i + d.pxy);
+  if (c.z > 0) a -= f.gz[c.i - d.pxy] * val(c.i - d.pxy);
+  return a;
+}
+
+template <int DUMMY = 0>
+__global__ void k_apply64x(Dims d, Faces64 f, const double* __restrict__ dg, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  const Cell c = cell_of(d);
+  if (!c.valid) return;
+  y[c.i] = row64x(f, dg, d, c, x[c.i], [&](long long j) { return x[j]; });
+}
+
+// Chebyshev step (see k_cheb), FP64, expanded form
+template <bool SCALED, bool LAST>
+__global__ void k_cheb64x(Dims d, Ctl* ctl, Faces64 f, const double* __restrict__ dg, const double* __restrict__ r,
+                          const double* __restrict__ zprev, const double* __restrict__ zcur,
+                          double* __restrict__ znext, const double* __restrict__ invd, double c1, double c2,
+                          double* partials, int stride, unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const Cell c = cell_of(d);
+  double v[1] = {0.0};
+  if (c.valid) {
+    const double zi = zcur[c.i];
+    const double az = row64x(f, dg, d, c, zi, [&](long long j) { return zcur[j]; });
+    const double ri = r[c.i];
+    double res = ri - az;
+    if (SCALED) res *= invd[c.i];
+    const double zp = zprev ? zprev[c.i] : 0.0;
+    const double zn = zi + c1 * (zi - zp) + c2 * res;
+    znext[c.i] = zn;
+    if (LAST) v[0] = ri * zn;
+  }
+  if (!LAST) return;
+  double tot[1];
+  if (!grid_reduce<double, 1>(v, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
+}
+
+// search direction + product + p^T A p (see k_spmv_dot), FP64, expanded form
+template <int DUMMY = 0>
+__global__ void k_spmv_dot64x(Dims d, Ctl* ctl, Faces64 f, const double* __restrict__ dg,
+                              const double* __restrict__ z, const double* __restrict__ p_old,
+                              double* __restrict__ p_new, double* __restrict__ mu, double* partials, int stride,
+                              unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  const Cell c = cell_of(d);
+  const int first = ld_int(&ctl->first);
+  const double beta = first ? 0.0 : ctl_beta<double>(ctl);
+  double v[1] = {0.0};
+  if (c.valid) {
+    auto pv = [&](long long j) -> double { return first ? z[j] : z[j] + beta * p_old[j]; };
+    const double pi = pv(c.i);
+    const double ai = row64x(f, dg, d, c, pi, pv);
+    p_new[c.i] = pi;
+    mu[c.i] = ai;
+    v[0] = pi * ai;
+  }
+  double tot[1];
+  if (!grid_reduce<double, 1>(v, partials, stride, counter, tot)) return;
+  fin_pap(ctl, tot[0]);
+}
+
 // z-line block Jacobi: per (x, y) column, solve the tridiagonal system with
 // diagonal A_ii and off-diagonals -gz (Thomas algorithm, factors from setup).
 // Reduces r^T z.  Launch: block (TH_BX, TH_BY), grid (ceil(nx/TH_BX), ceil(ny/TH_BY), 1).

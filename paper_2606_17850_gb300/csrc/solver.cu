@@ -80,14 +80,6 @@ __global__ void k_apply_f32(Dims d, const float* __restrict__ gx, const float* _
   float dg;
   y[c.i] = stencil_row<float>(gx, gy, gz, d, c, lay_s<float>(tab, c.z), x[c.i], [&](long long j) { return x[j]; }, dg);
 }
-__global__ void k_apply_f64(Dims d, const double* __restrict__ gx, const double* __restrict__ gy,
-                            const double* __restrict__ gz, const LayerTab* tab, const double* __restrict__ x,
-                            double* __restrict__ y) {
-  const Cell c = cell_of(d);
-  if (!c.valid) return;
-  double dg;
-  y[c.i] = stencil_row<double>(gx, gy, gz, d, c, lay_s<double>(tab, c.z), x[c.i], [&](long long j) { return x[j]; }, dg);
-}
 
 // ------------------------------------------------------------------ host tridiagonal eigenvalues
 
@@ -331,6 +323,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
   }
   if (P.pc == TH_PC_ZLINE) TH_TRY(grid_ensure_zline(g, dt, s));
   if (P.pc == TH_PC_MG) TH_TRY(grid_ensure_mg(g, dt, s));
+  if (P.prec == TH_PREC_FP64) TH_TRY(grid_ensure_dg64(g, dt, s));
   P.v4 = (g->nx % 4 == 0);
   P.uni = g->uniform;
   if (P.v4) {
@@ -616,6 +609,19 @@ static th_status enq_cheb_tail(const Plan& P, const VecSet<TV>& V, const TC* gx,
         continue;
       }
     }
+    if constexpr (sizeof(TV) == 8) {  // plain FP64 path: expanded form with the stored diagonal
+#define TH_CHEB64(SC, LA)                                                                                    \
+  k_cheb64x<SC, LA><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64, g->dg64, V.r, zprev, zcur, znext, V.invd, c1, c2, \
+                                           g->partials, g->partials_stride, g->counters)
+      if (P.scaled) {
+        if (last) TH_CHEB64(true, true); else TH_CHEB64(true, false);
+      } else {
+        if (last) TH_CHEB64(false, true); else TH_CHEB64(false, false);
+      }
+#undef TH_CHEB64
+      TH_CHECK_LAUNCH();
+      continue;
+    }
 #define TH_CHEB(SC, LA)                                                                                      \
   k_cheb<TV, TC, SC, LA><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, gx, gy, gz, g->tab, V.r, zprev, zcur, znext, \
                                                 V.invd, c1, c2, g->partials, g->partials_stride, g->counters)
@@ -664,9 +670,8 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
   thermal_grid* g = P.g;
   TV* zf = z_final(P, V);
   if constexpr (sizeof(TV) == 8) {
-    k_spmv_dot<double, double><<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, zf,
-                                                      V.p[parity], V.p[1 - parity], V.mu, g->partials,
-                                                      g->partials_stride, g->counters);
+    k_spmv_dot64x<<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64, g->dg64, zf, V.p[parity], V.p[1 - parity], V.mu,
+                                         g->partials, g->partials_stride, g->counters);
   } else if (P.v4) {
     TH_UNI(P.uni, k_spmv_dot_v4<U><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
                                                            g->tab, zf, V.p[parity], V.p[1 - parity], V.mu,
@@ -1563,13 +1568,11 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
                                                        g->partials, g->partials_stride, g->counters);
         break;
       case 6:
-        k_apply_f64<<<P.gb, P.tb, 0, s>>>(P.d, g->f64.gx, g->f64.gy, g->f64.gz, g->tab, g->zc64[0], g->zc64[1]);
+        k_apply64x<<<P.gb, P.tb, 0, s>>>(P.d, g->f64, g->dg64, g->zc64[0], g->zc64[1]);
         break;
       case 7:
-        k_cheb<double, double, true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f64.gx, g->f64.gy, g->f64.gz,
-                                                                  g->tab, W.r, W.zc[0], W.zc[1], W.zc[2], W.invd,
-                                                                  0.5, 0.5, g->partials, g->partials_stride,
-                                                                  g->counters);
+        k_cheb64x<true, false><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, g->f64, g->dg64, W.r, W.zc[0], W.zc[1], W.zc[2],
+                                                     W.invd, 0.5, 0.5, g->partials, g->partials_stride, g->counters);
         break;
       default:
         if (uni && P.v4) {
