@@ -1,5 +1,6 @@
 """The bench workload at full size (1024 x 1024 x 8, 8.4M unknowns), in the launch
-configuration bench.py times (mixed FP32/FP64, Chebyshev degree 6, CUDA graph).
+configuration bench.py times (mixed FP32/FP64, Chebyshev degree 20 in fused 4-step
+chunks, inner tolerance 1e-5, quadratic extrapolated guess, CUDA graph).
 
 The oracle cannot solve this system in seconds, so it checks properties that fix the
 answer at any size: the FP64 relative residual of the returned temperatures against
@@ -44,7 +45,7 @@ def test_fullsize_steps_residual_and_energy(setup):
     for s in range(3):
         P = maps[s % 4]
         T, stats = g.run_transient([torch.from_numpy(P).cuda()], 25, 1, DT, T, precision="mixed",
-                                   precond="cheb", cheb_degree=6, tol_rel=1e-8, use_graph=1)
+                                   precond="cheb", cheb_degree=20, inner_tol=1e-5, tol_rel=1e-8, use_graph=1)
         Th = T.cpu().numpy()
         b = disc.rhs_transient(NX, NY, st, P.astype(np.float64), prev, DT)
         rel = osolve.rel_residual(A, Th, b, st.t_amb)
@@ -60,8 +61,11 @@ def test_fullsize_mixed_matches_fp64_path(setup):
     maps = [torch.from_numpy(m).cuda() for m in [inst.power] + list(inst.extra_power)]
     Tm = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
     Td = Tm.clone()
-    g.run_transient(maps, 2, 4, DT, Tm, precision="mixed", cheb_degree=6, tol_rel=1e-10, use_graph=1)
-    g.run_transient(maps, 2, 4, DT, Td, precision="fp64", cheb_degree=6, tol_rel=1e-10, use_graph=1)
+    # the bench's configuration (quadratic extrapolation over the 8 steps, maps switching
+    # every 2) against the plain FP64 path warm-started from the previous step
+    g.run_transient(maps, 2, 8, DT, Tm, precision="mixed", cheb_degree=20, inner_tol=1e-5, guess=2, tol_rel=1e-10,
+                    use_graph=1)
+    g.run_transient(maps, 2, 8, DT, Td, precision="fp64", cheb_degree=6, guess=0, tol_rel=1e-10, use_graph=1)
     rise = (Td - st.t_amb).abs().max().item()
     assert (Tm - Td).abs().max().item() <= 1e-6 * rise
 
