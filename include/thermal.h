@@ -141,7 +141,8 @@ void thermal_default_opts(thermal_solve_opts* opts);
  * k[layers]: thermal conductivity per layer, W/(m K), > 0 (host).
  * c[layers]: volumetric heat capacity per layer, J/(m^3 K), > 0; may be NULL for a
  *            steady-only grid (transient calls then fail with TH_ESTATE).
- * h:         convective coefficient of the top face, W/(m^2 K), >= 0.
+ * h:         convective coefficient of the top face, W/(m^2 K), >= 0; h = 0 leaves
+ *            only transient solves (steady, adjoint and batched calls: TH_EINVAL).
  * The geometry must be set with thermal_grid_set_geometry before any solve.
  * Allocates the face-conductance arrays on the current device.
  */
@@ -279,7 +280,8 @@ th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, 
  * (TH_F32 or TH_F64), W per cell, host or device.  T: n_cells doubles, deg C, host
  * or device; on entry the initial guess when opts->use_guess, on exit the solution.
  * Stops at ||P - G theta||_2 <= tol_rel ||P||_2 (theta = T - T_amb, FP64).
- * Returns TH_ENOCONV (with T holding the last iterate) if the limits are reached.
+ * Returns TH_ENOCONV (with T holding the last iterate) if the limits are reached,
+ * TH_EINVAL if the grid has h = 0 (every face adiabatic: G is singular).
  */
 th_status thermal_solve_steady(thermal_grid* g, const void* power, int power_dtype, double* T,
                                const thermal_solve_opts* opts, thermal_solve_stats* stats,
@@ -338,7 +340,8 @@ th_status thermal_grad(thermal_grid* g, const double* T, const double* dJdT, voi
  * (device, power_dtype) and T[i] (device doubles, deg C; the initial guess when
  * opts->use_guess).  Finished instances drop out of the work list while the others
  * keep iterating.  stats[i] (host array of n) receives each instance's result; the
- * return value is the first non-OK instance status, or TH_OK.
+ * return value is the first non-OK instance status, or TH_OK.  n = 0 is a no-op
+ * (the arrays may then be NULL); an instance with h = 0 is TH_EINVAL (G singular).
  */
 th_status thermal_solve_batched(thermal_grid* const* grids, int n, const void* const* power,
                                 int power_dtype, double* const* T, const thermal_solve_opts* opts,

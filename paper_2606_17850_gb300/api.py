@@ -204,7 +204,10 @@ def solve_batched(grids: List[ThermalGrid], powers: List[torch.Tensor], Ts: List
     gh = (C.c_void_p * n)(*[g.handle.value for g in grids])
     ph = (C.c_void_p * n)(*[p.data_ptr() for p in powers])
     th = (C.c_void_p * n)(*[t.data_ptr() for t in Ts])
-    L.check(L.load().thermal_solve_batched(gh, n, ph, _dtype_code(powers[0]), th, C.byref(o), stats, _stream()))
+    if not (len(powers) == len(Ts) == n):
+        raise ValueError("grids, powers and Ts must have the same length")
+    pdt = _dtype_code(powers[0]) if n else L.TH_F64
+    L.check(L.load().thermal_solve_batched(gh, n, ph, pdt, th, C.byref(o), stats, _stream()))
     return [s.as_dict() for s in stats]
 
 

@@ -570,14 +570,16 @@ extern "C" th_status thermal_solve_batched(thermal_grid* const* grids, int n, co
                                            thermal_solve_stats* stats, void* stream) {
   try {
     th_clear_error();
-    if (!grids || !power || !T || n < 0) return th_fail(TH_EINVAL, "NULL argument or n < 0");
+    if (n < 0) return th_fail(TH_EINVAL, "n < 0");
     TH_TRY(validate_opts(opts));
     if (power_dtype != TH_F32 && power_dtype != TH_F64) return th_fail(TH_EINVAL, "power dtype");
-    if (n == 0) return TH_OK;
+    if (n == 0) return TH_OK;  // the arrays may be NULL when there is nothing to solve
+    if (!grids || !power || !T) return th_fail(TH_EINVAL, "NULL argument");
     bool all_dev = true, v4 = true;
     for (int i = 0; i < n; ++i) {
       if (!grids[i] || !power[i] || !T[i]) return th_fail(TH_EINVAL, "instance %d has a NULL pointer", i);
       if (!grids[i]->geom) return th_fail(TH_ESTATE, "instance %d has no geometry", i);
+      if (!(grids[i]->h > 0.0)) return th_fail(TH_EINVAL, "instance %d has h = 0 (G singular)", i);
       all_dev = all_dev && is_device_pointer(power[i]) && is_device_pointer(T[i]);
       v4 = v4 && grids[i]->nx % 4 == 0 && ((uintptr_t)power[i] % 16) == 0;
     }

@@ -1264,6 +1264,9 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   Plan P;
   const bool transient = (kind == KIND_STEP || kind == KIND_RUN);
   if (o->guess < 0 || o->guess > 2) return th_fail(TH_EINVAL, "guess must be 0, 1 or 2");
+  // with h = 0 every face of G is adiabatic: G 1 = 0 and the steady system is singular
+  if (!transient && !(g->h > 0.0))
+    return th_fail(TH_EINVAL, "a steady solve needs h > 0 (h = 0 leaves G singular)");
   const double toff = (kind == KIND_ADJ) ? 0.0 : g->t_amb;  // the adjoint state has no offset
   TH_TRY(make_plan(g, transient ? dt : 0.0, o, pdtype, transient, P, s));
   P.extrap = (kind == KIND_RUN && o->guess >= 1);

@@ -108,3 +108,14 @@ def test_oracle_zline_exact_without_inplane_coupling():
     A = disc.assemble(1, 1, st)
     r = ti.random_vector(st.L, 3)
     np.testing.assert_allclose(krylov.zline(A, 1, 1, st.L)(r), np.linalg.solve(A.toarray(), r), rtol=1e-12)
+
+
+def test_empty_and_negative_batches(lib):
+    """n = 0 solves nothing and touches no device; n < 0 and bad options are rejected."""
+    from paper_2606_17850_gb300 import _lib
+    o = _lib.default_opts()
+    assert lib.thermal_solve_batched(None, 0, None, _lib.TH_F64, None, C.byref(o), None, None) == _lib.TH_OK
+    assert lib.thermal_solve_batched(None, -1, None, _lib.TH_F64, None, C.byref(o), None, None) == _lib.TH_EINVAL
+    assert lib.thermal_solve_batched(None, 0, None, 7, None, C.byref(o), None, None) == _lib.TH_EINVAL
+    o.cheb_degree = 0
+    assert lib.thermal_solve_batched(None, 0, None, _lib.TH_F64, None, C.byref(o), None, None) == _lib.TH_EINVAL

@@ -638,3 +638,78 @@ def test_invalid_options_rejected():
         g.solve_steady(cuda(inst.power), inner_tol=2.0)
     with pytest.raises(ThermalError):
         g.solve_steady(cuda(inst.power), cheb_degree=0)
+
+
+# ----------------------------------------------------------------- degenerate inputs
+
+def _one_layer(h=1e4):
+    return ti.Stack((ti.Layer("si", 100e-6, 150.0, 1.63e6, True),), h=h)
+
+
+@pytest.mark.parametrize("nx,ny", [(36, 21), (37, 21), (1, 1), (4, 1)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_layer_steady_and_transient(nx, ny, prec):
+    """L = 1: no vertical faces, the top layer is also the bottom one."""
+    st = _one_layer()
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, 3)], np.float64)
+    g = grid_of(nx, ny, st)
+    T, stats = g.solve_steady(cuda(P), precision=prec, tol_rel=1e-10, cheb_degree=8)
+    assert stats["status"] == 0
+    ref = osolve.steady(nx, ny, st, P)
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+    dt = 1e-4
+    T0 = np.full(nx * ny, st.t_amb)
+    T = cuda(T0.copy())
+    T, stats = g.run_transient([cuda(P)], 1, 5, dt, T, precision=prec, tol_rel=1e-10, cheb_degree=8, guess=2)
+    ref = osolve.transient(nx, ny, st, [P] * 5, dt, T0)[-1]
+    assert stats["status"] == 0 and stats["steps"] == 5
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+def test_single_layer_fused_chebyshev():
+    st = _one_layer()
+    nx, ny, dt = 64, 40, 1e-4
+    g = grid_of(nx, ny, st)
+    r = cuda(ti.random_vector(nx * ny, 9), torch.float32)
+    z1 = g.precond(r, dt, precond="cheb", cheb_degree=12, cheb_fuse=1)
+    scale = z1.abs().max().item()
+    for fuse in (0, 2, 3, 4):
+        zf = g.precond(r, dt, precond="cheb", cheb_degree=12, cheb_fuse=fuse)
+        assert (zf - z1).abs().max().item() <= 1e-6 * scale, fuse
+
+
+def test_adiabatic_grid():
+    """h = 0: G 1 = 0, so the steady system is singular and rejected; transient steps
+    are well posed and conserve energy, sum_i C_i V_i (T_{n+1} - T_n)_i = dt sum_i p_i."""
+    from paper_2606_17850_gb300 import ThermalError
+    st = ti.stack_c1(h=0.0)
+    nx, ny, dt = 40, 23, 1e-4
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, 7)], np.float64)
+    g = grid_of(nx, ny, st)
+    with pytest.raises(ThermalError) as e:
+        g.solve_steady(cuda(P))
+    assert e.value.status == 1
+    T0 = np.full(nx * ny * st.L, st.t_amb)
+    for prec in ("fp64", "mixed"):
+        T = cuda(T0.copy())
+        T, stats = g.run_transient([cuda(P)], 1, 6, dt, T, precision=prec, tol_rel=1e-11, cheb_degree=8)
+        assert stats["status"] == 0
+        ref = osolve.transient(nx, ny, st, [P] * 6, dt, T0)[-1]
+        Th = T.cpu().numpy()
+        assert osolve.rise_relative_error(Th, ref, st.t_amb) <= 1e-6
+        c = disc.capacity_over_dt(nx, ny, st, dt) * dt
+        assert abs(c @ (Th - T0) - 6 * dt * P.sum()) <= 1e-7 * 6 * dt * P.sum()
+    from paper_2606_17850_gb300 import solve_batched
+    with pytest.raises(ThermalError):
+        solve_batched([g], [cuda(P)], [cuda(T0.copy())])
+
+
+def test_empty_runs():
+    from paper_2606_17850_gb300 import solve_batched
+    inst = ti.c1(nx=8, ny=8)
+    g = grid_of(8, 8, inst.stack)
+    T0 = cuda(np.full(inst.n, inst.stack.t_amb + 1.0))
+    T = T0.clone()
+    g.run_transient([cuda(inst.power)], 1, 0, 1e-4, T)
+    assert torch.equal(T, T0)
+    assert solve_batched([], [], []) == []
