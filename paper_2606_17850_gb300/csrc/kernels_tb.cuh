@@ -15,13 +15,19 @@
 // while the current tile computes; completion is tracked by an mbarrier.  Two plane
 // buffers alternate between steps, so a step needs a single CTA barrier.
 //
-// Per-layer constants (face conductances of the layer table, sink, the inverse
-// diagonal for every in-plane boundary case) and the step coefficients are kernel
-// parameters, so the stencil's multiplications take them straight from the
-// constant bank.  Missing neighbours (domain edges) are read as the cell itself,
-// which makes their difference term exactly zero, as the adiabatic boundary
-// requires; the accumulation order equals the one-step kernels' (s v, +x, -x, +y,
-// -y, +z, -z).
+// Per-layer constants (face conductances of the layer table, the diagonal of an
+// interior cell, the inverse diagonal for every in-plane boundary case) and the
+// step coefficients are kernel parameters, so the stencil's multiplications take
+// them straight from the constant bank.  The product is taken in expanded form,
+// (A v)_i = d v_i - gx (v_E + v_W) - gy (v_N + v_S) - gzu v_U - gzd v_D, the
+// diagonal-plus-off-diagonals form of the paper's stored product (Algorithm 3),
+// with d the diagonal of a cell that has all four in-plane faces.  A missing
+// neighbour (domain edge) is read as the cell itself: its -g v_i cancels the g v_i
+// that d holds for the absent face, which is the adiabatic boundary.  Seven FP32
+// operations per cell instead of the difference form's thirteen; the result equals
+// the one-step kernels' difference form up to rounding.  With the Jacobi scaling
+// D^-1 r is formed once per tile, so a step's update is one FMA more than the
+// stencil: z_{m+1} = z_m + c1 (z_m - z_{m-1}) + c2 (D^-1 r - D^-1 A z_m).
 //
 // DRAM traffic per S steps: the three inputs once plus one or two outputs
 // (about 20 B/cell) instead of 16 B/cell per step.
@@ -40,7 +46,7 @@
 template <int LMAX>
 struct TBParams {
   float c1[TB_H], c2[TB_H];     // Chebyshev step coefficients of this chunk
-  float s[LMAX];                // sink (+ capacity) per layer
+  float d[LMAX];                // diagonal of a cell with all four in-plane faces
   float gx[LMAX], gy[LMAX];     // in-plane face conductances per layer
   float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
@@ -125,6 +131,13 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
   const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
 
+  // Layers L..LMAX-1 of the three boxes, and the whole z_{m-1} box when there is
+  // none, are never written by the tensor copies: zero them once, so the staged
+  // loads below need no per-layer guard.
+  for (int b = 0; b < 3; ++b) {
+    const int z0 = (b == 1 && !has_prev) ? 0 : L;
+    for (int i = tid; i < (LMAX - z0) * SL; i += TB_EX * EY) stage[(b * LMAX + z0) * SL + i] = 0.f;
+  }
   if (tid == 0) {
     tb_mbar_init(bar, 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -132,14 +145,25 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   __syncthreads();
   // the box starts at the grown tile's first column rounded down to a multiple of 4
   // cells (a 16-byte boundary, as the tensor copy requires)
-  auto issue = [&](int t) {
-    const int xa = ((t % ntx) * TX - H) & ~3, y0 = (t / ntx) * TY - H;
+  auto issue = [&](int tx, int ty) {
+    const int xa = (tx * TX - H) & ~3, y0 = ty * TY - H;
     tb_mbar_expect(bar, tx_bytes);
     tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
     if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
     tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
   };
-  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+  // tile t = tx + ntx ty, advanced by gridDim.x without a division per tile
+  const int dtx = (int)gridDim.x % ntx, dty = (int)gridDim.x / ntx;
+  auto advance = [&](int& tx, int& ty) {
+    tx += dtx;
+    ty += dty;
+    if (tx >= ntx) {
+      tx -= ntx;
+      ++ty;
+    }
+  };
+  int tx = (int)blockIdx.x % ntx, ty = (int)blockIdx.x / ntx;
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(tx, ty);
 
   float part[1] = {0.f};
   unsigned parity = 0;
@@ -154,62 +178,67 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       break;
     }
     parity ^= 1u;
-    const int x0 = (t % ntx) * TX - H;
+    const int x0 = tx * TX - H;
     const int gx = x0 + ex;
-    const int gy = (t / ntx) * TY - H + ey;
+    const int gy = ty * TY - H + ey;
     const int st = ey * TB_BW + ex + (x0 - (x0 & ~3));  // this column in a staged layer
     const bool inside = gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
-    float cur[LMAX], prv[LMAX], rr[LMAX], inv[LMAX];
+    // za / zb hold z_m / z_{m-1} and swap roles every step: a step writes z_{m+1}
+    // over z_{m-1}, so no register moves are needed.  A row that skips a step keeps
+    // stale values in the swapped arrays; it lies outside the valid region from then
+    // on and is read only by rows that are outside it too.
+    float za[LMAX], zb[LMAX], rr[LMAX], inv[LMAX], rs[LMAX];
     const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
-      const bool on = z < L;
-      cur[z] = on ? stage[z * SL + st] : 0.f;
-      prv[z] = (on && has_prev) ? stage[(LMAX + z) * SL + st] : 0.f;
-      rr[z] = on ? stage[(2 * LMAX + z) * SL + st] : 0.f;
+      za[z] = stage[z * SL + st];
+      zb[z] = stage[(LMAX + z) * SL + st];
+      rr[z] = stage[(2 * LMAX + z) * SL + st];
       inv[z] = P.invd[nxf + 3 * nyf][z];
+      rs[z] = (SCALED && !LAST) ? rr[z] * inv[z] : rr[z];  // D^-1 r, fixed over the chunk
     }
     __syncthreads();  // staging buffer consumed by every thread
     const int tn = t + gridDim.x;
+    int txn = tx, tyn = ty;
+    advance(txn, tyn);
     if (tid == 0 && tn < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(tn);
+      issue(txn, tyn);
     }
     // neighbour offsets inside a plane; a missing neighbour reads the cell itself
     const int oR = tid + ((gx + 1 < d.nx) ? 1 : 0), oL = tid - ((gx > 0) ? 1 : 0);
     const int oU = tid + ((gy + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gy > 0) ? TB_EX : 0);
-#pragma unroll
-    for (int j = 0; j < STEPS; ++j) {
+    auto step = [&](const float (&C)[LMAX], float (&N)[LMAX], const int j) {
       float* pl = plane + (j & 1) * LMAX * PL;
 #pragma unroll
-      for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = cur[z];
+      for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = C[z];
       __syncthreads();
       // rows outside the shrinking valid region skip the step as whole warps
       const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
       if (upd) {
-        float below = 0.f;  // z_m of the layer below (before its update)
 #pragma unroll
         for (int z = 0; z < LMAX; ++z) {
-          const float v = cur[z];
-          const float va = (z + 1 < LMAX) ? cur[z + 1 < LMAX ? z + 1 : z] : 0.f;
+          const float v = C[z];
           const float* q = pl + z * PL;
-          float a = P.s[z] * v;
-          a += P.gx[z] * (v - q[oR]);
-          a += P.gx[z] * (v - q[oL]);
-          a += P.gy[z] * (v - q[oU]);
-          a += P.gy[z] * (v - q[oD]);
-          if (z + 1 < LMAX) a += P.gzu[z] * (v - va);
-          if (z > 0) a += P.gzd[z] * (v - below);
-          float res = rr[z] - a;
-          if (SCALED) res *= inv[z];
-          const float nxt = v + P.c1[j] * (v - prv[z]) + P.c2[j] * res;
-          below = v;
-          prv[z] = v;
-          cur[z] = nxt;
+          float a = P.d[z] * v;
+          a = fmaf(-P.gx[z], q[oR] + q[oL], a);
+          a = fmaf(-P.gy[z], q[oU] + q[oD], a);
+          if (z + 1 < LMAX) a = fmaf(-P.gzu[z], C[z + 1 < LMAX ? z + 1 : z], a);
+          if (z > 0) a = fmaf(-P.gzd[z], C[z > 0 ? z - 1 : z], a);
+          // the last chunk keeps r for z^T r and scales the residual instead
+          const float res = !SCALED ? rr[z] - a : (LAST ? (rr[z] - a) * inv[z] : fmaf(-inv[z], a, rs[z]));
+          N[z] = fmaf(P.c2[j], res, fmaf(P.c1[j], v - N[z], v));
         }
       }
+    };
+#pragma unroll
+    for (int j = 0; j < STEPS; ++j) {
+      if (j & 1) step(zb, za, j);
+      else step(za, zb, j);
     }
-    // the interior columns hold z_{m+STEPS} (cur) and z_{m+STEPS-1} (prv)
+    // the interior columns hold z_{m+STEPS} and z_{m+STEPS-1}
+    const float(&cur)[LMAX] = (STEPS & 1) ? zb : za;
+    const float(&prv)[LMAX] = (STEPS & 1) ? za : zb;
     const bool interior = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
     if (interior) {
       const long long base = (long long)gx + (long long)d.nx * gy;
@@ -223,6 +252,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
         }
       }
     }
+    tx = txn;
+    ty = tyn;
   }
   if (!LAST) return;
   double tot[1];

@@ -515,7 +515,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   const LayerTab& T = g->tab_host;
   const int L = P.d.L;
   for (int z = 0; z < L; ++z) {
-    prm.s[z] = T.s32[z];
+    const float sz = T.s32[z];
     prm.gx[z] = T.gxl[z];
     prm.gy[z] = T.gyl[z];
     prm.gzu[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
@@ -523,7 +523,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
     // diagonal summed in the one-step kernels' order: s, +x, -x, +y, -y, +z, -z
     for (int nyf = 0; nyf < 3; ++nyf)
       for (int nxf = 0; nxf < 3; ++nxf) {
-        float dg = prm.s[z];
+        float dg = sz;
         dg += nxf >= 1 ? prm.gx[z] : 0.f;
         dg += nxf >= 2 ? prm.gx[z] : 0.f;
         dg += nyf >= 1 ? prm.gy[z] : 0.f;
@@ -531,6 +531,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
         dg += prm.gzu[z];
         dg += prm.gzd[z];
         prm.invd[nxf + 3 * nyf][z] = 1.0f / dg;
+        if (nxf == 2 && nyf == 2) prm.d[z] = dg;
       }
   }
   CUtensorMap mc, mp, mr;
