@@ -5,9 +5,9 @@
 //
 // GB300 executes FP64 at about 1/64 of its FP32 rate, so the FP64 refinement
 // residual of the mixed path (about 20 FP64 operations per cell) is ALU-bound; in
-// double-float the same residual costs about 170 FP32 operations per cell and is
-// bound by HBM bandwidth instead.  The residual needs ~1e-12 relative accuracy on
-// each face flux (the fluxes through a cell cancel down to its power), which
+// double-float the same residual costs about 165 FP32 operations per cell (with
+// the unnormalised forms below).  The residual needs ~1e-12 relative accuracy on each
+// face flux (the fluxes through a cell cancel down to its power), which
 // double-float provides and FP32 does not.
 #pragma once
 
@@ -64,6 +64,26 @@ __device__ __forceinline__ df df_mul_f(df a, float b) {
   df p = two_prod(a.hi, b);
   const float e = __fmaf_rn(a.lo, b, p.lo);
   return fast_two_sum(p.hi, e);
+}
+
+// Unnormalised ("lazy") forms for chains of operations whose result is rounded to
+// FP32 at the end: the sum keeps TwoSum's exact high part and adds the low parts
+// without the final Fast2Sum, the product keeps TwoProduct's exact high part and
+// the two cross terms.  The low part may then exceed ulp(hi)/2, but the absolute
+// error of a chain stays of the order 2^-47 times its largest operand, the same
+// order as the normalised forms' (the low parts of double-float inputs already
+// carry that much rounding).
+__device__ __forceinline__ df ldf_add(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return df_make(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df ldf_sub(df a, df b) { return ldf_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df ldf_mul(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.hi, b.hi, -p)));
+  return df_make(p, e);
 }
 
 // FP64 <-> double-float (used once per solve at the boundary, not in the loops)
