@@ -200,7 +200,9 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
              });
 }
 
-// Vectorised k_update (element-wise; one thread per 4 consecutive cells).
+// Vectorised k_update (element-wise; a thread handles groups of 4 consecutive
+// cells, grid-stride, so that a grid of a few blocks per SM keeps the number of
+// per-block partials of the reduction small).
 template <bool INIT, int ZMODE>
 static __global__ void __launch_bounds__(256)
     k_update_v4(long long n4, Ctl* ctl, float* __restrict__ x, const float* __restrict__ p, float* __restrict__ r,
@@ -208,11 +210,11 @@ static __global__ void __launch_bounds__(256)
                 int scaled, int rz_here, int scale_r, double* partials, int stride, unsigned* counter) {
   if (!INIT && ld_int(&ctl->done)) return;
   if (INIT && ld_int(&ctl->outer_done)) return;
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const float alpha = INIT ? 0.f : ctl_alpha<float>(ctl);
   const float rs = (INIT && scale_r) ? __ldcg(&ctl->rscale_f) : 1.f;
   float v[2] = {0.f, 0.f};
-  if (q < n4) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+       q += (long long)gridDim.x * blockDim.x) {
     const long long i = 4 * q;
     float4 rv = ld4(r + i);
     float rr[4] = {rv.x, rv.y, rv.z, rv.w};
@@ -279,7 +281,7 @@ __device__ __forceinline__ void ldp4(const double* p, df (&o)[4]) {
 // whole value in the low part, and the next sum then rounds it relative to |theta|
 // rather than to the difference.
 template <typename TP>
-__global__ void __launch_bounds__(TH_BX* TH_BY4)
+__global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three blocks per SM
     k_residual_df_v4(Dims d, int zc, Ctl* ctl, const LayerTab* tab, const float* __restrict__ th_hi,
                      const float* __restrict__ th_lo, const TP* const* ptab, const float* __restrict__ thn_hi,
                      const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer, double* partials,

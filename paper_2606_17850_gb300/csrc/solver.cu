@@ -67,6 +67,7 @@ struct Plan {
   QDiag qdiag{};
   dim3 gb4, tb4;
   unsigned nbu4 = 1;
+  unsigned nbr4 = 1;  // grid of the grid-stride reducing element-wise kernels
 };
 
 static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
@@ -180,6 +181,8 @@ th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* 
 }
 
 // ------------------------------------------------------------------ z-chunk autotuner
+
+static int sm_count();
 
 static dim3 v4_blocks(const thermal_grid* g, int zc) {
   return dim3((g->nx + 4 * TH_BX - 1) / (4 * TH_BX), (g->ny + TH_BY4 - 1) / TH_BY4, (g->L + zc - 1) / zc);
@@ -332,6 +335,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     P.tb4 = dim3(TH_BX, TH_BY4);
     P.gb4 = v4_blocks(g, P.zc);
     P.nbu4 = (unsigned)((g->n / 4 + 255) / 256);
+    P.nbr4 = std::min(P.nbu4, (unsigned)(8 * sm_count()));
   }
   P.pc_spmv = 0;
   if (P.pc == TH_PC_CHEB) {
@@ -425,7 +429,7 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
   if constexpr (sizeof(TV) == 4) {
     if (P.v4) {
 #define TH_UPD4(ZM)                                                                                          \
-  k_update_v4<INIT, ZM><<<P.nbu4, 256, 0, st>>>(P.d.n / 4, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], zs, P.scaled, \
+  k_update_v4<INIT, ZM><<<P.nbr4, 256, 0, st>>>(P.d.n / 4, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], zs, P.scaled, \
                                                 rz1, scale_r, g->partials, g->partials_stride, g->counters)
       switch (P.pc) {
         case TH_PC_NONE: TH_UPD4(0); break;
@@ -1558,7 +1562,7 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
         break;
       case 4:
         if (P.v4) {
-          k_update_v4<false, 1><<<P.nbu4, 256, 0, s>>>(P.d.n / 4, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0],
+          k_update_v4<false, 1><<<P.nbr4, 256, 0, s>>>(P.d.n / 4, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0],
                                                       1.0f, 1, 1, 0, g->partials, g->partials_stride, g->counters);
           break;
         }
