@@ -167,17 +167,16 @@ __global__ void k_copy_df(long long n, const float* __restrict__ ah, const float
   bl[i] = al[i];
 }
 
-// Start of a step with the extrapolated guess: theta_n <- theta (the solution of
-// the previous step), theta <- 2 theta_n - theta_{n-1}, theta_{n-1} <- theta_n.
-__global__ void k_step_extrap_df(long long n, float* th_hi, float* th_lo, float* thn_hi, float* thn_lo,
-                                 float* thm_hi, float* thm_lo) {
+// Start of a step with the extrapolated guess: theta <- 2 theta_n - theta_{n-1} and
+// theta_{n-1} <- theta_n, theta holding the previous step's solution theta_n on
+// entry.  The history array then holds theta_n for the whole step, so it also serves
+// as the step's theta_n (the right-hand side's C/dt T_n term).
+__global__ void k_step_extrap_df(long long n, float* th_hi, float* th_lo, float* thm_hi, float* thm_lo) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const df cur = df_make(th_hi[i], th_lo[i]);
   const df prev = df_make(thm_hi[i], thm_lo[i]);
   const df g = df_sub(df_add(cur, cur), prev);
-  thn_hi[i] = cur.hi;
-  thn_lo[i] = cur.lo;
   thm_hi[i] = cur.hi;
   thm_lo[i] = cur.lo;
   th_hi[i] = g.hi;

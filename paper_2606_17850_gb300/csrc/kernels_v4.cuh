@@ -382,8 +382,7 @@ static __global__ void __launch_bounds__(256)
 
 // Start of a step with the extrapolated guess (see k_step_extrap_df).
 static __global__ void __launch_bounds__(256)
-    k_step_extrap_df_v4(long long n4, float* th_hi, float* th_lo, float* thn_hi, float* thn_lo, float* thm_hi,
-                        float* thm_lo) {
+    k_step_extrap_df_v4(long long n4, float* th_hi, float* th_lo, float* thm_hi, float* thm_lo) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n4) return;
   const long long i = 4 * q;
@@ -396,8 +395,6 @@ static __global__ void __launch_bounds__(256)
     gh[k] = g.hi;
     gl[k] = g.lo;
   }
-  st4(thn_hi + i, ch);
-  st4(thn_lo + i, cl);
   st4(thm_hi + i, ch);
   st4(thm_lo + i, cl);
   st4(th_hi + i, make_float4(gh[0], gh[1], gh[2], gh[3]));
@@ -408,8 +405,8 @@ static __global__ void __launch_bounds__(256)
 // 3 theta_{n-1} + theta_{n-2} (2 theta_n - theta_{n-1} on the second step, theta_n on
 // the first), history shifted; theta holds the previous step's solution on entry.
 static __global__ void __launch_bounds__(256)
-    k_step_extrap2_df_v4(long long n4, const Ctl* ctl, float* th_hi, float* th_lo, float* thn_hi, float* thn_lo,
-                         float* thm_hi, float* thm_lo, float* thm2_hi, float* thm2_lo) {
+    k_step_extrap2_df_v4(long long n4, const Ctl* ctl, float* th_hi, float* th_lo, float* thm_hi, float* thm_lo,
+                         float* thm2_hi, float* thm2_lo) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n4) return;
   const int step = ld_int(&ctl->step);
@@ -430,8 +427,6 @@ static __global__ void __launch_bounds__(256)
     gh[k] = g.hi;
     gl[k] = g.lo;
   }
-  st4(thn_hi + i, ch);
-  st4(thn_lo + i, cl);
   st4(thm2_hi + i, ph);
   st4(thm2_lo + i, pl);
   st4(thm_hi + i, ch);

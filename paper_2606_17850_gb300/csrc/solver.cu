@@ -696,8 +696,9 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
 static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int count_outer, bool out64) {
   thermal_grid* g = P.g;
   if (!out64 && mode == 0) {  // mixed path: double-float residual
-    const float* nh = P.transient ? g->thn_hi : nullptr;
-    const float* nl = P.transient ? g->thn_lo : nullptr;
+    // theta_n of the step: with the extrapolated guess the history array holds it
+    const float* nh = P.transient ? (P.extrap ? g->thm_hi : g->thn_hi) : nullptr;
+    const float* nl = P.transient ? (P.extrap ? g->thm_lo : g->thn_lo) : nullptr;
     if (P.uni && P.v4) {
       if (P.pdtype == TH_F32)
         k_residual_df_v4<float><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
@@ -910,14 +911,12 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
       k_step_extrap64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n, g->thm64);
     else
       if (P.extrap_order == 2)
-        k_step_extrap2_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->ctl, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo,
-                                                     g->thm_hi, g->thm_lo, g->thm2_hi, g->thm2_lo);
+        k_step_extrap2_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->ctl, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo,
+                                                     g->thm2_hi, g->thm2_lo);
       else if (P.v4)
-        k_step_extrap_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo, g->thm_hi,
-                                                    g->thm_lo);
+        k_step_extrap_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo);
       else
-        k_step_extrap_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thn_hi, g->thn_lo, g->thm_hi,
-                                                 g->thm_lo);
+        k_step_extrap_df<<<nb1(n), 256, 0, st>>>(n, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo);
     TH_CHECK_LAUNCH();
     return TH_OK;
   }
