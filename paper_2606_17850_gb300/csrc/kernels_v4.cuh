@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
         // exactly); the sums, products and the accumulation run unnormalised
         const df dx = ldf_add(df_sub(t, tr), df_sub(t, tl));
         const df dy = ldf_add(df_sub(t, df_make(cmp(hu, k), cmp(lu, k))), df_sub(t, df_make(cmp(hd, k), cmp(ld_, k))));
-        df acc = ldf_sub(pv[k], ldf_mul(sk, t));
+        df acc = pv[k];
+        if (sk.hi != 0.f) acc = ldf_sub(acc, ldf_mul(sk, t));  // the sink is on the top layer only
         float bh = pv[k].hi;  // ||b|| needs FP32 accuracy only
         if (thn_hi) {
           const df tn = df_make(cmp(nh, k), cmp(nl, k));
