@@ -280,16 +280,29 @@ __device__ __forceinline__ void ldp4(const double* p, df (&o)[4]) {
 // spreader.  Likewise an unnormalised difference whose high parts cancel keeps its
 // whole value in the low part, and the next sum then rounds it relative to |theta|
 // rather than to the difference.
-template <typename TP>
+//
+// ZI >= 0 also starts the inner solve on the unscaled r (what k_update_v4<true, ZI>
+// does after it): x = 0, z = r (ZI 0), D^-1 r (1) or zs (D^-1) r (2, D^-1 when
+// `scaled`), and r^T z; the last block then makes the inner solve's start decision
+// unless the system has converged, and the correction is applied with scale 1.
+struct ResidInit {
+  float* x;
+  const float* invd;
+  float* z;
+  float zs;
+  int scaled, rz_here;
+};
+
+template <typename TP, int ZI>
 __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three blocks per SM
     k_residual_df_v4(Dims d, int zc, Ctl* ctl, const LayerTab* tab, const float* __restrict__ th_hi,
                      const float* __restrict__ th_lo, const TP* const* ptab, const float* __restrict__ thn_hi,
-                     const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer, double* partials,
-                     int stride, unsigned* counter) {
+                     const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer, ResidInit ri,
+                     double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->outer_done)) return;
   const Walk4 w = walk4_of(d, zc);
   const TP* P = ptab[ld_int(&ctl->map_idx)];
-  float v[2] = {0.f, 0.f};
+  float v[3] = {0.f, 0.f, 0.f};
   if (w.valid) {
     const long long pxy = d.pxy;
     const bool hasL = w.x0 > 0, hasR = w.x0 + 4 < d.nx, hasD = w.y > 0, hasU = w.y + 1 < d.ny;
@@ -348,13 +361,33 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
         v[1] += bh * bh;
       }
       st4(r + i, make_float4(o[0], o[1], o[2], o[3]));
+      if (ZI >= 0) {
+        st4(ri.x + i, z4());
+        float zz[4] = {o[0], o[1], o[2], o[3]};
+        if (ZI == 1 || (ZI == 2 && ri.scaled)) {
+          const float4 iv = __ldg(reinterpret_cast<const float4*>(ri.invd + i));
+          zz[0] *= iv.x; zz[1] *= iv.y; zz[2] *= iv.z; zz[3] *= iv.w;
+        }
+        if (ZI == 2) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) zz[k] *= ri.zs;
+        }
+        if (ZI >= 1) st4(ri.z + i, make_float4(zz[0], zz[1], zz[2], zz[3]));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[2] += o[k] * zz[k];
+      }
       hb = hc; lb = lc;
       hc = ha; lc = la;
     }
   }
-  double tot[2];
-  if (!grid_reduce<float, 2>(v, partials, stride, counter, tot)) return;
+  double tot[3];
+  if (!grid_reduce<float, 3>(v, partials, stride, counter, tot)) return;
   fin_residual(ctl, tot[0], tot[1], 0, count_outer);
+  if (ZI >= 0) {
+    ctl->rnorm_hi = 1.f;  // the inner solve runs on the unscaled r
+    ctl->rnorm_lo = 0.f;
+    if (!ctl->outer_done) fin_update(ctl, tot[0], tot[2], true, ri.rz_here);
+  }
 }
 
 // Element-wise double-float kernels of the mixed path, 4 cells per thread (n % 4 == 0,

@@ -68,6 +68,7 @@ struct Plan {
   dim3 gb4, tb4;
   unsigned nbu4 = 1;
   unsigned nbr4 = 1;  // grid of the grid-stride reducing element-wise kernels
+  bool fused_init = false;  // the refinement residual also starts the inner solve
 };
 
 static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
@@ -370,6 +371,10 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
       }
     }
   }
+  // the refinement residual starts the inner solve itself (mixed path, layer table,
+  // 4-cell kernels, a first z that is a scaling of r)
+  P.fused_init = P.prec != TH_PREC_FP64 && !P.ad && P.v4 && P.uni &&
+                 (P.pc == TH_PC_NONE || P.pc == TH_PC_JACOBI || P.pc == TH_PC_CHEB);
   return TH_OK;
 }
 
@@ -693,6 +698,23 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
 
 // ------------------------------------------------------------------ enqueue: residual & control
 
+// zi: -1, or the preconditioner's z mode (0 none, 1 Jacobi, 2 Chebyshev) when the
+// residual also starts the inner solve
+template <typename TP>
+static void launch_residual_v4(const Plan& P, cudaStream_t st, const float* nh, const float* nl, int count_outer,
+                               int zi, const ResidInit& ri) {
+  thermal_grid* g = P.g;
+  const TP* const* pt = (const TP* const*)g->dev_ptrs;
+#define TH_RES4(ZI)                                                                                              k_residual_df_v4<TP, ZI><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo, pt, nh, nl,                                                     g->r32, count_outer, ri, g->partials, g->partials_stride,                                                      g->counters)
+  switch (zi) {
+    case 0: TH_RES4(0); break;
+    case 1: TH_RES4(1); break;
+    case 2: TH_RES4(2); break;
+    default: TH_RES4(-1); break;
+  }
+#undef TH_RES4
+}
+
 static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int count_outer, bool out64) {
   thermal_grid* g = P.g;
   if (!out64 && mode == 0) {  // mixed path: double-float residual
@@ -700,14 +722,21 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
     const float* nh = P.transient ? (P.extrap ? g->thm_hi : g->thn_hi) : nullptr;
     const float* nl = P.transient ? (P.extrap ? g->thm_lo : g->thn_lo) : nullptr;
     if (P.uni && P.v4) {
+      ResidInit ri{};
+      int zi = -1;
+      if (P.fused_init) {
+        zi = (P.pc == TH_PC_NONE) ? 0 : (P.pc == TH_PC_JACOBI ? 1 : 2);
+        ri.x = g->d32;
+        ri.invd = g->invd32;
+        ri.z = g->zc32[0];
+        ri.zs = (float)P.inv_theta;
+        ri.scaled = P.scaled;
+        ri.rz_here = (P.pc == TH_PC_NONE || P.pc == TH_PC_JACOBI || (P.pc == TH_PC_CHEB && P.k == 1)) ? 1 : 0;
+      }
       if (P.pdtype == TH_F32)
-        k_residual_df_v4<float><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
-                                                         (const float* const*)g->dev_ptrs, nh, nl, g->r32,
-                                                         count_outer, g->partials, g->partials_stride, g->counters);
+        launch_residual_v4<float>(P, st, nh, nl, count_outer, zi, ri);
       else
-        k_residual_df_v4<double><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
-                                                          (const double* const*)g->dev_ptrs, nh, nl, g->r32,
-                                                          count_outer, g->partials, g->partials_stride, g->counters);
+        launch_residual_v4<double>(P, st, nh, nl, count_outer, zi, ri);
       TH_CHECK_LAUNCH();
       return TH_OK;
     }
@@ -830,7 +859,7 @@ struct Pieces {
   // mixed: scale r, x = 0, z_0 = M r
   th_status inner_init(cudaStream_t st) {
     VecSet<float> V = vec32(P.g);
-    TH_TRY((enq_update<float, true>(P, V, st, 0, 1, 1)));
+    if (!P.fused_init) TH_TRY((enq_update<float, true>(P, V, st, 0, 1, 1)));
     return enq_precond_tail<float>(P, V, st);
   }
   th_status inner_pair(cudaStream_t st) {
@@ -1583,11 +1612,8 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
         break;
       default:
         if (uni && P.v4) {
-          k_residual_df_v4<float><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo,
-                                                          (const float* const*)g->dev_ptrs,
-                                                          P.transient ? g->thn_hi : nullptr,
-                                                          P.transient ? g->thn_lo : nullptr, g->r32, 0, g->partials,
-                                                          g->partials_stride, g->counters);
+          launch_residual_v4<float>(P, s, P.transient ? g->thn_hi : nullptr, P.transient ? g->thn_lo : nullptr, 0,
+                                    -1, ResidInit{});
           break;
         }
         TH_UNI(uni, k_residual_df<float, U><<<P.gb, P.tb, 0, s>>>(
