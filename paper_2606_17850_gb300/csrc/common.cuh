@@ -356,8 +356,10 @@ __device__ __forceinline__ bool grid_reduce(T (&v)[NQ], double* partials, int st
       for (int w = 0; w < nw; ++w) s += sm[q][w];
       partials[(size_t)q * stride + bid] = s;
     }
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
+    // acq_rel ticket: orders the partial above before the increment (release) in one
+    // round trip, instead of a full fence followed by a relaxed atomic
+    unsigned prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
     am_last = (prev == (unsigned)(block_count() - 1));
   }
   __syncthreads();
@@ -367,9 +369,20 @@ __device__ __forceinline__ bool grid_reduce(T (&v)[NQ], double* partials, int st
   double s[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    s[q] = 0.0;
-    for (int j = t; j < nb; j += block_threads()) s[q] += __ldcg(partials + (size_t)q * stride + j);
-    s[q] = warp_sum(s[q]);
+    // four independent accumulators, so the partials' loads overlap instead of
+    // forming a chain of dependent L2 round trips (fixed order: deterministic)
+    const double* pq = partials + (size_t)q * stride;
+    const int bt = block_threads();
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = t;
+    for (; j + 3 * bt < nb; j += 4 * bt) {
+      a0 += __ldcg(pq + j);
+      a1 += __ldcg(pq + j + bt);
+      a2 += __ldcg(pq + j + 2 * bt);
+      a3 += __ldcg(pq + j + 3 * bt);
+    }
+    for (; j < nb; j += bt) a0 += __ldcg(pq + j);
+    s[q] = warp_sum((a0 + a1) + (a2 + a3));
   }
   __syncthreads();
   if ((t & 31) == 0) {

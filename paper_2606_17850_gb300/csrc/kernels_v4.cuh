@@ -48,6 +48,26 @@ __device__ __forceinline__ Walk4 walk4_of(const Dims& d, int zc) {
   return w;
 }
 
+// Tiles (x block, y block, z chunk) of the z-walk, for kernels that walk them
+// grid-stride (a grid of resident blocks pays a reduction's per-block tail once).
+__device__ __forceinline__ int walk4_tiles(const Dims& d, int zc) {
+  const int gbx = (d.nx + 4 * TH_BX - 1) / (4 * TH_BX), gby = (d.ny + TH_BY4 - 1) / TH_BY4;
+  return gbx * gby * ((d.L + zc - 1) / zc);
+}
+
+__device__ __forceinline__ Walk4 walk4_tile(const Dims& d, int zc, int t) {
+  const int gbx = (d.nx + 4 * TH_BX - 1) / (4 * TH_BX), gby = (d.ny + TH_BY4 - 1) / TH_BY4;
+  const int bx = t % gbx, by = (t / gbx) % gby, bz = t / (gbx * gby);
+  Walk4 w;
+  w.x0 = 4 * (bx * TH_BX + threadIdx.x);
+  w.y = by * TH_BY4 + threadIdx.y;
+  w.zs = bz * zc;
+  w.ze = min(w.zs + zc, d.L);
+  w.valid = (w.x0 < d.nx) && (w.y < d.ny);
+  w.b0 = (long long)w.x0 + (long long)d.nx * w.y;
+  return w;
+}
+
 // Walks the layers of one 4-cell row segment.  V4(i) returns the operand at cells
 // i..i+3 (float4), V1(j) at one cell.  For each layer z calls
 // epi(i, z, v, acc, dg): v = operand, acc = (A v) and dg = A_ii for the 4 cells,
@@ -162,11 +182,13 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4)
                   const float* __restrict__ p_old, float* __restrict__ p_new, float* __restrict__ mu,
                   double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->done)) return;
-  const Walk4 w = walk4_of(d, zc);
   const int first = ld_int(&ctl->first);
   const float beta = first ? 0.f : ctl_beta<float>(ctl);
   float part[1] = {0.f};
-  if (w.valid) {
+  const int ntl = walk4_tiles(d, zc);
+  for (int t = blockIdx.x; t < ntl; t += gridDim.x) {
+    const Walk4 w = walk4_tile(d, zc, t);
+    if (!w.valid) continue;
     auto P4 = [&](long long i) -> float4 {
       const float4 a = ld4(z + i);
       if (first) return a;
@@ -300,10 +322,12 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
                      const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer, ResidInit ri,
                      double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->outer_done)) return;
-  const Walk4 w = walk4_of(d, zc);
   const TP* P = ptab[ld_int(&ctl->map_idx)];
   float v[3] = {0.f, 0.f, 0.f};
-  if (w.valid) {
+  const int ntl = walk4_tiles(d, zc);
+  for (int t = blockIdx.x; t < ntl; t += gridDim.x) {
+    const Walk4 w = walk4_tile(d, zc, t);
+    if (!w.valid) continue;
     const long long pxy = d.pxy;
     const bool hasL = w.x0 > 0, hasR = w.x0 + 4 < d.nx, hasD = w.y > 0, hasU = w.y + 1 < d.ny;
     float4 hb = z4(), lb = z4();

@@ -68,6 +68,7 @@ struct Plan {
   dim3 gb4, tb4;
   unsigned nbu4 = 1;
   unsigned nbr4 = 1;  // grid of the grid-stride reducing element-wise kernels
+  unsigned nbs4 = 1, nbq4 = 1;  // grids of the tile-walking spmv_dot and residual (resident blocks)
   bool fused_init = false;  // the refinement residual also starts the inner solve
 };
 
@@ -184,6 +185,16 @@ th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* 
 // ------------------------------------------------------------------ z-chunk autotuner
 
 static int sm_count();
+
+// blocks of a 256-thread z-walk kernel that are resident at once on the device
+static unsigned resident_grid(const void* fn) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH_BX * TH_BY4, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return (unsigned)(per_sm * sm_count());
+}
 
 static dim3 v4_blocks(const thermal_grid* g, int zc) {
   return dim3((g->nx + 4 * TH_BX - 1) / (4 * TH_BX), (g->ny + TH_BY4 - 1) / TH_BY4, (g->L + zc - 1) / zc);
@@ -337,6 +348,10 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     P.gb4 = v4_blocks(g, P.zc);
     P.nbu4 = (unsigned)((g->n / 4 + 255) / 256);
     P.nbr4 = std::min(P.nbu4, (unsigned)(8 * sm_count()));
+    const unsigned ntl = P.gb4.x * P.gb4.y * P.gb4.z;
+    P.nbs4 = std::min(ntl, resident_grid(g->uniform ? (const void*)k_spmv_dot_v4<true>
+                                                     : (const void*)k_spmv_dot_v4<false>));
+    P.nbq4 = std::min(ntl, resident_grid((const void*)k_residual_df_v4<float, 2>));
   }
   P.pc_spmv = 0;
   if (P.pc == TH_PC_CHEB) {
@@ -683,7 +698,7 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
     k_spmv_dot64x<<<P.gb, P.tb, 0, st>>>(P.d, g->ctl, g->f64, g->dg64, zf, V.p[parity], V.p[1 - parity], V.mu,
                                          g->partials, g->partials_stride, g->counters);
   } else if (P.v4) {
-    TH_UNI(P.uni, k_spmv_dot_v4<U><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
+    TH_UNI(P.uni, k_spmv_dot_v4<U><<<P.nbs4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
                                                            g->tab, zf, V.p[parity], V.p[1 - parity], V.mu,
                                                            g->partials, g->partials_stride, g->counters));
   } else {
@@ -705,7 +720,7 @@ static void launch_residual_v4(const Plan& P, cudaStream_t st, const float* nh, 
                                int zi, const ResidInit& ri) {
   thermal_grid* g = P.g;
   const TP* const* pt = (const TP* const*)g->dev_ptrs;
-#define TH_RES4(ZI)                                                                                              k_residual_df_v4<TP, ZI><<<P.gb4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo, pt, nh, nl,                                                     g->r32, count_outer, ri, g->partials, g->partials_stride,                                                      g->counters)
+#define TH_RES4(ZI)                                                                                              k_residual_df_v4<TP, ZI><<<P.nbq4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo, pt, nh, nl,                                                     g->r32, count_outer, ri, g->partials, g->partials_stride,                                                      g->counters)
   switch (zi) {
     case 0: TH_RES4(0); break;
     case 1: TH_RES4(1); break;
@@ -1579,7 +1594,7 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
         break;
       case 3:
         if (P.v4) {
-          TH_UNI(uni, k_spmv_dot_v4<U><<<P.gb4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
+          TH_UNI(uni, k_spmv_dot_v4<U><<<P.nbs4, P.tb4, 0, s>>>(P.d, P.zc, g->ctl, g->f32.gx, g->f32.gy, g->f32.gz,
                                                               g->tab, V.zc[0], V.p[0], V.p[1], V.mu, g->partials,
                                                               g->partials_stride, g->counters));
           break;
