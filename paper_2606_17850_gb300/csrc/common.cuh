@@ -43,6 +43,10 @@ struct LayerTab {
   // double-float; faces on the domain boundary are 0.
   float gxl[TH_MAXL], gyl[TH_MAXL], gzl[TH_MAXL];
   float gxl_hi[TH_MAXL], gxl_lo[TH_MAXL], gyl_hi[TH_MAXL], gyl_lo[TH_MAXL], gzl_hi[TH_MAXL], gzl_lo[TH_MAXL];
+  // layer-uniform grids: the FP32 inverse diagonal for each in-plane boundary case,
+  // index (x faces present) + 3 (y faces present); copied on the device from the
+  // per-cell array, so both are bit-identical
+  float invd9[9][TH_MAXL];
 };
 
 // Control block of one solve, in device memory.  Fields written by the last

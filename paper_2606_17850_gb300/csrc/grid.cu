@@ -159,6 +159,19 @@ __global__ void k_setup_diag(Dims d, Faces64 f, const LayerTab* tab, float* invd
   isqd32[c.i] = (float)(1.0 / sqrt(a));
 }
 
+// Per-layer table of the inverse diagonal by in-plane boundary case, read from the
+// per-cell array at one cell of each case that occurs (layer-uniform grids only).
+__global__ void k_setup_invd9(Dims d, const float* __restrict__ invd32, LayerTab* tab) {
+  const int c = threadIdx.x, z = blockIdx.x;  // c = nxf + 3 nyf
+  if (c >= 9 || z >= d.L) return;
+  const int nxf = c % 3, nyf = c / 3;
+  // a column with nxf x faces: interior (2), an end (1), or the only one (0)
+  const int x = nxf == 2 ? 1 : 0, y = nyf == 2 ? 1 : 0;
+  const bool occurs = (nxf == 2 ? d.nx >= 3 : (nxf == 1 ? d.nx >= 2 : d.nx == 1)) &&
+                      (nyf == 2 ? d.ny >= 3 : (nyf == 1 ? d.ny >= 2 : d.ny == 1));
+  tab->invd9[c][z] = occurs ? invd32[x + (long long)d.nx * y + d.pxy * z] : 0.f;
+}
+
 // largest main diagonal entry (positive doubles order like their bit patterns)
 __global__ void k_diag_max(Dims d, Faces64 f, const LayerTab* tab, unsigned long long* out) {
   const Cell c = cell_of(d);
@@ -359,6 +372,10 @@ th_status grid_ensure_tab(thermal_grid* g, double dt, cudaStream_t s) {
   k_setup_diag<<<grid_blocks(g), dim3(TH_BX, TH_BY), 0, s>>>(grid_dims(g), g->f64, g->tab, g->invd32,
                                                               g->invd64, g->isqd32);
   TH_CHECK_LAUNCH();
+  if (g->uniform) {
+    k_setup_invd9<<<g->L, 32, 0, s>>>(grid_dims(g), g->invd32, g->tab);
+    TH_CHECK_LAUNCH();
+  }
   TH_CUDA(cudaStreamSynchronize(s));
   g->tab_dt = key;
   g->tab_valid = true;

@@ -448,9 +448,11 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
   TV* xw = (INIT && !zero_x) ? nullptr : x;
   if constexpr (sizeof(TV) == 4) {
     if (P.v4) {
-#define TH_UPD4(ZM)                                                                                          \
-  k_update_v4<INIT, ZM><<<P.nbr4, 256, 0, st>>>(P.d.n / 4, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], zs, P.scaled, \
-                                                rz1, scale_r, g->partials, g->partials_stride, g->counters)
+#define TH_UPD4(ZM)                                                                                        \
+  TH_UNI(P.uni && P.d.n < (1LL << 33),                                                                     \
+         k_update_v4<INIT, ZM, U><<<P.nbr4, 256, 0, st>>>(P.d.n / 4, ctl, xw, pp, V.r, V.mu, V.invd, V.zc[0], \
+                                                          zs, P.scaled, rz1, scale_r, g->partials,          \
+                                                          g->partials_stride, g->counters, P.d, g->tab))
       switch (P.pc) {
         case TH_PC_NONE: TH_UPD4(0); break;
         case TH_PC_JACOBI: TH_UPD4(1); break;
@@ -1605,8 +1607,9 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
         break;
       case 4:
         if (P.v4) {
-          k_update_v4<false, 1><<<P.nbr4, 256, 0, s>>>(P.d.n / 4, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0],
-                                                      1.0f, 1, 1, 0, g->partials, g->partials_stride, g->counters);
+          TH_UNI(uni, k_update_v4<false, 1, U><<<P.nbr4, 256, 0, s>>>(P.d.n / 4, g->ctl, V.x, V.p[1], V.r, V.mu,
+                                                                     V.invd, V.zc[0], 1.0f, 1, 1, 0, g->partials,
+                                                                     g->partials_stride, g->counters, P.d, g->tab));
           break;
         }
         k_update<float, false, 1><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, V.x, V.p[1], V.r, V.mu, V.invd, V.zc[0], 1.0f,
