@@ -322,7 +322,6 @@ __device__ __forceinline__ void ldp4(const double* p, df (&o)[4]) {
 // unless the system has converged, and the correction is applied with scale 1.
 struct ResidInit {
   float* x;
-  const float* invd;
   float* z;
   float zs;
   int scaled, rz_here;
@@ -401,9 +400,13 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
       if (ZI >= 0) {
         st4(ri.x + i, z4());
         float zz[4] = {o[0], o[1], o[2], o[3]};
-        if (ZI == 1 || (ZI == 2 && ri.scaled)) {
-          const float4 iv = __ldg(reinterpret_cast<const float4*>(ri.invd + i));
-          zz[0] *= iv.x; zz[1] *= iv.y; zz[2] *= iv.z; zz[3] *= iv.w;
+        if (ZI == 1 || (ZI == 2 && ri.scaled)) {  // inverse diagonal from the boundary-case table
+          const int nyf = 3 * ((int)hasU + (int)hasD);
+          const float mid = __ldg(&tab->invd9[2 + nyf][z]), end = __ldg(&tab->invd9[1 + nyf][z]);
+          zz[0] *= hasL ? mid : end;
+          zz[1] *= mid;
+          zz[2] *= mid;
+          zz[3] *= hasR ? mid : end;
         }
         if (ZI == 2) {
 #pragma unroll

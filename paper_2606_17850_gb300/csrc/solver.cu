@@ -744,7 +744,6 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
       if (P.fused_init) {
         zi = (P.pc == TH_PC_NONE) ? 0 : (P.pc == TH_PC_JACOBI ? 1 : 2);
         ri.x = g->d32;
-        ri.invd = g->invd32;
         ri.z = g->zc32[0];
         ri.zs = (float)P.inv_theta;
         ri.scaled = P.scaled;
