@@ -46,6 +46,7 @@
 template <int LMAX>
 struct TBParams {
   float c1[TB_H], c2[TB_H];     // Chebyshev step coefficients of this chunk
+  float z1s;                    // first chunk: z_1 = z1s D^-1 r, formed from the staged r
   float d[LMAX];                // diagonal of a cell with all four in-plane faces
   float gx[LMAX], gy[LMAX];     // in-plane face conductances per layer
   float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
@@ -109,7 +110,10 @@ constexpr size_t tb_smem_bytes() {
 // (EY - 2 STEPS) columns.  Layers L..LMAX-1 (when the stack has fewer than LMAX
 // layers) are carried as zeros: their coefficients and inverse diagonal are 0, so
 // they stay 0 and the step loop needs no per-layer guard.
-template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST>
+//
+// FIRST: the chunk starts the polynomial: z_1 = z1s D^-1 r and z_0 = 0 are formed from
+// the staged r, so only the r box is staged and z_1 is never stored.
+template <int LMAX, int EY, int STEPS, bool SCALED, bool LAST, bool FIRST>
 __global__ void __launch_bounds__(TB_EX * EY, 1)
     k_cheb_tb(Dims d, int ntx, int ntiles, int has_prev, Ctl* ctl,
               const __grid_constant__ CUtensorMap m_cur, const __grid_constant__ CUtensorMap m_prev,
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   const int ex = threadIdx.x, ey = threadIdx.y;
   const int tid = ex + TB_EX * ey;
   const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
-  const unsigned tx_bytes = box_bytes * (has_prev ? 3u : 2u);
+  const unsigned tx_bytes = box_bytes * (FIRST ? 1u : (has_prev ? 3u : 2u));
 
   // Layers L..LMAX-1 of the three boxes, and the whole z_{m-1} box when there is
   // none, are never written by the tensor copies: zero them once, so the staged
@@ -148,8 +152,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   auto issue = [&](int tx, int ty) {
     const int xa = (tx * TX - H) & ~3, y0 = ty * TY - H;
     tb_mbar_expect(bar, tx_bytes);
-    tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
-    if (has_prev) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+    if (!FIRST) tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
+    if (has_prev && !FIRST) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
     tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
   };
   // tile t = tx + ntx ty, advanced by gridDim.x without a division per tile
@@ -191,11 +195,16 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
-      za[z] = stage[z * SL + st];
-      zb[z] = stage[(LMAX + z) * SL + st];
       rr[z] = stage[(2 * LMAX + z) * SL + st];
       inv[z] = P.invd[nxf + 3 * nyf][z];
       rs[z] = (SCALED && !LAST) ? rr[z] * inv[z] : rr[z];  // D^-1 r, fixed over the chunk
+      if (FIRST) {
+        za[z] = (SCALED ? rr[z] * inv[z] : rr[z]) * P.z1s;
+        zb[z] = 0.f;
+      } else {
+        za[z] = stage[z * SL + st];
+        zb[z] = stage[(LMAX + z) * SL + st];
+      }
     }
     __syncthreads();  // staging buffer consumed by every thread
     const int tn = t + gridDim.x;

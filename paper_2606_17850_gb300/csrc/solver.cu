@@ -456,7 +456,10 @@ static th_status enq_update(const Plan& P, const VecSet<TV>& V, cudaStream_t st,
       switch (P.pc) {
         case TH_PC_NONE: TH_UPD4(0); break;
         case TH_PC_JACOBI: TH_UPD4(1); break;
-        case TH_PC_CHEB: TH_UPD4(2); break;
+        case TH_PC_CHEB:  // fused chunks form z_1 in their first chunk: no z written here
+          if (P.fused) TH_UPD4(0);
+          else TH_UPD4(2);
+          break;
         default: TH_UPD4(3); break;
       }
 #undef TH_UPD4
@@ -527,7 +530,7 @@ static int sm_count() {
   return n[dev];
 }
 
-template <int LM, int EY, int ST, bool SC, bool LA>
+template <int LM, int EY, int ST, bool SC, bool LA, bool FI>
 static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   thermal_grid* g = P.g;
   constexpr int TX = TB_EX - 2 * ST, TY = EY - 2 * ST;
@@ -538,6 +541,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
     prm.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
     prm.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
   }
+  prm.z1s = (float)P.inv_theta;
   const LayerTab& T = g->tab_host;
   const int L = P.d.L;
   for (int z = 0; z < L; ++z) {
@@ -567,32 +571,38 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   const int ntx = (P.d.nx + TX - 1) / TX;
   const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
   const size_t smem = tb_smem_bytes<LM, EY>();
-  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, EY, ST, SC, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TH_CUDA(cudaFuncSetAttribute(k_cheb_tb<LM, EY, ST, SC, LA, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
   const int nblk = std::min(ntiles, sm_count());
   if (nblk > g->partials_stride) return th_fail(TH_ESTATE, "partials buffer smaller than the temporal-blocking grid");
-  k_cheb_tb<LM, EY, ST, SC, LA><<<nblk, dim3(TB_EX, EY), smem, st>>>(
+  k_cheb_tb<LM, EY, ST, SC, LA, FI><<<nblk, dim3(TB_EX, EY), smem, st>>>(
       P.d, ntx, ntiles, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, pool[c.out_cur],
       c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
 
-// chunk dispatch on (steps, last chunk)
-template <int LM, int EY, bool SC, bool LA>
+// chunk dispatch on (steps, last chunk, first chunk)
+template <int LM, int EY, bool SC, bool LA, bool FI>
 static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
   switch (c.steps) {
-    case 1: return tb_launch<LM, EY, 1, SC, LA>(P, V, st, c);
-    case 2: return tb_launch<LM, EY, 2, SC, LA>(P, V, st, c);
-    case 3: return tb_launch<LM, EY, 3, SC, LA>(P, V, st, c);
-    case 4: return tb_launch<LM, EY, 4, SC, LA>(P, V, st, c);
+    case 1: return tb_launch<LM, EY, 1, SC, LA, FI>(P, V, st, c);
+    case 2: return tb_launch<LM, EY, 2, SC, LA, FI>(P, V, st, c);
+    case 3: return tb_launch<LM, EY, 3, SC, LA, FI>(P, V, st, c);
+    case 4: return tb_launch<LM, EY, 4, SC, LA, FI>(P, V, st, c);
     default: return th_fail(TH_ESTATE, "temporal-blocking chunk with %d steps", c.steps);
   }
 }
 
+// The first chunk of the polynomial (m0 = 1, no z_0 input) forms z_1 = D^-1 r / theta
+// itself from the staged r.
+static bool tb_first(const Plan::Chunk& c) { return c.m0 == 1 && c.in_prev < 0; }
+
 template <int LM, int EY>
 static th_status tb_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last) {
-  return last ? tb_steps<LM, EY, true, true>(P, V, st, c) : tb_steps<LM, EY, true, false>(P, V, st, c);
+  if (tb_first(c))
+    return last ? tb_steps<LM, EY, true, true, true>(P, V, st, c) : tb_steps<LM, EY, true, false, true>(P, V, st, c);
+  return last ? tb_steps<LM, EY, true, true, false>(P, V, st, c) : tb_steps<LM, EY, true, false, false>(P, V, st, c);
 }
 
 static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st) {
@@ -742,7 +752,8 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
       ResidInit ri{};
       int zi = -1;
       if (P.fused_init) {
-        zi = (P.pc == TH_PC_NONE) ? 0 : (P.pc == TH_PC_JACOBI ? 1 : 2);
+        // with fused Chebyshev chunks the first chunk forms z_1 itself (no z written)
+        zi = (P.pc == TH_PC_NONE || P.fused) ? 0 : (P.pc == TH_PC_JACOBI ? 1 : 2);
         ri.x = g->d32;
         ri.z = g->zc32[0];
         ri.zs = (float)P.inv_theta;
