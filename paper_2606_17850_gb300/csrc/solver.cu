@@ -732,7 +732,10 @@ static void launch_residual_v4(const Plan& P, cudaStream_t st, const float* nh, 
                                int zi, const ResidInit& ri) {
   thermal_grid* g = P.g;
   const TP* const* pt = (const TP* const*)g->dev_ptrs;
-#define TH_RES4(ZI)                                                                                              k_residual_df_v4<TP, ZI><<<P.nbq4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo, pt, nh, nl,                                                     g->r32, count_outer, ri, g->partials, g->partials_stride,                                                      g->counters)
+#define TH_RES4(ZI)                                                                                   \
+  k_residual_df_v4<TP, ZI><<<P.nbq4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo, pt, \
+                                                    nh, nl, g->r32, count_outer, ri, g->partials,      \
+                                                    g->partials_stride, g->counters)
   switch (zi) {
     case 0: TH_RES4(0); break;
     case 1: TH_RES4(1); break;
