@@ -46,11 +46,11 @@
 template <int LMAX>
 struct TBParams {
   float c1[TB_H], c2[TB_H];     // Chebyshev step coefficients of this chunk
-  float z1s;                    // first chunk: z_1 = z1s D^-1 r, formed from the staged r
   float d[LMAX];                // diagonal of a cell with all four in-plane faces
   float gx[LMAX], gy[LMAX];     // in-plane face conductances per layer
   float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
+  float z1s;                    // first chunk: z_1 = z1s D^-1 r, formed from the staged r
 };
 
 __device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -195,15 +195,16 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
+      if (!FIRST) {
+        za[z] = stage[z * SL + st];
+        zb[z] = stage[(LMAX + z) * SL + st];
+      }
       rr[z] = stage[(2 * LMAX + z) * SL + st];
       inv[z] = P.invd[nxf + 3 * nyf][z];
       rs[z] = (SCALED && !LAST) ? rr[z] * inv[z] : rr[z];  // D^-1 r, fixed over the chunk
       if (FIRST) {
         za[z] = (SCALED ? rr[z] * inv[z] : rr[z]) * P.z1s;
         zb[z] = 0.f;
-      } else {
-        za[z] = stage[z * SL + st];
-        zb[z] = stage[(LMAX + z) * SL + st];
       }
     }
     __syncthreads();  // staging buffer consumed by every thread
