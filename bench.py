@@ -46,7 +46,7 @@ KERNEL_BYTES = {
     "cheb_tb3": 20,      # three fused steps, same traffic per launch
     "cheb_tb2": 20,      # two fused steps, same traffic per launch
     "spmv_dot_f32": 16,  # z, p_old (8) + p_new, mu (8)
-    "update_f32": 32,    # x, r (read+write 16) + p, mu, 1/diag (12) + z (4)
+    "update_f32": 28,    # x, r (read+write 16) + p, mu (8) + z (4); 1/diag from the per-layer table
     "stencil_f32": 8,    # x (4) + y (4)
     "residual_df": 24,   # theta, theta_n as hi+lo (16) + P f32 (4) + r f32 (4)
     # the same kernels reading per-face arrays (grids with a per-cell conductivity map)
