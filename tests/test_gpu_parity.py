@@ -711,3 +711,29 @@ def test_empty_runs():
     g.run_transient([cuda(inst.power)], 1, 0, 1e-4, T)
     assert torch.equal(T, T0)
     assert solve_batched([], [], []) == []
+
+
+@pytest.mark.parametrize("guess", [1, 2])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_run_transient_conductivity_map(guess, graph):
+    """Per-cell conductivities (per-face kernels, no layer table) with the
+    extrapolated guess, against backward-Euler steps assembled by the oracle."""
+    st = ti.stack_c2()
+    nx, ny, dt = 36, 21, 1e-4
+    kc = _kmap(st, nx, ny, 12)
+    maps = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s + j) for j in (0, 1)], np.float64)
+            for s in (70, 72)]
+    n_steps, spm = 6, 2
+    g = grid_of(nx, ny, st)
+    g.set_conductivity_map(cuda(kc))
+    T0 = np.full(nx * ny * st.L, st.t_amb)
+    T = cuda(T0.copy())
+    T, stats = g.run_transient([cuda(m) for m in maps], spm, n_steps, dt, T, tol_rel=1e-10, cheb_degree=8,
+                               use_graph=graph, guess=guess)
+    assert stats["status"] == 0 and stats["steps"] == n_steps
+    A = disc.assemble(nx, ny, st, dt=dt, k_cell=kc)
+    solve = osolve.Factorised(A)
+    ref = T0
+    for s in range(n_steps):
+        ref = solve(disc.rhs_transient(nx, ny, st, maps[(s // spm) % 2], ref, dt))
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
