@@ -361,11 +361,13 @@ def main():
                         "status": stats["status"], "first_call_ms (setup+graph build+solve)": t_setup}
     k = args.degree
     # kernel launches per trajectory from the solver's counters (graph mode): a
-    # Chebyshev application is ceil((k-1)/4) fused launches on this layer-uniform grid
+    # Chebyshev application is ceil((k-1)/4) fused launches on this layer-uniform grid;
+    # an outer iteration adds the preconditioner, the correction, the residual (which
+    # also starts the next inner solve) and the loop conditions
     fuse = args.fuse or 4
     cheb = -(-(k - 1) // fuse)
     pairs = (stats["inner_it"] + stats["outer_it"]) // 2 + stats["outer_it"]
-    launches = (3 + nsteps * 6 + stats["outer_it"] * (cheb + 5) + pairs * (2 * (cheb + 2) + 1) + 1) * args.steps
+    launches = (3 + nsteps * 6 + stats["outer_it"] * (cheb + 4) + pairs * (2 * (cheb + 2) + 1) + 1) * args.steps
     result["gpu_launches"] = int(launches)
     result["clocks"] = clk.summary()
 
