@@ -737,3 +737,25 @@ def test_run_transient_conductivity_map(guess, graph):
     for s in range(n_steps):
         ref = solve(disc.rhs_transient(nx, ny, st, maps[(s // spm) % 2], ref, dt))
     assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+@pytest.mark.parametrize("scaled,fuse,k", [(1, 1, 8), (0, 0, 8), (1, 4, 8), (1, 0, 1), (1, 0, 2)])
+def test_mixed_solve_chebyshev_variants(scaled, fuse, k):
+    """The residual kernel starts each inner solve itself on layer-table grids: with
+    the stepwise polynomial (fuse 1), the unscaled one, fused chunks (z_1 formed in
+    the first chunk), degree 1 (the start supplies r^T z) and degree 2 (one fused
+    chunk that is first and last at once), steady and transient, against the oracle."""
+    st = ti.stack_c2()
+    nx, ny, dt = 40, 26, 1e-4
+    P = ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s) for s in (80, 81)], np.float64)
+    g = grid_of(nx, ny, st)
+    o = dict(precision="mixed", precond="cheb", cheb_degree=k, cheb_scaled=scaled, cheb_fuse=fuse, tol_rel=1e-10)
+    T, stats = g.solve_steady(cuda(P), **o)
+    assert stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), osolve.steady(nx, ny, st, P), st.t_amb) <= 1e-6
+    T0 = np.full(nx * ny * st.L, st.t_amb)
+    T = cuda(T0.copy())
+    T, stats = g.run_transient([cuda(P)], 1, 4, dt, T, guess=2, **o)
+    assert stats["status"] == 0
+    ref = osolve.transient(nx, ny, st, [P] * 4, dt, T0)[-1]
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
