@@ -274,8 +274,9 @@ struct MGRow4 {
   }
 };
 
+template <int LMAX>
 __global__ void __launch_bounds__(256, 2) k_mg_smooth4(const Ctl* ctl, int nx, int ny, int L,
-                                                       const __grid_constant__ MGUni<8> U,
+                                                       const __grid_constant__ MGUni<LMAX> U,
                                                        const float* __restrict__ b, const float* __restrict__ xin,
                                                        const float* __restrict__ xc, int nxc, int nyc,
                                                        float* __restrict__ xout, float omega) {
@@ -289,12 +290,12 @@ __global__ void __launch_bounds__(256, 2) k_mg_smooth4(const Ctl* ctl, int nx, i
   const int nyf = (int)hasU + (int)hasD;
   // boundary case of each of the 4 columns (only the outer two can miss an x neighbour)
   const int cs0 = (1 + (int)hasL) + 3 * nyf, cs3 = (1 + (int)hasR) + 3 * nyf, csm = 2 + 3 * nyf;
-  float xv[4][8], dp[4][8];
+  float xv[4][LMAX], dp[4][LMAX];
   float4 xb = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 xcur = X.row(x0, y, 0);
   float dprev[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int z = 0; z < 8; ++z) {
+  for (int z = 0; z < LMAX; ++z) {
     if (z >= L) break;
     const long long i = (long long)x0 + (long long)nx * y + pxy * z;
     const float4 xa = (xin && z + 1 < L) ? X.row(x0, y, z + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(256, 2) k_mg_smooth4(const Ctl* ctl, int nx, i
   }
   float dn[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int zz = 7; zz >= 0; --zz) {
+  for (int zz = LMAX - 1; zz >= 0; --zz) {
     if (zz >= L) continue;
     float o[4];
 #pragma unroll
@@ -350,8 +351,9 @@ __global__ void __launch_bounds__(256, 2) k_mg_smooth4(const Ctl* ctl, int nx, i
 
 // b_c = P^T (b - A x) on the vectorised finest level: 4 fine columns give 2 aggregate
 // partial sums per layer; the y pair is summed through shared memory.  Block (32, 8).
+template <int LMAX>
 __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, int ny, int L,
-                                                      const __grid_constant__ MGUni<8> U,
+                                                      const __grid_constant__ MGUni<LMAX> U,
                                                       const float* __restrict__ b, const float* __restrict__ x,
                                                       int nxc, int nyc, float* __restrict__ bc) {
   if (ld_int(&ctl->done)) return;
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, in
   const long long pxy = (long long)nx * ny;
   const bool hasL = x0 > 0, hasR = x0 + 4 < nx, hasD = y > 0, hasU = y + 1 < ny;
 #pragma unroll
-  for (int z = 0; z < 8; ++z) {
+  for (int z = 0; z < LMAX; ++z) {
     if (z >= L) break;
     float2 r2 = make_float2(0.f, 0.f);
     if (in) {
@@ -649,8 +651,9 @@ static MGUni<LMAX> uni_of(const MGHier* h) {
   return u;
 }
 
-// the vectorised finest-level kernels apply (layer table, nx % 4 == 0, <= 8 layers)
-static bool mg_v4(const thermal_grid* g, int k) { return k == 0 && g->mg->uni && g->nx % 4 == 0 && g->L <= 8; }
+// the vectorised finest-level kernels apply (layer table, nx % 4 == 0, <= 12 layers:
+// 4 columns x 12 layers of the iterate and the forward sweep fit the registers)
+static bool mg_v4(const thermal_grid* g, int k) { return k == 0 && g->mg->uni && g->nx % 4 == 0 && g->L <= 12; }
 
 template <int LMAX>
 static th_status smooth(thermal_grid* g, int k, const float* b, const float* xin, const float* xc, int nxc, int nyc,
@@ -658,9 +661,9 @@ static th_status smooth(thermal_grid* g, int k, const float* b, const float* xin
   const MGHier* h = g->mg;
   const MGLevelH& l = h->lv[k];
   const MGUni<LMAX> U = uni_of<LMAX>(h);
-  if constexpr (LMAX == 8) {
+  if constexpr (LMAX == 8 || LMAX == 12) {
     if (mg_v4(g, k)) {
-      k_mg_smooth4<<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U, b,
+      k_mg_smooth4<LMAX><<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U, b,
                                                                                      xin, xc, nxc, nyc, xout,
                                                                                      MG_OMEGA);
       TH_CHECK_LAUNCH();
@@ -683,9 +686,9 @@ static th_status restrict_(thermal_grid* g, int k, const float* b, const float* 
   const MGLevelH& l = h->lv[k];
   const MGLevelH& c = h->lv[k + 1];
   const MGUni<LMAX> U = uni_of<LMAX>(h);
-  if constexpr (LMAX == 8) {
+  if constexpr (LMAX == 8 || LMAX == 12) {
     if (mg_v4(g, k)) {
-      k_mg_restrict4<<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U,
+      k_mg_restrict4<LMAX><<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U,
                                                                                        b, x, c.nx, c.ny, bc);
       TH_CHECK_LAUNCH();
       return TH_OK;
@@ -704,12 +707,14 @@ static th_status restrict_(thermal_grid* g, int k, const float* b, const float* 
 static th_status smooth_any(thermal_grid* g, int k, const float* b, const float* xin, const float* xc, int nxc,
                             int nyc, float* xout, cudaStream_t s) {
   if (g->L <= 8) return smooth<8>(g, k, b, xin, xc, nxc, nyc, xout, s);
+  if (g->L <= 12) return smooth<12>(g, k, b, xin, xc, nxc, nyc, xout, s);
   if (g->L <= 16) return smooth<16>(g, k, b, xin, xc, nxc, nyc, xout, s);
   return smooth<32>(g, k, b, xin, xc, nxc, nyc, xout, s);
 }
 
 static th_status restrict_any(thermal_grid* g, int k, const float* b, const float* x, float* bc, cudaStream_t s) {
   if (g->L <= 8) return restrict_<8>(g, k, b, x, bc, s);
+  if (g->L <= 12) return restrict_<12>(g, k, b, x, bc, s);
   if (g->L <= 16) return restrict_<16>(g, k, b, x, bc, s);
   return restrict_<32>(g, k, b, x, bc, s);
 }

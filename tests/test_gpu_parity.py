@@ -391,7 +391,8 @@ def test_run_transient_long_schedule(prec):
 # ----------------------------------------------------- geometric multigrid (not in the paper)
 
 @pytest.mark.parametrize("nx,ny,mk,dt", [(37, 21, "c2", 1e-4), (37, 21, "c2", 0.0), (9, 30, "mol", 0.0),
-                                         (3, 2, "c1", 0.0), (64, 64, "c1", 1e-4)])
+                                         (3, 2, "c1", 0.0), (64, 64, "c1", 1e-4), (36, 30, "mol", 0.0),
+                                         (68, 22, "mol", 1e-4)])
 def test_mg_vcycle_matches_oracle(nx, ny, mk, dt):
     """One V-cycle (aggregation semi-coarsening, damped z-line Jacobi, exact coarsest
     solve) in FP32 on the GPU against the oracle's FP64 V-cycle, on odd sizes, a
