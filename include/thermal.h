@@ -82,7 +82,8 @@ typedef enum th_dtype { TH_F32 = 0, TH_F64 = 1 } th_dtype;
 typedef struct thermal_grid thermal_grid;
 
 typedef struct thermal_solve_opts {
-  double tol_rel;      /* stop when ||b - A theta||_2 <= tol_rel * ||b||_2 in FP64 (1e-8)      */
+  double tol_rel;      /* stop when ||b - A theta||_2 <= tol_rel * ||b||_2 in FP64 (1e-8); the  */
+                       /* mixed paths resolve it down to about 1e-10 (double-float residual) */
   double inner_tol;    /* MIXED_IR: each FP32 inner solve reduces its residual by this (1e-4)   */
   int max_outer;       /* MIXED_IR: refinement steps (30)                                      */
   int max_inner;       /* MIXED_IR: PCG iterations per inner solve (5000)                       */
