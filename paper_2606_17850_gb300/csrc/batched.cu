@@ -453,7 +453,7 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
     if (opts->precond == TH_PC_CHEB)
       TH_TRY(solver_cheb_coeffs(g, 0.0, opts, c1s[i], c2s[i], &inv_theta, &lmins[i], &lmaxs[i], s));
     BInst& I = hi[i];
-    std::memset(&I, 0, sizeof(I));
+    I = BInst{};
     I.d = grid_dims(g);
     I.tbx = (g->nx + 4 * TH_BX - 1) / (4 * TH_BX);
     I.tile0 = ntiles;
