@@ -106,7 +106,11 @@ typedef struct thermal_solve_opts {
   int ad_check;        /* ADAPTIVE: PCG iterations between true-residual evaluations of the   */
                        /* switching criterion, rounded up to even; 0: 20 steady, 6 transient  */
                        /* (the paper's 20 and 5 on the two-iteration loop body) (0)           */
-  int reserved[4];
+  int test_wait_expire; /* test hook, 0 in normal use: 1 makes every CTA of the fused        */
+                       /* Chebyshev kernel first wait on a barrier phase that nothing        */
+                       /* completes, so its bounded wait runs out after 2 ms and the solve   */
+                       /* ends with TH_ECUDA ("device wait timed out"); the grid stays usable */
+  int reserved[3];
 } thermal_solve_opts;
 
 typedef struct thermal_solve_stats {
@@ -343,6 +347,10 @@ th_status thermal_grad(thermal_grid* g, const double* T, const double* dJdT, voi
  * keep iterating.  stats[i] (host array of n) receives each instance's result; the
  * return value is the first non-OK instance status, or TH_OK.  n = 0 is a no-op
  * (the arrays may then be NULL); an instance with h = 0 is TH_EINVAL (G singular).
+ * Every instance iterates in its grid's work vectors: each needs a grid handle and a
+ * T buffer of its own (a handle or a T pointer that appears twice is TH_EINVAL; to
+ * solve several power maps on one geometry, create one grid per map).  The power
+ * maps may be shared.
  */
 th_status thermal_solve_batched(thermal_grid* const* grids, int n, const void* const* power,
                                 int power_dtype, double* const* T, const thermal_solve_opts* opts,
@@ -363,14 +371,18 @@ th_status thermal_solve_batched(thermal_grid* const* grids, int n, const void* c
  * s_layer: host array of `layers` floats, the per-layer diagonal term (h dx dy on the
  *   top layer plus c dx dy dz / dt in a transient step).
  * x (device, n_cells floats) in; y (device, n_cells floats) and *xAx (device, one
- *   double) out.  The stencil row and its FP32 arithmetic are those of thermal_apply.
+ *   double) out.  x and y must not overlap (TH_EINVAL when their ranges share an
+ *   element).  The stencil row and its FP32 arithmetic are those of thermal_apply.
  * Scratch: the per-block partial sums and a completion counter live in one static
  *   device array of 65536 doubles (+256 B), which every GPU that loads the library
  *   holds until the process exits.  Grids needing more than 65536 thread blocks
  *   (ceil(nx/32) * ceil(ny/8) * layers) are rejected with TH_EINVAL.
  * The first call on a device looks up that array's device address
- *   (cudaGetSymbolAddress) with the device current; make that first call before any
- *   stream capture.  Every call zeroes the counter on `stream` (cudaMemsetAsync).
+ *   (cudaGetSymbolAddress) with the device current.  Under lazy module loading (the
+ *   default of CUDA 12 and later) that first call is also when the library's module
+ *   is loaded on the device and the 512 KiB array takes its device memory, so a
+ *   caller held to a memory budget fixed at start-up should make the first call at
+ *   start-up, and in any case before any stream capture.  Every call zeroes the counter on `stream` (cudaMemsetAsync).
  *   All calls on one device share that device's array, which keeps the last call's
  *   contents: calls that may overlap on the GPU (e.g. on two streams of the same
  *   device) race and must be ordered by the caller.

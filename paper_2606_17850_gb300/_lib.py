@@ -37,7 +37,8 @@ class SolveOpts(C.Structure):
         ("guess", C.c_int),
         ("cheb_fuse", C.c_int),
         ("ad_check", C.c_int),
-        ("reserved", C.c_int * 4),
+        ("test_wait_expire", C.c_int),
+        ("reserved", C.c_int * 3),
     ]
 
 

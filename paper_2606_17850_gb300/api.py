@@ -27,6 +27,42 @@ def _ptr(t: Optional[torch.Tensor]):
     return C.c_void_p(t.data_ptr())
 
 
+F32, F64, F32_OR_F64 = (torch.float32,), (torch.float64,), (torch.float32, torch.float64)
+
+
+def _check(t, n: int, dtypes, name: str, device_only: bool = False) -> torch.Tensor:
+    """Validates a buffer before its pointer crosses the C ABI: a tensor of one of
+    ``dtypes`` with exactly ``n`` elements, contiguous, on a CUDA device (or on the
+    host where the call accepts host memory).  The library trusts sizes and dtypes,
+    so a short or mistyped buffer would be read or written past its end."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor, got {type(t).__name__}")
+    if t.dtype not in dtypes:
+        want = " or ".join(str(d).replace("torch.", "") for d in dtypes)
+        raise TypeError(f"{name} must be {want}, got {str(t.dtype).replace('torch.', '')}")
+    if t.numel() != n:
+        raise ValueError(f"{name} must hold {n} elements (one per cell), got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device.type not in ("cuda", "cpu") or (device_only and t.device.type != "cuda"):
+        where = "a CUDA device" if device_only else "a CUDA device or the host"
+        raise ValueError(f"{name} must live on {where}, got {t.device}")
+    return t
+
+
+def _check_maps(maps, n: int, name: str = "power maps", device_only: bool = False):
+    """A non-empty list of power maps of one dtype (float32 or float64) in one memory space."""
+    if not isinstance(maps, (list, tuple)) or not maps:
+        raise ValueError(f"{name} must be a non-empty list of tensors")
+    for i, m in enumerate(maps):
+        _check(m, n, F32_OR_F64, f"{name}[{i}]", device_only)
+    if len({m.dtype for m in maps}) != 1:
+        raise TypeError(f"all {name} must share one dtype")
+    if len({m.device.type for m in maps}) != 1:
+        raise ValueError(f"all {name} must be in the same memory space")
+    return maps
+
+
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -86,11 +122,13 @@ class ThermalGrid:
             pass
 
     def set_conductivity(self, k: Sequence[float]):
+        if len(k) != self.L:
+            raise ValueError(f"set_conductivity needs {self.L} values (one per layer), got {len(k)}")
         L.check(L.load().thermal_grid_set_conductivity(self._h, _darr(k)))
 
     def set_conductivity_map(self, k_cell: torch.Tensor):
         """Per-cell conductivities (float64, host or device, n values)."""
-        k_cell = k_cell.contiguous().to(torch.float64)
+        k_cell = _check(k_cell.contiguous().to(torch.float64), self.n, F64, "k_cell")
         L.check(L.load().thermal_grid_set_conductivity_map(self._h, _ptr(k_cell)))
 
     # ------------------------------------------------------------------ kernels
@@ -102,11 +140,13 @@ class ThermalGrid:
         return out
 
     def apply(self, x: torch.Tensor, dt=0.0, precision="fp64"):
+        _check(x, self.n, F64 if precision == "fp64" else F32, "x", device_only=True)
         y = torch.empty_like(x)
         L.check(L.load().thermal_apply(self._h, float(dt), PRECISION[precision], _ptr(x), _ptr(y), _stream()))
         return y
 
     def precond(self, r: torch.Tensor, dt=0.0, **opts):
+        _check(r, self.n, F32, "r", device_only=True)
         z = torch.empty_like(r)
         o = make_opts(**opts)
         L.check(L.load().thermal_precond_apply(self._h, float(dt), C.byref(o), _ptr(r), _ptr(z), _stream()))
@@ -137,6 +177,7 @@ class ThermalGrid:
         """y = A x through a CSR copy of the matrix (Sec. 5.5 comparison).  x float32 or
         float64 on the device.  Returns (y, ms): ms is the mean launch time over reps
         timed launches, or None when reps == 0."""
+        _check(x, self.n, F32_OR_F64, "x", device_only=True)
         prec = "fp64" if x.dtype == torch.float64 else "mixed"
         y = torch.empty_like(x)
         ms = C.c_double()
@@ -149,8 +190,10 @@ class ThermalGrid:
 
     def solve_steady(self, power: torch.Tensor, T: Optional[torch.Tensor] = None, **opts):
         """Returns (T, stats).  T (float64, deg C) is allocated on power's device when not given."""
+        _check(power, self.n, F32_OR_F64, "power")
         if T is None:
             T = torch.empty(self.n, dtype=torch.float64, device=power.device)
+        _check(T, self.n, F64, "T")
         o = make_opts(**opts)
         st = L.SolveStats()
         L.check(L.load().thermal_solve_steady(self._h, _ptr(power), _dtype_code(power), _ptr(T), C.byref(o),
@@ -159,6 +202,8 @@ class ThermalGrid:
 
     def step_transient(self, power: torch.Tensor, dt: float, T: torch.Tensor, **opts):
         """One backward-Euler step in place on T (T_n -> T_{n+1})."""
+        _check(power, self.n, F32_OR_F64, "power")
+        _check(T, self.n, F64, "T")
         o = make_opts(**opts)
         st = L.SolveStats()
         L.check(L.load().thermal_step_transient(self._h, _ptr(power), _dtype_code(power), float(dt), _ptr(T),
@@ -168,6 +213,8 @@ class ThermalGrid:
     def run_transient(self, maps: List[torch.Tensor], steps_per_map: int, n_steps: int, dt: float,
                       T: torch.Tensor, **opts):
         """n_steps backward-Euler steps in place on T; step s uses maps[(s // steps_per_map) % len(maps)]."""
+        _check_maps(maps, self.n)
+        _check(T, self.n, F64, "T")
         o = make_opts(**opts)
         st = L.SolveStats()
         arr = (C.c_void_p * len(maps))(*[m.data_ptr() for m in maps])
@@ -179,6 +226,9 @@ class ThermalGrid:
     # ------------------------------------------------------------------ adjoint
 
     def hotspot_lse(self, T: torch.Tensor, layers: Sequence[int], beta: float, want_grad=True):
+        _check(T, self.n, F64, "T", device_only=True)
+        if not layers or any(not 0 <= int(l) < self.L for l in layers):
+            raise ValueError(f"layers must be a non-empty list of indices in [0, {self.L})")
         ids = (C.c_int * len(layers))(*[int(l) for l in layers])
         J = C.c_double()
         g = torch.empty_like(T) if want_grad else None
@@ -188,6 +238,10 @@ class ThermalGrid:
 
     def grad(self, T: torch.Tensor, dJdT: torch.Tensor, dJdP_dtype=torch.float32, want_k=True, **opts):
         """Adjoint gradient: (dJ/dP on the device, dJ/dk per layer as a list)."""
+        _check(T, self.n, F64, "T", device_only=True)
+        _check(dJdT, self.n, F64, "dJdT", device_only=True)
+        if dJdP_dtype not in F32_OR_F64:
+            raise TypeError("dJdP_dtype must be torch.float32 or torch.float64")
         dJdP = torch.empty(self.n, dtype=dJdP_dtype, device=T.device)
         dk = (C.c_double * self.L)() if want_k else None
         o = make_opts(**opts)
@@ -199,13 +253,22 @@ class ThermalGrid:
 
 def solve_batched(grids: List[ThermalGrid], powers: List[torch.Tensor], Ts: List[torch.Tensor], **opts):
     n = len(grids)
+    if not (len(powers) == len(Ts) == n):
+        raise ValueError("grids, powers and Ts must have the same length")
+    if len({id(g) for g in grids}) != n:
+        raise ValueError("each instance needs its own grid (the same grid appears twice)")
+    if len({id(t) for t in Ts}) != n:
+        raise ValueError("each instance needs its own output T (the same tensor appears twice)")
+    for i, (g, p, t) in enumerate(zip(grids, powers, Ts)):
+        _check(p, g.n, F32_OR_F64, f"powers[{i}]", device_only=True)
+        _check(t, g.n, F64, f"Ts[{i}]", device_only=True)
+    if n and len({p.dtype for p in powers}) != 1:
+        raise TypeError("all power maps of a batch must share one dtype")
     o = make_opts(**opts)
     stats = (L.SolveStats * n)()
     gh = (C.c_void_p * n)(*[g.handle.value for g in grids])
     ph = (C.c_void_p * n)(*[p.data_ptr() for p in powers])
     th = (C.c_void_p * n)(*[t.data_ptr() for t in Ts])
-    if not (len(powers) == len(Ts) == n):
-        raise ValueError("grids, powers and Ts must have the same length")
     pdt = _dtype_code(powers[0]) if n else L.TH_F64
     L.check(L.load().thermal_solve_batched(gh, n, ph, pdt, th, C.byref(o), stats, _stream()))
     return [s.as_dict() for s in stats]

@@ -583,6 +583,18 @@ extern "C" th_status thermal_solve_batched(thermal_grid* const* grids, int n, co
       all_dev = all_dev && is_device_pointer(power[i]) && is_device_pointer(T[i]);
       v4 = v4 && grids[i]->nx % 4 == 0 && ((uintptr_t)power[i] % 16) == 0;
     }
+    // every instance iterates in its grid's own work vectors and control block and
+    // writes its own T: a grid or an output passed twice would be shared by two
+    // instances of one launch, so both are rejected
+    {
+      std::vector<const void*> gs(grids, grids + n), ts(T, T + n);
+      std::sort(gs.begin(), gs.end());
+      std::sort(ts.begin(), ts.end());
+      if (std::adjacent_find(gs.begin(), gs.end()) != gs.end())
+        return th_fail(TH_EINVAL, "the same grid handle appears twice in the batch (one grid per instance)");
+      if (std::adjacent_find(ts.begin(), ts.end()) != ts.end())
+        return th_fail(TH_EINVAL, "the same output buffer T appears twice in the batch");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // the persistent kernel covers the mixed path with the Jacobi, Chebyshev and no
     // preconditioner on grids with nx % 4 == 0; other combinations run the instances

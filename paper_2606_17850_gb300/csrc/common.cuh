@@ -146,15 +146,19 @@ __device__ __forceinline__ void fin_update(Ctl* ctl, double rr, double rz, bool 
 }
 
 // last-block decision after p^T A p: alpha for the update, breakdown check.
+// A is SPD, so p^T A p <= 0 means breakdown; r^T z <= 0 (r != 0 here: a converged
+// inner solve ends before this kernel) means the preconditioner is not positive
+// definite on r, e.g. a Chebyshev interval whose upper end lies below lambda_max.
 __device__ __forceinline__ void fin_pap(Ctl* ctl, double pAp) {
   ctl->pAp = pAp;
   ctl->rz = ctl->rz_next;
   ctl->first = 0;
-  const double al = (pAp > 0.0) ? ctl->rz / pAp : 0.0;
+  const bool ok = (pAp > 0.0) && (ctl->rz > 0.0);
+  const double al = ok ? ctl->rz / pAp : 0.0;
   ctl->alpha_d = al;
   ctl->alpha_f = (float)al;
-  if (!(pAp > 0.0)) {
-    ctl->status = isfinite(pAp) ? 5 : 6;
+  if (!ok) {
+    ctl->status = (isfinite(pAp) && isfinite(ctl->rz)) ? 5 : 6;
     ctl->done = 1;
     ctl->outer_done = 1;
   }
@@ -186,7 +190,7 @@ __device__ __forceinline__ void fin_residual(Ctl* ctl, double rr, double bb, int
   } else if (rel <= ctl->tol_rel) {
     ctl->outer_done = 1;
   } else if (ctl->outer_it_step >= ctl->max_outer) {
-    ctl->status = 4;
+    if (ctl->status == 0) ctl->status = 4;  // an earlier error status is kept
     ctl->outer_done = 1;
   } else if (mode == 0) {
     // reduce the residual as far as this system needs, never less than inner_tol

@@ -78,6 +78,8 @@ th_status validate_opts(const thermal_solve_opts* o) {
     return th_fail(TH_EINVAL, "lanczos_steps must lie in [2, 1000]");
   if (o->cheb_fuse < 0 || o->cheb_fuse > 4) return th_fail(TH_EINVAL, "cheb_fuse must lie in [0, 4]");
   if (o->ad_check < 0 || o->ad_check > 100000) return th_fail(TH_EINVAL, "ad_check must lie in [0, 100000]");
+  if (o->test_wait_expire != 0 && o->test_wait_expire != 1)
+    return th_fail(TH_EINVAL, "test_wait_expire must be 0 or 1");
   if (o->precision == TH_PREC_ADAPTIVE && (o->precond == TH_PC_ZLINE || o->precond == TH_PC_MG))
     return th_fail(TH_EINVAL, "the adaptive precision supports the none, Jacobi and Chebyshev preconditioners");
   if (o->precond == TH_PC_MG && o->precision == TH_PREC_FP64)

@@ -57,7 +57,8 @@ __global__ void k_step_end(Ctl* c) {
 __global__ void k_cond(cudaGraphConditionalHandle h, const Ctl* c, int which) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   unsigned v = 0;
-  const int fatal = (c->status == 5 || c->status == 6);  // TH_EBREAKDOWN, TH_ENONFINITE
+  // TH_ECUDA (a bounded device wait ran out), TH_EBREAKDOWN, TH_ENONFINITE
+  const int fatal = (c->status == 3 || c->status == 5 || c->status == 6);
   if (which == 0) v = (c->done == 0);
   else if (which == 1) v = (c->outer_done == 0);
   else v = (c->step < c->n_steps) && !fatal;

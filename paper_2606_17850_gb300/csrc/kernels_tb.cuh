@@ -42,6 +42,8 @@
 #define TB_BW 36  // staged box width: the grown tile's first column rounded down to 16 bytes, + 32
 // bounded mbarrier wait: give up after about one second of device time
 #define TB_WAIT_NS 1000000000ull
+// test hook: limit of the wait on a barrier phase that nothing completes
+#define TB_TEST_WAIT_NS 2000000ull
 
 template <int LMAX>
 struct TBParams {
@@ -51,6 +53,7 @@ struct TBParams {
   float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
   float z1s;                    // first chunk: z_1 = z1s D^-1 r, formed from the staged r
+  int expire_test;              // test hook: the first wait of each CTA runs out (see below)
 };
 
 __device__ __forceinline__ unsigned tb_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -81,12 +84,13 @@ __device__ __forceinline__ unsigned long long tb_clock_ns() {
   return t;
 }
 
-// true when the phase completed; false after about TB_WAIT_NS of device time
-__device__ __forceinline__ bool tb_mbar_wait(unsigned long long* bar, unsigned parity) {
+// true when the phase completed; false after about limit_ns of device time
+__device__ __forceinline__ bool tb_mbar_wait(unsigned long long* bar, unsigned parity,
+                                             unsigned long long limit_ns = TB_WAIT_NS) {
   if (tb_mbar_try(bar, parity)) return true;
   const unsigned long long t0 = tb_clock_ns();
   while (!tb_mbar_try(bar, parity))
-    if (tb_clock_ns() - t0 > TB_WAIT_NS) return false;
+    if (tb_clock_ns() - t0 > limit_ns) return false;
   return true;
 }
 
@@ -99,8 +103,9 @@ __device__ __forceinline__ void tb_tma_3d(float* dst, const CUtensorMap* map, in
       : "memory");
 }
 
-// dynamic shared memory of one CTA: staging (3 boxes) + two planes + mbarrier,
-// plus room to align the staging boxes to 128 bytes
+// dynamic shared memory of one CTA: staging (3 boxes) + two planes + two mbarriers
+// (the staged loads' and the test hook's), plus room to align the staging boxes to
+// 128 bytes
 template <int LMAX, int EY>
 constexpr size_t tb_smem_bytes() {
   return ((size_t)3 * LMAX * EY * TB_BW + (size_t)2 * LMAX * EY * TB_EX) * sizeof(float) + 16 + 128;
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   }
   if (tid == 0) {
     tb_mbar_init(bar, 1);
+    tb_mbar_init(bar + 1, 1);  // test hook only: no thread ever arrives on it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
@@ -172,11 +178,20 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   float part[1] = {0.f};
   unsigned parity = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const bool timed_out = !tb_mbar_wait(bar, parity);
-    if (__syncthreads_or(timed_out)) {
+    // With the test hook the CTA first waits on a phase of the second barrier that
+    // nothing completes, so that wait runs out after TB_TEST_WAIT_NS and the expiry
+    // path below runs with this tile's copy still outstanding or just landed.
+    bool ok = !(P.expire_test && t == (int)blockIdx.x) || tb_mbar_wait(bar + 1, 0u, TB_TEST_WAIT_NS);
+    if (ok) ok = tb_mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {
+      // Expiry: record the error and end the solve's loops, then wait (bounded
+      // again) for this tile's tensor copy, so the CTA never exits while a copy
+      // into its shared memory may still be in flight.  No later copy was issued.
       if (tid == 0) {
-        tb_mbar_wait(bar, parity);  // give the copy in flight a second chance to land
-        ctl->status = 3;
+        tb_mbar_wait(bar, parity);
+        atomicCAS(&ctl->status, 0, 3);  // TH_ECUDA, unless an error is recorded already
+        ctl->outer_done = 1;
+        __threadfence();
         atomicExch(&ctl->done, 1);
       }
       break;

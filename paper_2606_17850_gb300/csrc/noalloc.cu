@@ -79,6 +79,13 @@ extern "C" th_status thermal_apply_dot_noalloc(int nx, int ny, int layers, const
                      "grid too large for the allocation-free entry point: ceil(nx/32)*ceil(ny/8)*layers = %lld "
                      "thread blocks, the static scratch holds %d",
                      blocks, TH_NOALLOC_MAX_BLOCKS);
+    {
+      // the product reads neighbours of x while other threads write y: the two
+      // vectors must not share any element
+      const long long cells = (long long)nx * ny * layers;
+      const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y, nb = (uintptr_t)cells * sizeof(float);
+      if (xa < ya + nb && ya < xa + nb) return th_fail(TH_EINVAL, "x and y must not overlap");
+    }
     LayerS tab;
     for (int l = 0; l < TH_MAXL; ++l) tab.s[l] = l < layers ? s_layer[l] : 0.0f;
     double* scratch = nullptr;

@@ -70,6 +70,7 @@ struct Plan {
   unsigned nbr4 = 1;  // grid of the grid-stride reducing element-wise kernels
   unsigned nbs4 = 1, nbq4 = 1;  // grids of the tile-walking spmv_dot and residual (resident blocks)
   bool fused_init = false;  // the refinement residual also starts the inner solve
+  int expire_test = 0;      // test hook of the fused Chebyshev kernel's bounded wait
 };
 
 static inline unsigned nb1(long long n) { return (unsigned)((n + 255) / 256); }
@@ -325,6 +326,7 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
   P.dt = dt;
   P.pdtype = pdtype;
   P.transient = transient;
+  P.expire_test = o->test_wait_expire;
   TH_TRY(grid_ensure_tab(g, dt, s));
   P.ad = (P.prec == TH_PREC_ADAPTIVE);
   TH_TRY(grid_ensure_workspace(g, P.prec == TH_PREC_FP64 || P.ad, s));
@@ -542,6 +544,7 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
     prm.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
   }
   prm.z1s = (float)P.inv_theta;
+  prm.expire_test = P.expire_test;
   const LayerTab& T = g->tab_host;
   const int L = P.d.L;
   for (int z = 0; z < L; ++z) {
@@ -990,11 +993,12 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
 // ------------------------------------------------------------------ graph building
 
 struct GraphKey {
-  int kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs;
+  int kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, expire;
   double dt;
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, dt) <
-           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.extrap, o.fuse, o.ad_pairs, o.dt);
+    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, expire, dt) <
+           std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.extrap, o.fuse, o.ad_pairs, o.expire,
+                    o.dt);
   }
 };
 struct GraphEntry {
@@ -1364,7 +1368,7 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   TH_CUDA(cudaEventRecord(e0, s));
   if (o->use_graph) {
     const GraphKey key{kind,   P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.extrap ? P.extrap_order : 0,
-                       o->cheb_fuse, P.ad ? P.ad_pairs : 0, P.transient ? dt : 0.0};
+                       o->cheb_fuse, P.ad ? P.ad_pairs : 0, P.expire_test, P.transient ? dt : 0.0};
     if (!g->graphs) {
       g->graphs = new GraphCache();
       for (auto& sx : g->graphs->cs) TH_CUDA(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
@@ -1401,7 +1405,7 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
         k_step_end<<<1, 1, 0, s>>>(g->ctl);
         TH_CHECK_LAUNCH();
         TH_TRY(poll(g, s, &h));
-        if (h.status == TH_EBREAKDOWN || h.status == TH_ENONFINITE) break;
+        if (h.status == TH_ECUDA || h.status == TH_EBREAKDOWN || h.status == TH_ENONFINITE) break;
       }
     } else {
       TH_TRY(polled_solve(P, s));
@@ -1423,6 +1427,9 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   th_status res = (th_status)h.status;
   if (res == TH_OK && !(h.rel_res <= o->tol_rel)) res = TH_ENOCONV;
   if (stats) stats->status = res;
+  if (res == TH_ECUDA)
+    return th_fail(res, "device wait timed out: a bounded wait for staged data in the fused Chebyshev kernel ran "
+                        "out (rel. residual %.3e)", h.rel_res);
   if (res != TH_OK) return th_fail(res, "solve ended with status %d (rel. residual %.3e, tol %.1e)", (int)res,
                                    h.rel_res, o->tol_rel);
   return TH_OK;

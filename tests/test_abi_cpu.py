@@ -119,3 +119,23 @@ def test_empty_and_negative_batches(lib):
     assert lib.thermal_solve_batched(None, 0, None, 7, None, C.byref(o), None, None) == _lib.TH_EINVAL
     o.cheb_degree = 0
     assert lib.thermal_solve_batched(None, 0, None, _lib.TH_F64, None, C.byref(o), None, None) == _lib.TH_EINVAL
+
+
+def test_noalloc_rejects_before_any_device_work(lib):
+    """The allocation-free product checks sizes, NULLs and x/y overlap on the host
+    before it looks up its scratch or launches anything (placeholder addresses here
+    are never dereferenced)."""
+    from paper_2606_17850_gb300 import _lib
+    s_arr = (C.c_float * 2)(0.0, 1.0)
+    a, b = C.c_void_p(1 << 20), C.c_void_p(1 << 30)   # two placeholder ranges far apart
+    xAx = C.c_void_p(1 << 31)
+    f = lib.thermal_apply_dot_noalloc
+    assert f(0, 4, 1, a, a, a, s_arr, a, b, xAx, None) == _lib.TH_EINVAL
+    assert f(4, 4, 1, a, a, a, s_arr, None, b, xAx, None) == _lib.TH_EINVAL
+    # ceil(4096/32) * ceil(4096/8) * 2 = 131072 thread blocks > the 65536 partials
+    assert f(4096, 4096, 2, a, a, a, s_arr, a, b, xAx, None) == _lib.TH_EINVAL
+    assert b"static scratch" in lib.thermal_last_error()
+    # x == y, and y starting inside x's 16 floats
+    for y in (a, C.c_void_p((1 << 20) + 32)):
+        assert f(4, 4, 1, a, a, a, s_arr, a, y, xAx, None) == _lib.TH_EINVAL
+        assert b"overlap" in lib.thermal_last_error()

@@ -256,6 +256,37 @@ def test_preconditioner_apply(pc, scaled, nx):
     np.testing.assert_allclose(z, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
 
 
+# the whole chain on each side: the oracle's own FP64 Lanczos interval feeds the
+# oracle's polynomial, the GPU's FP32 Lanczos feeds the GPU's.  Transient systems
+# with m close to N Lanczos steps, where FP64 Ritz values equal the extreme
+# eigenvalues (numpy eigvalsh) and FP32 ones agree with them to < 3e-6.
+@pytest.mark.parametrize("nx,ny,mk,m,scaled", [(36, 29, "c2", 300, 1), (37, 29, "c2", 300, 1),
+                                               (6, 5, "c2", 240, 1), (6, 5, "c2", 240, 0),
+                                               (12, 10, "c1", 480, 1)])
+def test_chebyshev_chain_from_oracle_lanczos(nx, ny, mk, m, scaled):
+    st = STACKS[mk]()
+    dt, k = 1e-4, 12
+    A = disc.assemble(nx, ny, st, dt=dt)
+    D = A.diagonal()
+    op_l = krylov.jacobi_scaled(A)[0] if scaled else (lambda v: A @ v)
+    a, b = krylov.lanczos(op_l, krylov.splitmix64_uniform(A.shape[0], 0x5EED), m)
+    lmin, lmax = krylov.chebyshev_bounds(*krylov.ritz_extremes(a, b))
+    M = (A.toarray() / np.sqrt(D)[:, None] / np.sqrt(D)[None, :]) if scaled else A.toarray()
+    ev = np.linalg.eigvalsh(M)
+    ex_min, ex_max = krylov.chebyshev_bounds(ev[0], ev[-1])
+    assert abs(lmax / ex_max - 1) <= 1e-10 and abs(lmin / ex_min - 1) <= 1e-6   # the oracle's interval
+    g = grid_of(nx, ny, st)
+    _, _, glmin, glmax = g.spectral_bounds(dt, lanczos_steps=m, cheb_scaled=scaled)
+    assert abs(glmax / lmax - 1) <= 1e-5 and abs(glmin / lmin - 1) <= 1e-4
+    r = ti.random_vector(A.shape[0], 6).astype(np.float32)
+    z = g.precond(cuda(r), dt, precond="cheb", cheb_degree=k, cheb_scaled=scaled,
+                  lanczos_steps=m).cpu().double().numpy()
+    r64 = r.astype(np.float64)
+    op = (lambda v: (A @ v) / D) if scaled else (lambda v: A @ v)
+    ref = krylov.chebyshev(op, r64 / D if scaled else r64, lmin, lmax, k)
+    np.testing.assert_allclose(z, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("k", [2, 5, 8, 12])
 @pytest.mark.parametrize("dt", [0.0, 1e-4])
 @pytest.mark.parametrize("mk", ["c2", "c1", "mol"])

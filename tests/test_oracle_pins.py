@@ -97,6 +97,64 @@ def _bruteforce_apply(nx, ny, stack, x, dt=None):
     return y
 
 
+
+# ----------------------------------------------------------------- error metrics (Sec. 5.1)
+
+def _two_cell_column():
+    """A 1 x 1 x 2 column worked by hand: face conductance g = 2 W/K between the cells,
+    top sink hS = 3 W/K, T_amb = 45 C, power P = (1, 0.5) W.  The rows of
+    Eq. (steady-state) are g(T0 - T1) = P0 and g(T1 - T0) + hS T1 = P1 + hS T_amb,
+    whose solution is theta = T - T_amb = (1.0, 0.5) K."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(np.array([[2.0, -2.0], [-2.0, 5.0]]))
+    b = np.array([1.0, 0.5 + 3.0 * 45.0])
+    return A, b, 45.0
+
+
+def test_rel_residual_hand_computed():
+    """||b - A T|| / ||b_theta||: for T = T_amb + (1.1, 0.5) the residual is (-0.2, 0.2)
+    and b_theta = P = (1, 0.5), so the value is 0.2 sqrt(2) / sqrt(1.25) = 0.252982...
+    Normalising by ||b|| (which holds hS T_amb = 135) would give 0.00209 instead."""
+    A, b, ta = _two_cell_column()
+    exact = ta + np.array([1.0, 0.5])
+    assert solve.rel_residual(A, exact, b, ta) == 0.0
+    T = ta + np.array([1.1, 0.5])
+    want = 0.2 * np.sqrt(2.0) / np.sqrt(1.25)
+    assert abs(solve.rel_residual(A, T, b, ta) - want) <= 1e-14
+    assert abs(np.linalg.norm(b - A @ T) / np.linalg.norm(b) - want) > 0.2   # the other normalisation
+    # scale invariance of a relative residual: P and theta scaled together
+    T2 = ta + 7.0 * np.array([1.1, 0.5])
+    b2 = np.array([7.0, 3.5 + 3.0 * 45.0])
+    assert abs(solve.rel_residual(A, T2, b2, ta) - want) <= 1e-13
+
+
+def test_rise_relative_and_inf_error_hand_computed():
+    """max|T - T_ref| / max|T_ref - T_amb| = 0.1 / 1.0 for the column above; relative to
+    the absolute temperature (about 46 C) it would be 0.00217.  ||e||_inf = 0.1 K."""
+    ta = 45.0
+    T_ref = ta + np.array([1.0, 0.5])
+    T = ta + np.array([1.1, 0.45])
+    assert abs(solve.rise_relative_error(T, T_ref, ta) - 0.1) <= 1e-13
+    assert abs(solve.inf_error(T, T_ref) - 0.1) <= 1e-13
+    # the metric is symmetric in sign and unchanged by a common shift of T_amb
+    assert abs(solve.rise_relative_error(2 * T_ref - T, T_ref, ta) - 0.1) <= 1e-13
+    assert abs(solve.rise_relative_error(T + 10, T_ref + 10, ta + 10) - 0.1) <= 1e-12
+
+
+def test_rel_residual_on_an_assembled_stack_matches_theta_system():
+    """On an assembled stack the metric equals ||P - G theta|| / ||P|| computed from the
+    theta form directly (G = A, b_theta = P: every conduction row sums to zero)."""
+    st = ti.stack_c1()
+    nx, ny = 6, 5
+    A = disc.assemble(nx, ny, st)
+    P = uniform_power(st, nx, ny)
+    b = disc.rhs_steady(nx, ny, st, P)
+    theta = ti.random_vector(A.shape[0], 4, lo=0.0, hi=30.0)
+    want = np.linalg.norm(P - A @ theta) / np.linalg.norm(P)
+    got = solve.rel_residual(A, st.t_amb + theta, b, st.t_amb)
+    assert abs(got - want) <= 1e-12 * want
+
+
 @pytest.mark.parametrize("nx,ny,mk", [(3, 2, "c1"), (4, 5, "c2"), (1, 3, "mol")])
 @pytest.mark.parametrize("dt", [None, 1e-4])
 def test_assembly_matches_bruteforce(nx, ny, mk, dt):
