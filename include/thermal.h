@@ -101,8 +101,10 @@ typedef struct thermal_solve_opts {
                        /* start); inside a step loop 1 linear extrapolation 2 T_n - T_{n-1},  */
                        /* 2 quadratic 3 T_n - 3 T_{n-1} + T_{n-2} (mixed path with nx % 4 == 0; */
                        /* linear elsewhere); lower orders while the history is short (0)     */
-  int cheb_fuse;       /* Chebyshev steps per launch on layer-uniform grids (temporal blocking */
-                       /* in shared memory): 0 auto (4), 1 one step per launch, 2..4 (0)      */
+  int cheb_fuse;       /* Chebyshev steps per launch (temporal blocking in shared memory) on  */
+                       /* grids with nx % 4 == 0: layer table up to 12 layers, per-face arrays */
+                       /* up to 8 (not with the BF16 coefficients): 0 auto (4), 1 one step   */
+                       /* per launch, 2..4 (0)                                                */
   int ad_check;        /* ADAPTIVE: PCG iterations between true-residual evaluations of the   */
                        /* switching criterion, rounded up to even; 0: 20 steady, 6 transient  */
                        /* (the paper's 20 and 5 on the two-iteration loop body) (0)           */
@@ -274,6 +276,9 @@ th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solv
  *  17  adaptive path, early stage: FP64 mu = A p with FP32 coefficients + p^T mu
  *  18  adaptive path, late stage: the same with FP64 coefficients
  *  19  one multigrid V-cycle (all levels; several launches)
+ *  20, 21, 22  four, two, three Chebyshev steps fused in one launch on the per-face
+ *      arrays (the variant grids with a conductivity map run); nx % 4 == 0 and at
+ *      most 8 layers, else TH_EINVAL
  * Synchronous.
  */
 th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream);

@@ -164,7 +164,7 @@ class ThermalGrid:
                "cheb_f32_faces": 9, "spmv_dot_f32_faces": 10, "residual_df_faces": 11, "stencil_f32_faces": 12,
                "cheb_tb4": 13, "cheb_tb2": 14, "cheb_tb3": 15,
                "ad_cheb_a3": 16, "ad_spmv_early": 17, "ad_spmv_late": 18,
-               "mg_vcycle": 19}
+               "mg_vcycle": 19, "cheb_tbf4": 20, "cheb_tbf2": 21, "cheb_tbf3": 22}
 
     def kernel_time(self, kernel, reps=50, dt=0.0):
         """Average duration (ms) of one launch of a hot kernel on this grid (CUDA events)."""

@@ -286,3 +286,217 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   ctl->rz_next = tot[0];
   ctl_set_beta(ctl);
 }
+
+// ---------------------------------------------------------------------------
+// Fused Chebyshev steps on grids with per-face conductances (a per-cell
+// conductivity map): the same tile walk, staging pipeline and bounded waits as
+// k_cheb_tb, with the face arrays staged beside the vectors.
+//
+// A tile is 32 x TBF_EY columns (768 threads, so a thread may hold 85 registers).
+// Six boxes are staged per tile: z_m, z_{m-1}, r, gx, gy, gz.  Each thread keeps
+// its column's own faces (+x, +y, +z per layer) and the face to the row below
+// (-y) in registers; the face to the west (-x) is the west lane's +x face, taken by
+// a warp shuffle.  The diagonal is summed once per tile in the one-step kernels'
+// order (s, +x, -x, +y, -y, +z, -z) and inverted in FP32.  With the Jacobi
+// scaling, D^-1 A v = v - D^-1 (sum_f g_f v_f) over the six neighbours f, so a
+// step is
+//   z_{m+1} = z_m + c1 (z_m - z_{m-1}) + c2 (D^-1 (r + sum_f g_f z_f) - z_m)
+// (six products, no diagonal register).  Faces outside the grid are stored as 0;
+// a missing neighbour is read as the cell itself and multiplied by that 0.
+#define TBF_EY 24
+
+template <int LMAX>
+struct TBFParams {
+  float c1[TB_H], c2[TB_H];  // Chebyshev step coefficients of this chunk
+  float s[LMAX];             // per-layer diagonal term: h dx dy (top) + c dx dy dz / dt
+  float z1s;                 // first chunk: z_1 = z1s D^-1 r
+  int expire_test;           // test hook of the bounded wait (as in k_cheb_tb)
+};
+
+template <int LMAX>
+constexpr size_t tbf_smem_bytes() {
+  return ((size_t)6 * LMAX * TBF_EY * TB_BW + (size_t)2 * LMAX * TBF_EY * TB_EX) * sizeof(float) + 16 + 128;
+}
+
+template <int LMAX, int STEPS, bool LAST, bool FIRST>
+__global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
+    k_cheb_tbf(Dims d, int ntx, int ntiles, int has_prev, Ctl* ctl, const __grid_constant__ CUtensorMap m_cur,
+               const __grid_constant__ CUtensorMap m_prev, const __grid_constant__ CUtensorMap m_r,
+               const __grid_constant__ CUtensorMap m_gx, const __grid_constant__ CUtensorMap m_gy,
+               const __grid_constant__ CUtensorMap m_gz, const float* __restrict__ invd, float* __restrict__ out_cur,
+               float* __restrict__ out_prev, const __grid_constant__ TBFParams<LMAX> P, double* partials, int stride,
+               unsigned* counter) {
+  if (ld_int(&ctl->done)) return;
+  constexpr int EY = TBF_EY;
+  constexpr int H = STEPS;
+  constexpr int TX = TB_EX - 2 * H, TY = EY - 2 * H;  // interior of a tile
+  constexpr int PL = EY * TB_EX;                        // floats per layer plane
+  constexpr int SL = EY * TB_BW;                        // floats per staged layer
+  extern __shared__ __align__(128) float tb_dyn[];
+  float* tb_sm = tb_dyn + (((128u - (tb_smem(tb_dyn) & 127u)) & 127u) >> 2);  // 128-byte aligned
+  float* stage = tb_sm;                  // [6][LMAX][EY][TB_BW]: z_m, z_{m-1}, r, gx, gy, gz
+  float* plane = tb_sm + 6 * LMAX * SL;  // [2][LMAX][EY][TB_EX]
+  unsigned long long* bar = (unsigned long long*)(plane + 2 * LMAX * PL);
+  const int L = d.L;
+  const int ex = threadIdx.x, ey = threadIdx.y;
+  const int tid = ex + TB_EX * ey;
+  const unsigned box_bytes = (unsigned)(L * SL * sizeof(float));
+  const unsigned nbox = 4u + (FIRST ? 0u : (has_prev ? 2u : 1u));
+  const unsigned tx_bytes = box_bytes * nbox;
+
+  // staged layers the tensor copies never write (L..LMAX-1, and z_{m-1} when there
+  // is none) are zeroed once
+  for (int b = 0; b < 6; ++b) {
+    const int z0 = (b == 1 && !has_prev) ? 0 : L;
+    for (int i = tid; i < (LMAX - z0) * SL; i += TB_EX * EY) stage[(b * LMAX + z0) * SL + i] = 0.f;
+  }
+  if (tid == 0) {
+    tb_mbar_init(bar, 1);
+    tb_mbar_init(bar + 1, 1);  // test hook only: no thread ever arrives on it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int tx, int ty) {
+    const int xa = (tx * TX - H) & ~3, y0 = ty * TY - H;
+    tb_mbar_expect(bar, tx_bytes);
+    if (!FIRST) tb_tma_3d(stage, &m_cur, xa, y0, 0, bar);
+    if (has_prev && !FIRST) tb_tma_3d(stage + LMAX * SL, &m_prev, xa, y0, 0, bar);
+    tb_tma_3d(stage + 2 * LMAX * SL, &m_r, xa, y0, 0, bar);
+    tb_tma_3d(stage + 3 * LMAX * SL, &m_gx, xa, y0, 0, bar);
+    tb_tma_3d(stage + 4 * LMAX * SL, &m_gy, xa, y0, 0, bar);
+    tb_tma_3d(stage + 5 * LMAX * SL, &m_gz, xa, y0, 0, bar);
+  };
+  const int dtx = (int)gridDim.x % ntx, dty = (int)gridDim.x / ntx;
+  auto advance = [&](int& tx, int& ty) {
+    tx += dtx;
+    ty += dty;
+    if (tx >= ntx) {
+      tx -= ntx;
+      ++ty;
+    }
+  };
+  int tx = (int)blockIdx.x % ntx, ty = (int)blockIdx.x / ntx;
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(tx, ty);
+
+  float part[1] = {0.f};
+  unsigned parity = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    bool ok = !(P.expire_test && t == (int)blockIdx.x) || tb_mbar_wait(bar + 1, 0u, TB_TEST_WAIT_NS);
+    if (ok) ok = tb_mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {
+      // expiry: as in k_cheb_tb, record the error, end the loops and wait (bounded)
+      // for this tile's copies before the CTA leaves
+      if (tid == 0) {
+        tb_mbar_wait(bar, parity);
+        atomicCAS(&ctl->status, 0, 3);
+        ctl->outer_done = 1;
+        __threadfence();
+        atomicExch(&ctl->done, 1);
+      }
+      break;
+    }
+    parity ^= 1u;
+    const int x0 = tx * TX - H;
+    const int gxi = x0 + ex;
+    const int gyi = ty * TY - H + ey;
+    const int st = ey * TB_BW + ex + (x0 - (x0 & ~3));  // this column in a staged layer
+    const bool inside = gxi >= 0 && gxi < d.nx && gyi >= 0 && gyi < d.ny;
+    float za[LMAX], zb[LMAX], rr[LMAX], inv[LMAX], fx[LMAX], fy[LMAX], fyd[LMAX], fz[LMAX];
+#pragma unroll
+    for (int z = 0; z < LMAX; ++z) {
+      if (!FIRST) {
+        za[z] = stage[z * SL + st];
+        zb[z] = stage[(LMAX + z) * SL + st];
+      }
+      rr[z] = stage[(2 * LMAX + z) * SL + st];
+      fx[z] = stage[(3 * LMAX + z) * SL + st];
+      fy[z] = stage[(4 * LMAX + z) * SL + st];
+      fyd[z] = ey > 0 ? stage[(4 * LMAX + z) * SL + st - TB_BW] : 0.f;
+      fz[z] = stage[(5 * LMAX + z) * SL + st];
+    }
+    // The diagonal in the one-step kernels' order: s, +x, -x, +y, -y, +z, -z.  A first
+    // chunk forms z_1 = z1s D^-1 r on every column of the grown tile (step 0 reads the
+    // outer ring too); the west ring (lane 0) and the south ring (row 0) lack the
+    // staged -x / -y face, so they take 1/A_ii from the per-cell array.
+    const bool ring = FIRST && (ex == 0 || ey == 0) && inside;
+    const long long cbase = (long long)gxi + (long long)d.nx * gyi;
+#pragma unroll
+    for (int z = 0; z < LMAX; ++z) {
+      const float fxw = __shfl_up_sync(0xffffffffu, fx[z], 1);
+      float dg = P.s[z];
+      dg += fx[z];
+      dg += ex > 0 ? fxw : 0.f;
+      dg += fy[z];
+      dg += fyd[z];
+      dg += fz[z];
+      dg += z > 0 ? fz[z > 0 ? z - 1 : 0] : 0.f;
+      float iv = 1.0f / dg;
+      if (ring && z < L) iv = __ldg(invd + cbase + d.pxy * z);
+      inv[z] = (z < L && inside) ? iv : 0.f;  // columns outside the grid stay 0
+      if (FIRST) {
+        za[z] = rr[z] * inv[z] * P.z1s;
+        zb[z] = 0.f;
+      }
+    }
+    __syncthreads();  // staging buffer consumed by every thread
+    const int tn = t + gridDim.x;
+    int txn = tx, tyn = ty;
+    advance(txn, tyn);
+    if (tid == 0 && tn < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(txn, tyn);
+    }
+    const int oR = tid + ((gxi + 1 < d.nx) ? 1 : 0), oL = tid - ((gxi > 0) ? 1 : 0);
+    const int oU = tid + ((gyi + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gyi > 0) ? TB_EX : 0);
+    auto step = [&](const float (&C)[LMAX], float (&N)[LMAX], const int j) {
+      float* pl = plane + (j & 1) * LMAX * PL;
+#pragma unroll
+      for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = C[z];
+      __syncthreads();
+      const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
+#pragma unroll
+      for (int z = 0; z < LMAX; ++z) {
+        const float fxw = __shfl_up_sync(0xffffffffu, fx[z], 1);  // every lane: outside the branch
+        if (upd) {
+          const float v = C[z];
+          const float* q = pl + z * PL;
+          float a = fx[z] * q[oR];
+          a = fmaf(fxw, q[oL], a);
+          a = fmaf(fy[z], q[oU], a);
+          a = fmaf(fyd[z], q[oD], a);
+          if (z + 1 < LMAX) a = fmaf(fz[z], C[z + 1 < LMAX ? z + 1 : z], a);
+          if (z > 0) a = fmaf(fz[z > 0 ? z - 1 : 0], C[z > 0 ? z - 1 : z], a);
+          const float res = fmaf(inv[z], rr[z] + a, -v);  // D^-1 (r - A v)
+          N[z] = fmaf(P.c2[j], res, fmaf(P.c1[j], v - N[z], v));
+        }
+      }
+    };
+#pragma unroll
+    for (int j = 0; j < STEPS; ++j) {
+      if (j & 1) step(zb, za, j);
+      else step(za, zb, j);
+    }
+    const float(&cur)[LMAX] = (STEPS & 1) ? zb : za;
+    const float(&prv)[LMAX] = (STEPS & 1) ? za : zb;
+    const bool interior = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
+    if (interior) {
+      const long long base = (long long)gxi + (long long)d.nx * gyi;
+#pragma unroll
+      for (int z = 0; z < LMAX; ++z) {
+        if (z < L) {
+          const long long i = base + d.pxy * z;
+          out_cur[i] = cur[z];
+          if (out_prev) out_prev[i] = prv[z];
+          if (LAST) part[0] += rr[z] * cur[z];
+        }
+      }
+    }
+    tx = txn;
+    ty = tyn;
+  }
+  if (!LAST) return;
+  double tot[1];
+  if (!grid_reduce<float, 1>(part, partials, stride, counter, tot)) return;
+  ctl->rz_next = tot[0];
+  ctl_set_beta(ctl);
+}

@@ -327,12 +327,15 @@ struct ResidInit {
   int scaled, rz_here;
 };
 
-template <typename TP, int ZI>
-__global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three blocks per SM
-    k_residual_df_v4(Dims d, int zc, Ctl* ctl, const LayerTab* tab, const float* __restrict__ th_hi,
-                     const float* __restrict__ th_lo, const TP* const* ptab, const float* __restrict__ thn_hi,
-                     const float* __restrict__ thn_lo, float* __restrict__ r, int count_outer, ResidInit ri,
-                     double* partials, int stride, unsigned* counter) {
+// UNI: layer-uniform grid, face conductances (hi, lo) from the per-layer table.
+// Otherwise the per-face arrays: fh = FP32 high parts, fl = low parts g - (float)g
+// (zero on the domain boundary), six face products per cell.
+template <typename TP, int ZI, bool UNI>
+__global__ void __launch_bounds__(TH_BX* TH_BY4, UNI ? 3 : 2)  // layer table: 80 registers, three blocks per SM
+    k_residual_df_v4(Dims d, int zc, Ctl* ctl, const LayerTab* tab, Faces32 fh, Faces32 fl,
+                     const float* __restrict__ th_hi, const float* __restrict__ th_lo, const TP* const* ptab,
+                     const float* __restrict__ thn_hi, const float* __restrict__ thn_lo, float* __restrict__ r,
+                     int count_outer, ResidInit ri, double* partials, int stride, unsigned* counter) {
   if (ld_int(&ctl->outer_done)) return;
   const TP* P = ptab[ld_int(&ctl->map_idx)];
   float v[3] = {0.f, 0.f, 0.f};
@@ -343,9 +346,14 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
     const long long pxy = d.pxy;
     const bool hasL = w.x0 > 0, hasR = w.x0 + 4 < d.nx, hasD = w.y > 0, hasU = w.y + 1 < d.ny;
     float4 hb = z4(), lb = z4();
+    float4 gbh = z4(), gbl = z4();  // per-face grids: the faces below the current layer
     if (w.zs > 0) {
       hb = ld4(th_hi + w.b0 + (long long)(w.zs - 1) * pxy);
       lb = ld4(th_lo + w.b0 + (long long)(w.zs - 1) * pxy);
+      if (!UNI) {
+        gbh = ldc4(fh.gz + w.b0 + (long long)(w.zs - 1) * pxy);
+        gbl = ldc4(fl.gz + w.b0 + (long long)(w.zs - 1) * pxy);
+      }
     }
     float4 hc = ld4(th_hi + w.b0 + (long long)w.zs * pxy), lc = ld4(th_lo + w.b0 + (long long)w.zs * pxy);
     for (int z = w.zs; z < w.ze; ++z) {
@@ -364,22 +372,38 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
         nh = ld4(thn_hi + i);
         nl = ld4(thn_lo + i);
       }
-      const df gx = df_make(__ldg(&tab->gxl_hi[z]), __ldg(&tab->gxl_lo[z]));
-      const df gy = df_make(__ldg(&tab->gyl_hi[z]), __ldg(&tab->gyl_lo[z]));
-      const df ga = df_make(__ldg(&tab->gzl_hi[z]), __ldg(&tab->gzl_lo[z]));
-      const df gb = hasB ? df_make(__ldg(&tab->gzl_hi[z - 1]), __ldg(&tab->gzl_lo[z - 1])) : df_make(0.f, 0.f);
       const df sk = df_make(__ldg(&tab->sink_hi[z]), __ldg(&tab->sink_lo[z]));
       const df cd = df_make(__ldg(&tab->cdt_hi[z]), __ldg(&tab->cdt_lo[z]));
+      df gx, gy, ga, gb;  // layer table
+      float4 gxh, gxl_, gyh, gyl_, gdh, gdl, gah, gal;  // per-face arrays
+      float gLh = 0.f, gLl = 0.f;
+      if (UNI) {
+        gx = df_make(__ldg(&tab->gxl_hi[z]), __ldg(&tab->gxl_lo[z]));
+        gy = df_make(__ldg(&tab->gyl_hi[z]), __ldg(&tab->gyl_lo[z]));
+        ga = df_make(__ldg(&tab->gzl_hi[z]), __ldg(&tab->gzl_lo[z]));
+        gb = hasB ? df_make(__ldg(&tab->gzl_hi[z - 1]), __ldg(&tab->gzl_lo[z - 1])) : df_make(0.f, 0.f);
+      } else {
+        gxh = ldc4(fh.gx + i);
+        gxl_ = ldc4(fl.gx + i);
+        gyh = ldc4(fh.gy + i);
+        gyl_ = ldc4(fl.gy + i);
+        gdh = hasD ? ldc4(fh.gy + i - d.nx) : z4();
+        gdl = hasD ? ldc4(fl.gy + i - d.nx) : z4();
+        gah = hasA ? ldc4(fh.gz + i) : z4();
+        gal = hasA ? ldc4(fl.gz + i) : z4();
+        if (hasL) {
+          gLh = ldc(fh.gx + i - 1);
+          gLl = ldc(fl.gx + i - 1);
+        }
+      }
       float o[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const df t = df_make(cmp(hc, k), cmp(lc, k));
         const df tr = (k == 3) ? df_make(hr1, lr1) : df_make(cmp(hc, k + 1), cmp(lc, k + 1));
         const df tl = (k == 0) ? df_make(hl1, ll1) : df_make(cmp(hc, k - 1), cmp(lc, k - 1));
-        // the neighbour differences are normalised (their high parts often cancel
-        // exactly); the sums, products and the accumulation run unnormalised
-        const df dx = ldf_add(df_sub(t, tr), df_sub(t, tl));
-        const df dy = ldf_add(df_sub(t, df_make(cmp(hu, k), cmp(lu, k))), df_sub(t, df_make(cmp(hd, k), cmp(ld_, k))));
+        const df tu = df_make(cmp(hu, k), cmp(lu, k)), td = df_make(cmp(hd, k), cmp(ld_, k));
+        const df ta = df_make(cmp(ha, k), cmp(la, k)), tb = df_make(cmp(hbz, k), cmp(lbz, k));
         df acc = pv[k];
         if (sk.hi != 0.f) acc = ldf_sub(acc, ldf_mul(sk, t));  // the sink is on the top layer only
         float bh = pv[k].hi;  // ||b|| needs FP32 accuracy only
@@ -388,10 +412,25 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
           acc = ldf_add(acc, ldf_mul(cd, df_sub(tn, t)));
           bh = __fmaf_rn(cd.hi, tn.hi, bh);
         }
-        acc = ldf_sub(acc, ldf_mul(gx, dx));
-        acc = ldf_sub(acc, ldf_mul(gy, dy));
-        acc = ldf_sub(acc, ldf_mul(ga, df_sub(t, df_make(cmp(ha, k), cmp(la, k)))));
-        acc = ldf_sub(acc, ldf_mul(gb, df_sub(t, df_make(cmp(hbz, k), cmp(lbz, k)))));
+        // the neighbour differences are normalised (their high parts often cancel
+        // exactly); the sums, products and the accumulation run unnormalised
+        if (UNI) {
+          const df dx = ldf_add(df_sub(t, tr), df_sub(t, tl));
+          const df dy = ldf_add(df_sub(t, tu), df_sub(t, td));
+          acc = ldf_sub(acc, ldf_mul(gx, dx));
+          acc = ldf_sub(acc, ldf_mul(gy, dy));
+          acc = ldf_sub(acc, ldf_mul(ga, df_sub(t, ta)));
+          acc = ldf_sub(acc, ldf_mul(gb, df_sub(t, tb)));
+        } else {
+          const df gR = df_make(cmp(gxh, k), cmp(gxl_, k));
+          const df gL = (k == 0) ? df_make(gLh, gLl) : df_make(cmp(gxh, k - 1), cmp(gxl_, k - 1));
+          acc = ldf_sub(acc, ldf_mul(gR, df_sub(t, tr)));
+          acc = ldf_sub(acc, ldf_mul(gL, df_sub(t, tl)));
+          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gyh, k), cmp(gyl_, k)), df_sub(t, tu)));
+          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gdh, k), cmp(gdl, k)), df_sub(t, td)));
+          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gah, k), cmp(gal, k)), df_sub(t, ta)));
+          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gbh, k), cmp(gbl, k)), df_sub(t, tb)));
+        }
         o[k] = acc.hi + acc.lo;
         v[0] += o[k] * o[k];
         v[1] += bh * bh;
@@ -418,6 +457,10 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3)  // 80 registers: three bloc
       }
       hb = hc; lb = lc;
       hc = ha; lc = la;
+      if (!UNI) {
+        gbh = gah;
+        gbl = gal;
+      }
     }
   }
   double tot[3];

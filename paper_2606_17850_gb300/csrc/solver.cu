@@ -69,6 +69,7 @@ struct Plan {
   unsigned nbu4 = 1;
   unsigned nbr4 = 1;  // grid of the grid-stride reducing element-wise kernels
   unsigned nbs4 = 1, nbq4 = 1;  // grids of the tile-walking spmv_dot and residual (resident blocks)
+  unsigned nbf4 = 1;            // grid of the per-face residual (resident blocks)
   bool fused_init = false;  // the refinement residual also starts the inner solve
   int expire_test = 0;      // test hook of the fused Chebyshev kernel's bounded wait
 };
@@ -353,7 +354,8 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     const unsigned ntl = P.gb4.x * P.gb4.y * P.gb4.z;
     P.nbs4 = std::min(ntl, resident_grid(g->uniform ? (const void*)k_spmv_dot_v4<true>
                                                      : (const void*)k_spmv_dot_v4<false>));
-    P.nbq4 = std::min(ntl, resident_grid((const void*)k_residual_df_v4<float, 2>));
+    P.nbq4 = std::min(ntl, resident_grid((const void*)k_residual_df_v4<float, 2, true>));
+    P.nbf4 = std::min(ntl, resident_grid((const void*)k_residual_df_v4<float, -1, false>));
   }
   P.pc_spmv = 0;
   if (P.pc == TH_PC_CHEB) {
@@ -364,9 +366,12 @@ static th_status make_plan(thermal_grid* g, double dt, const thermal_solve_opts*
     const int fuse = o->cheb_fuse == 0 ? TB_H : o->cheb_fuse;
     // fused chunks exist for the Jacobi-scaled form (the default); the unscaled
     // polynomial of the paper runs one step per launch
-    if (P.prec != TH_PREC_FP64 && !P.ad && P.v4 && P.uni && P.scaled && fuse > 1 && P.k > 1) {
-      // register columns: up to 8 layers with 32 x 32 threads, up to 12 with 32 x 24
-      P.tb_lmax = g->L <= 8 ? 8 : (g->L <= 12 ? 12 : 0);
+    // (per-face grids: FP32 faces, so not the BF16-coefficient precision)
+    if (P.prec != TH_PREC_FP64 && !P.ad && P.v4 && P.scaled && fuse > 1 && P.k > 1 &&
+        (P.uni || P.prec == TH_PREC_MIXED_IR)) {
+      // register columns: layer table up to 8 layers with 32 x 32 threads, up to 12
+      // with 32 x 24; per-face arrays up to 8 layers with 32 x 24
+      P.tb_lmax = g->L <= 8 ? 8 : ((g->L <= 12 && P.uni) ? 12 : 0);
       if (P.tb_lmax > 0) {
         P.fused = true;
         int cur = 0, prev = -1, m = 1, left = P.k - 1;
@@ -585,6 +590,53 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   return TH_OK;
 }
 
+// Per-face grids: the fused chunk with the face arrays staged beside the vectors.
+template <int ST, bool LA, bool FI>
+static th_status tbf_launch(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
+  thermal_grid* g = P.g;
+  constexpr int LM = 8;
+  constexpr int TX = TB_EX - 2 * ST, TY = TBF_EY - 2 * ST;
+  float* pool[4] = {V.zc[0], V.zc[1], V.zc[2], V.mu};
+  TBFParams<LM> prm;
+  std::memset(&prm, 0, sizeof(prm));
+  for (int j = 0; j < TB_H; ++j) {
+    prm.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
+    prm.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+  }
+  for (int z = 0; z < P.d.L; ++z) prm.s[z] = g->tab_host.s32[z];
+  prm.z1s = (float)P.inv_theta;
+  prm.expire_test = P.expire_test;
+  CUtensorMap mc, mp, mr, mx, my, mz;
+  TH_TRY(tb_map(&mc, P.d, pool[c.in_cur], TBF_EY));
+  TH_TRY(tb_map(&mp, P.d, c.in_prev >= 0 ? pool[c.in_prev] : pool[c.in_cur], TBF_EY));
+  TH_TRY(tb_map(&mr, P.d, V.r, TBF_EY));
+  TH_TRY(tb_map(&mx, P.d, g->f32.gx, TBF_EY));
+  TH_TRY(tb_map(&my, P.d, g->f32.gy, TBF_EY));
+  TH_TRY(tb_map(&mz, P.d, g->f32.gz, TBF_EY));
+  const int ntx = (P.d.nx + TX - 1) / TX;
+  const int ntiles = ntx * ((P.d.ny + TY - 1) / TY);
+  const size_t smem = tbf_smem_bytes<LM>();
+  TH_CUDA(cudaFuncSetAttribute(k_cheb_tbf<LM, ST, LA, FI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int nblk = std::min(ntiles, sm_count());
+  if (nblk > g->partials_stride) return th_fail(TH_ESTATE, "partials buffer smaller than the temporal-blocking grid");
+  k_cheb_tbf<LM, ST, LA, FI><<<nblk, dim3(TB_EX, TBF_EY), smem, st>>>(
+      P.d, ntx, ntiles, c.in_prev >= 0 ? 1 : 0, g->ctl, mc, mp, mr, mx, my, mz, g->invd32, pool[c.out_cur],
+      c.out_prev >= 0 ? pool[c.out_prev] : nullptr, prm, g->partials, g->partials_stride, g->counters);
+  TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+template <bool LA, bool FI>
+static th_status tbf_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
+  switch (c.steps) {
+    case 1: return tbf_launch<1, LA, FI>(P, V, st, c);
+    case 2: return tbf_launch<2, LA, FI>(P, V, st, c);
+    case 3: return tbf_launch<3, LA, FI>(P, V, st, c);
+    case 4: return tbf_launch<4, LA, FI>(P, V, st, c);
+    default: return th_fail(TH_ESTATE, "temporal-blocking chunk with %d steps", c.steps);
+  }
+}
+
 // chunk dispatch on (steps, last chunk, first chunk)
 template <int LM, int EY, bool SC, bool LA, bool FI>
 static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c) {
@@ -601,6 +653,11 @@ static th_status tb_steps(const Plan& P, const VecSet<float>& V, cudaStream_t st
 // itself from the staged r.
 static bool tb_first(const Plan::Chunk& c) { return c.m0 == 1 && c.in_prev < 0; }
 
+static th_status tbf_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last) {
+  if (tb_first(c)) return last ? tbf_steps<true, true>(P, V, st, c) : tbf_steps<false, true>(P, V, st, c);
+  return last ? tbf_steps<true, false>(P, V, st, c) : tbf_steps<false, false>(P, V, st, c);
+}
+
 template <int LM, int EY>
 static th_status tb_chunk(const Plan& P, const VecSet<float>& V, cudaStream_t st, const Plan::Chunk& c, bool last) {
   if (tb_first(c))
@@ -612,7 +669,8 @@ static th_status tb_chain(const Plan& P, const VecSet<float>& V, cudaStream_t st
   for (size_t ci = 0; ci < P.chunks.size(); ++ci) {
     const bool last = (ci + 1 == P.chunks.size());
     const Plan::Chunk& c = P.chunks[ci];
-    if (P.tb_lmax == 8) TH_TRY((tb_chunk<8, 32>(P, V, st, c, last)));
+    if (!P.uni) TH_TRY(tbf_chunk(P, V, st, c, last));
+    else if (P.tb_lmax == 8) TH_TRY((tb_chunk<8, 32>(P, V, st, c, last)));
     else TH_TRY((tb_chunk<12, 24>(P, V, st, c, last)));
   }
   return TH_OK;
@@ -730,15 +788,23 @@ static th_status enq_iteration(const Plan& P, const VecSet<TV>& V, cudaStream_t 
 
 // zi: -1, or the preconditioner's z mode (0 none, 1 Jacobi, 2 Chebyshev) when the
 // residual also starts the inner solve
+// uni: layer-table coefficients (the start of the inner solve, zi >= 0, needs them);
+// otherwise the per-face arrays (hi, lo)
 template <typename TP>
 static void launch_residual_v4(const Plan& P, cudaStream_t st, const float* nh, const float* nl, int count_outer,
-                               int zi, const ResidInit& ri) {
+                               int zi, const ResidInit& ri, bool uni) {
   thermal_grid* g = P.g;
   const TP* const* pt = (const TP* const*)g->dev_ptrs;
-#define TH_RES4(ZI)                                                                                   \
-  k_residual_df_v4<TP, ZI><<<P.nbq4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->th_hi, g->th_lo, pt, \
-                                                    nh, nl, g->r32, count_outer, ri, g->partials,      \
-                                                    g->partials_stride, g->counters)
+  if (!uni) {
+    k_residual_df_v4<TP, -1, false><<<P.nbf4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->f32, g->f32lo, g->th_hi,
+                                                              g->th_lo, pt, nh, nl, g->r32, count_outer, ri,
+                                                              g->partials, g->partials_stride, g->counters);
+    return;
+  }
+#define TH_RES4(ZI)                                                                                           \
+  k_residual_df_v4<TP, ZI, true><<<P.nbq4, P.tb4, 0, st>>>(P.d, P.zc, g->ctl, g->tab, g->f32, g->f32lo, g->th_hi, \
+                                                          g->th_lo, pt, nh, nl, g->r32, count_outer, ri,        \
+                                                          g->partials, g->partials_stride, g->counters)
   switch (zi) {
     case 0: TH_RES4(0); break;
     case 1: TH_RES4(1); break;
@@ -754,7 +820,7 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
     // theta_n of the step: with the extrapolated guess the history array holds it
     const float* nh = P.transient ? (P.extrap ? g->thm_hi : g->thn_hi) : nullptr;
     const float* nl = P.transient ? (P.extrap ? g->thm_lo : g->thn_lo) : nullptr;
-    if (P.uni && P.v4) {
+    if (P.v4) {
       ResidInit ri{};
       int zi = -1;
       if (P.fused_init) {
@@ -767,9 +833,9 @@ static th_status enq_residual(const Plan& P, cudaStream_t st, int mode, int coun
         ri.rz_here = (P.pc == TH_PC_NONE || P.pc == TH_PC_JACOBI || (P.pc == TH_PC_CHEB && P.k == 1)) ? 1 : 0;
       }
       if (P.pdtype == TH_F32)
-        launch_residual_v4<float>(P, st, nh, nl, count_outer, zi, ri);
+        launch_residual_v4<float>(P, st, nh, nl, count_outer, zi, ri, P.uni);
       else
-        launch_residual_v4<double>(P, st, nh, nl, count_outer, zi, ri);
+        launch_residual_v4<double>(P, st, nh, nl, count_outer, zi, ri, P.uni);
       TH_CHECK_LAUNCH();
       return TH_OK;
     }
@@ -1524,13 +1590,15 @@ extern "C" th_status thermal_precond_apply(thermal_grid* g, double dt, const the
 extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, double dt, double* ms, void* stream) {
   ABI_BEGIN
   th_clear_error();
-  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 19) return th_fail(TH_EINVAL, "invalid argument");
+  if (!g || !ms || reps < 1 || kernel < 0 || kernel > 22) return th_fail(TH_EINVAL, "invalid argument");
   if (kernel >= 13 && kernel <= 15 && !(g->uniform && g->nx % 4 == 0))
     return th_fail(TH_EINVAL, "fused Chebyshev steps need a layer-uniform grid with nx %% 4 == 0");
+  if (kernel >= 20 && !(g->nx % 4 == 0 && g->L <= 8))
+    return th_fail(TH_EINVAL, "fused per-face Chebyshev steps need nx %% 4 == 0 and at most 8 layers");
   cudaStream_t s = (cudaStream_t)stream;
   thermal_solve_opts o;
   thermal_default_opts(&o);
-  o.precond = (kernel >= 13 && kernel <= 15) ? TH_PC_CHEB : (kernel == 19 ? TH_PC_MG : TH_PC_JACOBI);
+  o.precond = ((kernel >= 13 && kernel <= 15) || kernel >= 20) ? TH_PC_CHEB : (kernel == 19 ? TH_PC_MG : TH_PC_JACOBI);
   o.cheb_degree = 5;  // one chunk of four fused steps
   o.precision = (kernel >= 5 && kernel <= 7) ? TH_PREC_FP64
                 : ((kernel >= 16 && kernel <= 18) ? TH_PREC_ADAPTIVE : TH_PREC_MIXED_IR);
@@ -1565,6 +1633,10 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
   auto launch = [&]() -> th_status {
     const bool uni = g->uniform && kernel < 9;  // ids 9..12: the per-face variants
     if (kernel == 19) return mg_vcycle(g, g->r32, g->zc32[0], s);
+    if (kernel >= 20) {  // per-face fused chunk: 4, 2 or 3 steps, inner chunk
+      const Plan::Chunk c{kernel == 20 ? 4 : (kernel == 21 ? 2 : 3), 1, 0, 1, 2, 3};
+      return tbf_chunk(P, V, s, c, false);
+    }
     if (kernel == 16) {
       k_ad_cheb<true><<<P.gb, P.tb, 0, s>>>(P.d, g->ctl, P.qd, P.qd_sinv, g->r32, g->zc32[0], g->zc32[1], g->zc32[2],
                                             g->invd32, c1, c2);
@@ -1649,9 +1721,9 @@ extern "C" th_status thermal_kernel_time(thermal_grid* g, int kernel, int reps, 
                                                      W.invd, 0.5, 0.5, g->partials, g->partials_stride, g->counters);
         break;
       default:
-        if (uni && P.v4) {
+        if (P.v4) {
           launch_residual_v4<float>(P, s, P.transient ? g->thn_hi : nullptr, P.transient ? g->thn_lo : nullptr, 0,
-                                    -1, ResidInit{});
+                                    -1, ResidInit{}, uni);
           break;
         }
         TH_UNI(uni, k_residual_df<float, U><<<P.gb, P.tb, 0, s>>>(

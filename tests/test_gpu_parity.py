@@ -305,6 +305,42 @@ def test_fused_chebyshev_equals_stepwise(k, dt, mk):
         assert (zf - z1).abs().max().item() <= 1e-6 * scale, fuse
 
 
+@pytest.mark.parametrize("k", [2, 5, 8, 12])
+@pytest.mark.parametrize("dt", [0.0, 1e-4])
+@pytest.mark.parametrize("mk", ["c2", "c1"])
+def test_fused_chebyshev_per_face_equals_stepwise(k, dt, mk):
+    """Fused chunks on per-face arrays (a per-cell conductivity map; 32 x 24 tiles with
+    the faces staged beside the vectors) compute the same polynomial as one launch per
+    step: ragged tiles on both axes, 8 layers and 4 layers (zero-padded)."""
+    st = STACKS[mk]()
+    nx, ny = 76, 37
+    g = grid_of(nx, ny, st)
+    g.set_conductivity_map(cuda(_kmap(st, nx, ny, 21)))
+    r = cuda(ti.random_vector(nx * ny * st.L, 5).astype(np.float32))
+    z1 = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=1)
+    scale = z1.abs().max().item()
+    for fuse in (0, 2, 3, 4):
+        zf = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=fuse)
+        assert (zf - z1).abs().max().item() <= 1e-6 * scale, fuse
+
+
+def test_fused_chebyshev_per_face_matches_oracle():
+    """The per-face fused preconditioner against the oracle's Chebyshev algorithm on
+    the assembled per-cell-conductivity matrix (same spectral interval)."""
+    st = ti.stack_c2()
+    nx, ny, dt, k = 44, 29, 1e-4, 12
+    kc = _kmap(st, nx, ny, 22)
+    A = disc.assemble(nx, ny, st, dt=dt, k_cell=kc)
+    g = grid_of(nx, ny, st)
+    g.set_conductivity_map(cuda(kc))
+    r = ti.random_vector(A.shape[0], 9).astype(np.float32)
+    z = g.precond(cuda(r), dt, precond="cheb", cheb_degree=k).cpu().double().numpy()
+    _, _, lmin, lmax = g.spectral_bounds(dt)
+    D = A.diagonal()
+    ref = krylov.chebyshev(lambda v: (A @ v) / D, r.astype(np.float64) / D, lmin, lmax, k)
+    np.testing.assert_allclose(z, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
+
+
 # ----------------------------------------------------------------- A5/A6: steady solves
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_bf16"])
@@ -643,6 +679,40 @@ def test_batched_initial_guess_and_repeat():
     for a, b, s in zip(first, Ts, stats):
         assert s["status"] == 0 and s["outer_it"] <= 1
         assert (a - b).abs().max().item() <= 1e-8 * (a - 45.0).abs().max().item()
+
+
+def test_batched_rejects_a_repeated_grid_or_output():
+    """Through the C ABI directly (the binding rejects this before the call): one grid
+    handle twice, or one output buffer twice, is TH_EINVAL and nothing is solved;
+    separate grids on one shared power map solve normally."""
+    import ctypes as C
+    from paper_2606_17850_gb300 import _lib, solve_batched
+    lib = _lib.load()
+    inst = ti.c4_instances(n=1, scale=8)[0]
+    g1, g2 = grid_of(inst.nx, inst.ny, inst.stack), grid_of(inst.nx, inst.ny, inst.stack)
+    P = cuda(inst.power)
+    T1 = torch.full((inst.n,), -1.0, dtype=torch.float64, device="cuda")
+    T2 = T1.clone()
+    o = _lib.default_opts(tol_rel=1e-10)
+    stats = (_lib.SolveStats * 2)()
+    pdt = _lib.TH_F32 if P.dtype == torch.float32 else _lib.TH_F64
+
+    def call(grids, outs):
+        gh = (C.c_void_p * 2)(*[g.handle.value for g in grids])
+        ph = (C.c_void_p * 2)(P.data_ptr(), P.data_ptr())
+        th = (C.c_void_p * 2)(*[t.data_ptr() for t in outs])
+        return lib.thermal_solve_batched(gh, 2, ph, pdt, th, C.byref(o), stats, None)
+
+    assert call([g1, g1], [T1, T2]) == _lib.TH_EINVAL
+    assert b"same grid" in lib.thermal_last_error()
+    assert call([g1, g2], [T1, T1]) == _lib.TH_EINVAL
+    torch.cuda.synchronize()
+    assert (T1 == -1.0).all() and (T2 == -1.0).all()
+    st = solve_batched([g1, g2], [P, P], [T1, T2], tol_rel=1e-10)
+    T_ref = osolve.steady(inst.nx, inst.ny, inst.stack, inst.power.astype(np.float64))
+    for T, s in zip((T1, T2), st):
+        assert s["status"] == 0
+        assert osolve.rise_relative_error(T.cpu().numpy(), T_ref, inst.stack.t_amb) <= 1e-6
 
 
 # ----------------------------------------------------------------- errors
