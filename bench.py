@@ -82,9 +82,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=20, help="Chebyshev degree k (SpMVs per application)")
-    ap.add_argument("--guess", type=int, default=2,
+    ap.add_argument("--guess", type=int, default=3,
                     help="transient initial guess: 0 previous step (the paper's warm start), "
-                         "1 linear extrapolation from the two previous steps, 2 quadratic from three")
+                         "1 linear extrapolation from the two previous steps, 2 quadratic from three, "
+                         "3 cubic from four (orders capped by the steps since the last power-map switch)")
     ap.add_argument("--inner-tol", type=float, default=1e-5,
                     help="smallest residual reduction an FP32 inner solve is asked for")
     ap.add_argument("--fuse", type=int, default=0,
@@ -205,7 +206,9 @@ def config_dict(degree, polled=False, guess=2, fuse=0):
             "preconditioner": f"Chebyshev degree {degree} on the Jacobi-scaled operator (Lanczos bounds), "
                               f"up to {fuse or 4} steps per launch (temporal blocking)",
             "initial_guess": {0: "previous step T_n", 1: "linear extrapolation 2 T_n - T_(n-1)",
-                              2: "quadratic extrapolation 3 T_n - 3 T_(n-1) + T_(n-2)"}[guess],
+                              2: "quadratic extrapolation 3 T_n - 3 T_(n-1) + T_(n-2)",
+                              3: "cubic extrapolation 4 T_n - 6 T_(n-1) + 4 T_(n-2) - T_(n-3)"}[guess]
+                             + (", order capped by the steps since the last power-map switch" if guess >= 2 else ""),
             "loop": ("host-polled launch chunks (profiling mode)" if polled else
                      "CUDA graph, conditional WHILE nodes (no host sync inside the 100 steps)"),
             "l2": "inputs larger than L2 (about 1 GB resident vs 129 MB L2); no flush"}
@@ -619,8 +622,8 @@ def batched_section(args):
             torch.distributed.barrier()
         ms, stats = _event_ms(lambda: solve_batched(grids, powers, Ts, **o), reps=max(1, args.steps))
         timing["ms"] = ms
-        res = {i: {"status": s["status"], "rel_res": s["rel_res"], "inner_it": s["inner_it"]}
-               for i, s in zip(idx, stats)}
+        res = {i: {"status": s["status"], "rel_res": s["rel_res"], "inner_it": s["inner_it"],
+                   "tile_rows": s["tile_rows"], "tile_layers": s["tile_layers"]} for i, s in zip(idx, stats)}
         for g in grids:
             g.close()
         return res
@@ -634,6 +637,9 @@ def batched_section(args):
             "status": max(s["status"] for s in st), "inner_it_sum": sum(s["inner_it"] for s in st),
             "max_inner_it": max(s["inner_it"] for s in st), "ranks": world,
             "instances_per_rank": [len(shard(len(insts), r, world)) for r in range(world)],
+            "tiles": {f"{insts[i].nx}x{insts[i].ny}x{insts[i].stack.L}":
+                      f"128 x {8 * st[i]['tile_rows']} columns x {st[i]['tile_layers']} layers"
+                      for i in range(len(insts))},
             "launch": "one cooperative persistent kernel per rank for its share of the 64 instances"}
 
 

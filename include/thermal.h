@@ -99,8 +99,10 @@ typedef struct thermal_solve_opts {
                        /* instance after another through the single-grid solver (0)          */
   int guess;           /* transient initial guess: 0 the previous step T_n (the paper's warm  */
                        /* start); inside a step loop 1 linear extrapolation 2 T_n - T_{n-1},  */
-                       /* 2 quadratic 3 T_n - 3 T_{n-1} + T_{n-2} (mixed path with nx % 4 == 0; */
-                       /* linear elsewhere); lower orders while the history is short (0)     */
+                       /* 2 quadratic 3 T_n - 3 T_{n-1} + T_{n-2}, 3 cubic 4 T_n - 6 T_{n-1} + */
+                       /* 4 T_{n-2} - T_{n-3} (2, 3: mixed path with nx % 4 == 0, linear       */
+                       /* elsewhere); the order is lowered while the history is short and to */
+                       /* the steps taken since the power map last switched (0)               */
   int cheb_fuse;       /* Chebyshev steps per launch (temporal blocking in shared memory) on  */
                        /* grids with nx % 4 == 0: layer table up to 12 layers, per-face arrays */
                        /* up to 8 (not with the BF16 coefficients): 0 auto (4), 1 one step   */
@@ -127,7 +129,10 @@ typedef struct thermal_solve_stats {
   double lam_max;
   int steps;           /* time steps taken (transient calls)                                  */
   int stage_switches;  /* ADAPTIVE: early-to-late switches (hot restarts), summed over steps  */
-  int reserved[6];
+  int tile_rows;       /* thermal_solve_batched, one persistent launch: the tile shape the     */
+  int tile_layers;     /* autotuner chose for this instance's size class, blocks of 128 x 8    */
+                       /* columns per tile and layers per tile                                */
+  int reserved[4];
 } thermal_solve_stats;
 
 /* ------------------------------------------------------------------ misc */

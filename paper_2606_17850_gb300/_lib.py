@@ -55,7 +55,9 @@ class SolveStats(C.Structure):
         ("lam_max", C.c_double),
         ("steps", C.c_int),
         ("stage_switches", C.c_int),
-        ("reserved", C.c_int * 6),
+        ("tile_rows", C.c_int),
+        ("tile_layers", C.c_int),
+        ("reserved", C.c_int * 4),
     ]
 
     def as_dict(self):

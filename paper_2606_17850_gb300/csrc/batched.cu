@@ -24,7 +24,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -35,6 +38,9 @@ namespace cg = cooperative_groups;
 struct BInst {
   Dims d;
   int tile0, ntiles, tbx, uni;
+  int rows;  // 8-row blocks per tile   } the tile shape the autotuner chose
+  int zl;    // layers per tile           } for this instance's size class
+  int tby;   // tiles along y
   Faces32 f32;
   Faces64 f64;
   const LayerTab* tab;
@@ -90,14 +96,15 @@ __device__ bool any_active(const BArgs& A, int what) {
   return r;
 }
 
-__device__ __forceinline__ Walk4 tile_walk(const BInst& I, int t) {
+// row block rb (0 <= rb < I.rows) of tile t: 128 x 8 columns, layers [zs, ze)
+__device__ __forceinline__ Walk4 tile_walk(const BInst& I, int t, int rb) {
   const int loc = t - I.tile0;
-  const int bx = loc % I.tbx, by = loc / I.tbx;
+  const int bx = loc % I.tbx, by = (loc / I.tbx) % I.tby, bz = loc / (I.tbx * I.tby);
   Walk4 w;
   w.x0 = 4 * (bx * TH_BX + threadIdx.x);
-  w.y = by * TH_BY4 + threadIdx.y;
-  w.zs = 0;
-  w.ze = I.d.L;
+  w.y = (by * I.rows + rb) * TH_BY4 + threadIdx.y;
+  w.zs = bz * I.zl;
+  w.ze = min(w.zs + I.zl, I.d.L);
   w.valid = (w.x0 < I.d.nx) && (w.y < I.d.ny);
   w.b0 = (long long)w.x0 + (long long)I.d.nx * w.y;
   return w;
@@ -105,32 +112,42 @@ __device__ __forceinline__ Walk4 tile_walk(const BInst& I, int t) {
 
 // One phase over the active instances' tiles: body(I, C, w, v) with the tile's
 // instance I and loop scalars C in shared memory fills NQ per-thread partial sums,
-// reduced per tile into partials[q][t].
+// reduced per tile into partials[q][t].  The loop scalars change only in finish
+// steps (between grid barriers), so within a phase the descriptor and scalars of an
+// instance are copied once and kept while the block's next tiles belong to the same
+// instance.
 template <int NQ, class F>
 __device__ void phase(const BArgs& A, int what, F body) {
   __shared__ BInst si;
   __shared__ BCtl sc;
   __shared__ double sm[2][32];
   const int tid = thread_linear_id(), nw = (block_threads() + 31) >> 5;
+  int cur = -1;
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
     const int ii = __ldg(A.tile_inst + t);
-    const int* src = reinterpret_cast<const int*>(A.inst + ii);
-    int* dst = reinterpret_cast<int*>(&si);
-    for (int q = tid; q < (int)(sizeof(BInst) / 4); q += block_threads()) dst[q] = __ldg(src + q);
-    if (tid == 0) {
-      const Ctl* c = A.inst[ii].ctl;
-      sc.act = active(c, what);
-      sc.first = __ldcg(&c->first);
-      sc.alpha = __ldcg(&c->alpha_f);
-      sc.beta = __ldcg(&c->beta_f);
-      sc.rscale = __ldcg(&c->rscale_f);
-      sc.rnorm = __ldcg(&c->rnorm);
+    if (ii != cur) {
+      __syncthreads();  // the previous instance's descriptor and scalars are no longer read
+      const int* src = reinterpret_cast<const int*>(A.inst + ii);
+      int* dst = reinterpret_cast<int*>(&si);
+      for (int q = tid; q < (int)(sizeof(BInst) / 4); q += block_threads()) dst[q] = __ldg(src + q);
+      if (tid == 0) {
+        const Ctl* c = A.inst[ii].ctl;
+        sc.act = active(c, what);
+        sc.first = __ldcg(&c->first);
+        sc.alpha = __ldcg(&c->alpha_f);
+        sc.beta = __ldcg(&c->beta_f);
+        sc.rscale = __ldcg(&c->rscale_f);
+        sc.rnorm = __ldcg(&c->rnorm);
+      }
+      __syncthreads();
+      cur = ii;
     }
-    __syncthreads();
     if (sc.act) {
-      const Walk4 w = tile_walk(si, t);
       float v[NQ > 0 ? NQ : 1] = {};
-      if (w.valid) body(si, sc, w, v);
+      for (int rb = 0; rb < si.rows; ++rb) {
+        const Walk4 w = tile_walk(si, t, rb);
+        if (w.valid) body(si, sc, w, v);
+      }
       if (NQ > 0) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -146,10 +163,11 @@ __device__ void phase(const BArgs& A, int what, F body) {
             A.partials[(size_t)q * A.ntiles + t] = s;
           }
         }
+        __syncthreads();  // sm is rewritten by the next tile's reduction
       }
     }
-    __syncthreads();  // descriptor and scalars are reused by the next tile
   }
+  __syncthreads();  // the next phase's blocks may reuse this block's shared memory
 }
 
 // One block per active instance sums its tiles' partials (fixed order) and runs fin.
@@ -186,7 +204,7 @@ __device__ void finish(const BArgs& A, int what, F fin) {
 // the layers of a tile column segment: f(i) for i = index of its first cell in each layer
 template <class F>
 __device__ __forceinline__ void for_layers(const BInst& I, const Walk4& w, F f) {
-  for (int z = 0; z < I.d.L; ++z) f(w.b0 + (long long)z * I.d.pxy, z);
+  for (int z = w.zs; z < w.ze; ++z) f(w.b0 + (long long)z * I.d.pxy, z);
 }
 
 // FP64 refinement residual r = P - A theta of 4 cells per layer, and ||r||^2, ||P||^2
@@ -436,74 +454,39 @@ static th_status sequential(thermal_grid* const* grids, int n, const void* const
   return TH_OK;
 }
 
-static th_status persistent(thermal_grid* const* grids, int n, const void* const* power, int power_dtype,
-                            double* const* T, const thermal_solve_opts* opts, thermal_solve_stats* stats,
-                            cudaStream_t s) {
-  std::vector<BInst> hi(n);
+// Control block of one instance at the start of a batched solve.
+static Ctl batch_ctl(const thermal_solve_opts* o, double tol, int max_outer, int max_inner) {
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  c.tol_rel = tol;
+  c.inner_tol = o->inner_tol;
+  c.inner_rel = o->inner_tol;
+  c.max_outer = max_outer;
+  c.max_inner = max_inner;
+  c.n_steps = 1;
+  c.steps_per_map = 1;
+  c.n_maps = 1;
+  c.rel_res = 1.0;
+  return c;
+}
+
+// One cooperative launch of the persistent kernel over the instances hi (tile lists
+// built from each instance's row blocks per tile); *ms = its duration (CUDA events).
+static th_status launch_batch(std::vector<BInst>& hi, const std::vector<thermal_grid*>& gs, const Ctl* ctl0,
+                              int power_dtype, const thermal_solve_opts* opts, int k, int max_sweeps,
+                              cudaStream_t s, float* ms) {
+  const int n = (int)hi.size();
   std::vector<int> tile_inst;
-  std::vector<std::vector<float>> c1s(n), c2s(n);
-  std::vector<double> lmins(n), lmaxs(n);
-  const int k = opts->precond == TH_PC_CHEB ? opts->cheb_degree : 1;
   int ntiles = 0;
   for (int i = 0; i < n; ++i) {
-    thermal_grid* g = grids[i];
-    TH_TRY(grid_ensure_tab(g, 0.0, s));
-    TH_TRY(grid_ensure_workspace(g, false, s));
-    float inv_theta = 1.0f;
-    if (opts->precond == TH_PC_CHEB)
-      TH_TRY(solver_cheb_coeffs(g, 0.0, opts, c1s[i], c2s[i], &inv_theta, &lmins[i], &lmaxs[i], s));
     BInst& I = hi[i];
-    I = BInst{};
-    I.d = grid_dims(g);
-    I.tbx = (g->nx + 4 * TH_BX - 1) / (4 * TH_BX);
+    I.tbx = (I.d.nx + 4 * TH_BX - 1) / (4 * TH_BX);
+    I.tby = (I.d.ny + TH_BY4 * I.rows - 1) / (TH_BY4 * I.rows);
     I.tile0 = ntiles;
-    I.ntiles = I.tbx * ((g->ny + TH_BY4 - 1) / TH_BY4);
-    I.uni = g->uniform ? 1 : 0;
+    I.ntiles = I.tbx * I.tby * ((I.d.L + I.zl - 1) / I.zl);
     ntiles += I.ntiles;
     for (int t = 0; t < I.ntiles; ++t) tile_inst.push_back(i);
-    I.f32 = g->f32;
-    I.f64 = g->f64;
-    I.tab = g->tab;
-    I.invd = g->invd32;
-    I.P = power[i];
-    I.T_in = opts->use_guess ? T[i] : nullptr;
-    I.T_out = T[i];
-    I.t_amb = g->t_amb;
-    I.theta = g->theta[0];
-    I.r = g->r32;
-    I.dv = g->d32;
-    I.p[0] = g->p32[0];
-    I.p[1] = g->p32[1];
-    I.mu = g->mu32;
-    for (int q = 0; q < 3; ++q) I.zc[q] = g->zc32[q];
-    I.inv_theta = inv_theta;
-    I.ctl = g->ctl;
-  }
-  // per-instance Chebyshev coefficients and control blocks
-  DevArr<float> coef;
-  TH_TRY(coef.alloc((size_t)2 * n * k));
-  std::vector<float> hc((size_t)2 * n * k, 0.0f);
-  for (int i = 0; i < n; ++i)
-    for (int m = 0; m < k && opts->precond == TH_PC_CHEB; ++m) {
-      hc[(size_t)(2 * i) * k + m] = c1s[i][m];
-      hc[(size_t)(2 * i + 1) * k + m] = c2s[i][m];
-    }
-  TH_CUDA(cudaMemcpyAsync(coef.p, hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
-  for (int i = 0; i < n; ++i) {
-    hi[i].c1 = coef.p + (size_t)(2 * i) * k;
-    hi[i].c2 = coef.p + (size_t)(2 * i + 1) * k;
-    Ctl c;
-    std::memset(&c, 0, sizeof(c));
-    c.tol_rel = opts->tol_rel;
-    c.inner_tol = opts->inner_tol;
-    c.inner_rel = opts->inner_tol;
-    c.max_outer = opts->max_outer;
-    c.max_inner = opts->max_inner;
-    c.n_steps = 1;
-    c.steps_per_map = 1;
-    c.n_maps = 1;
-    c.rel_res = 1.0;
-    TH_CUDA(cudaMemcpyAsync(grids[i]->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(gs[i]->ctl, &ctl0[i], sizeof(Ctl), cudaMemcpyHostToDevice, s));
   }
   DevArr<BInst> dinst;
   DevArr<int> dtiles;
@@ -522,7 +505,7 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
   A.pc = opts->precond;
   A.k = k;
   A.scaled = opts->cheb_scaled ? 1 : 0;
-  A.max_sweeps = std::max(1, opts->max_outer) * std::max(1, opts->max_inner);
+  A.max_sweeps = max_sweeps;
   // co-resident grid: every block must be resident for the grid-wide barriers
   int dev = 0, sms = 0, per_sm = 0;
   TH_CUDA(cudaGetDevice(&dev));
@@ -540,8 +523,159 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
   TH_CUDA(cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(TH_BX, TH_BY4), args, 0, s));
   TH_CUDA(cudaEventRecord(e1, s));
   TH_CUDA(cudaStreamSynchronize(s));
+  TH_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  return TH_OK;
+}
+
+// Tile autotuner: the tile shape of each size class (nx, ny, layers, coefficient
+// source), chosen once per process by timing a fixed amount of work (one refinement
+// step with three inner iterations, from theta = 0) on the batch's instances of the
+// class, launched together as in the real solve, with each candidate: row blocks per tile (1 or 2 blocks of 128 x 8 columns) times
+// layers per tile (all, half, a quarter).  More rows or layers per tile mean fewer
+// tiles and fewer per-tile descriptor copies; fewer layers per thread mean more
+// threads with loads in flight (the z-walk keeps the layer below and above in
+// registers, so a layer chunk re-reads one plane at each end).
+struct BClass {
+  int nx, ny, L, uni;
+  bool operator<(const BClass& o) const {
+    return std::tie(nx, ny, L, uni) < std::tie(o.nx, o.ny, o.L, o.uni);
+  }
+};
+struct BShape { int rows, zc; };
+static std::mutex g_rows_mu;
+static std::map<BClass, BShape> g_rows;
+
+static th_status tune_rows(std::vector<BInst>& hi, const std::vector<thermal_grid*>& gs, int power_dtype,
+                           const thermal_solve_opts* opts, int k, cudaStream_t s) {
+  // instances of each size class in this batch
+  std::map<BClass, std::vector<size_t>> classes;
+  for (size_t i = 0; i < hi.size(); ++i)
+    classes[BClass{hi[i].d.nx, hi[i].d.ny, hi[i].d.L, hi[i].uni}].push_back(i);
+  for (auto& kv : classes) {
+    const BClass& key = kv.first;
+    const std::vector<size_t>& members = kv.second;
+    BShape chosen{1, key.L};
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lk(g_rows_mu);
+      auto it = g_rows.find(key);
+      if (it != g_rows.end()) {
+        chosen = it->second;
+        cached = true;
+      }
+    }
+    if (!cached) {
+      const int L = key.L;
+      std::vector<BShape> cand;
+      for (int r : {1, 2})
+        for (int zl : {L, (L + 1) / 2, (L + 3) / 4}) {
+          if (r > 1 && (key.ny + TH_BY4 - 1) / TH_BY4 < r) continue;  // taller than the grid
+          bool dup = false;
+          for (const BShape& c : cand) dup = dup || (c.rows == r && c.zc == zl);
+          if (!dup) cand.push_back(BShape{r, zl});
+        }
+      // the class's instances of this batch together, as in the real launch; their
+      // outputs go to each grid's scratch (the caller's T is not touched)
+      std::vector<BInst> sub;
+      std::vector<thermal_grid*> sg;
+      for (size_t i : members) {
+        thermal_grid* g = gs[i];
+        if (!g->stage_T) {
+          if (cudaMalloc((void**)&g->stage_T, sizeof(double) * (size_t)g->n) != cudaSuccess) {
+            cudaGetLastError();
+            return th_fail(TH_ENOMEM, "staging allocation failed");
+          }
+        }
+        BInst I = hi[i];
+        I.T_in = nullptr;
+        I.T_out = g->stage_T;
+        sub.push_back(I);
+        sg.push_back(g);
+      }
+      const std::vector<Ctl> c0(sub.size(), batch_ctl(opts, 0.0, 1, 3));
+      float best = 1e30f;
+      for (const BShape& c : cand) {
+        for (BInst& I : sub) {
+          I.rows = c.rows;
+          I.zl = c.zc;
+        }
+        float ms = 0.f;
+        TH_TRY(launch_batch(sub, sg, c0.data(), power_dtype, opts, k, 3, s, &ms));  // warm-up
+        TH_TRY(launch_batch(sub, sg, c0.data(), power_dtype, opts, k, 3, s, &ms));
+        if (ms < best) {
+          best = ms;
+          chosen = c;
+        }
+      }
+      std::lock_guard<std::mutex> lk(g_rows_mu);
+      g_rows[key] = chosen;
+    }
+    for (size_t i : members) {
+      hi[i].rows = chosen.rows;
+      hi[i].zl = chosen.zc;
+    }
+  }
+  return TH_OK;
+}
+
+static th_status persistent(thermal_grid* const* grids, int n, const void* const* power, int power_dtype,
+                            double* const* T, const thermal_solve_opts* opts, thermal_solve_stats* stats,
+                            cudaStream_t s) {
+  std::vector<BInst> hi(n);
+  std::vector<thermal_grid*> gs(grids, grids + n);
+  std::vector<std::vector<float>> c1s(n), c2s(n);
+  std::vector<double> lmins(n), lmaxs(n);
+  const int k = opts->precond == TH_PC_CHEB ? opts->cheb_degree : 1;
+  for (int i = 0; i < n; ++i) {
+    thermal_grid* g = grids[i];
+    TH_TRY(grid_ensure_tab(g, 0.0, s));
+    TH_TRY(grid_ensure_workspace(g, false, s));
+    float inv_theta = 1.0f;
+    if (opts->precond == TH_PC_CHEB)
+      TH_TRY(solver_cheb_coeffs(g, 0.0, opts, c1s[i], c2s[i], &inv_theta, &lmins[i], &lmaxs[i], s));
+    BInst& I = hi[i];
+    I = BInst{};
+    I.d = grid_dims(g);
+    I.uni = g->uniform ? 1 : 0;
+    I.rows = 1;
+    I.zl = I.d.L;
+    I.f32 = g->f32;
+    I.f64 = g->f64;
+    I.tab = g->tab;
+    I.invd = g->invd32;
+    I.P = power[i];
+    I.T_in = opts->use_guess ? T[i] : nullptr;
+    I.T_out = T[i];
+    I.t_amb = g->t_amb;
+    I.theta = g->theta[0];
+    I.r = g->r32;
+    I.dv = g->d32;
+    I.p[0] = g->p32[0];
+    I.p[1] = g->p32[1];
+    I.mu = g->mu32;
+    for (int q = 0; q < 3; ++q) I.zc[q] = g->zc32[q];
+    I.inv_theta = inv_theta;
+    I.ctl = g->ctl;
+  }
+  // per-instance Chebyshev coefficients
+  DevArr<float> coef;
+  TH_TRY(coef.alloc((size_t)2 * n * k));
+  std::vector<float> hc((size_t)2 * n * k, 0.0f);
+  for (int i = 0; i < n; ++i)
+    for (int m = 0; m < k && opts->precond == TH_PC_CHEB; ++m) {
+      hc[(size_t)(2 * i) * k + m] = c1s[i][m];
+      hc[(size_t)(2 * i + 1) * k + m] = c2s[i][m];
+    }
+  TH_CUDA(cudaMemcpyAsync(coef.p, hc.data(), hc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < n; ++i) {
+    hi[i].c1 = coef.p + (size_t)(2 * i) * k;
+    hi[i].c2 = coef.p + (size_t)(2 * i + 1) * k;
+  }
+  TH_TRY(tune_rows(hi, gs, power_dtype, opts, k, s));
+  std::vector<Ctl> c0(n, batch_ctl(opts, opts->tol_rel, opts->max_outer, opts->max_inner));
   float ms = 0.f;
-  TH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  TH_TRY(launch_batch(hi, gs, c0.data(), power_dtype, opts, k,
+                      std::max(1, opts->max_outer) * std::max(1, opts->max_inner), s, &ms));
   th_status first_bad = TH_OK;
   for (int i = 0; i < n; ++i) {
     Ctl h;
@@ -558,6 +692,8 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
       stats[i].t_solve_ms = ms;
       stats[i].lam_min = lmins[i];
       stats[i].lam_max = lmaxs[i];
+      stats[i].tile_rows = hi[i].rows;
+      stats[i].tile_layers = hi[i].zl;
     }
     if (st != TH_OK && first_bad == TH_OK) first_bad = st;
   }

@@ -280,7 +280,7 @@ thermal_grid::~thermal_grid() {
   dfree(f32.gx); dfree(f32.gy); dfree(f32.gz);
   dfree(f32lo.gx); dfree(f32lo.gy); dfree(f32lo.gz);
   dfree(th_hi); dfree(th_lo); dfree(thn_hi); dfree(thn_lo);
-  dfree(thm_hi); dfree(thm_lo); dfree(thm64); dfree(thm2_hi); dfree(thm2_lo);
+  dfree(thm_hi); dfree(thm_lo); dfree(thm64); dfree(thm2_hi); dfree(thm2_lo); dfree(thm3_hi); dfree(thm3_lo);
   dfree(f16.gx); dfree(f16.gy); dfree(f16.gz);
   dfree(tab); dfree(invd32); dfree(invd64); dfree(isqd32); dfree(zl_c); dfree(zl_m);
   dfree(qd4); dfree(qd5); dfree(qd6); dfree(qd7); dfree(diag32); dfree(diag64);

@@ -120,6 +120,7 @@ struct thermal_grid {
   // theta_{n-1} for the extrapolated transient guess (allocated on first use)
   float *thm_hi = nullptr, *thm_lo = nullptr;
   float *thm2_hi = nullptr, *thm2_lo = nullptr;  // theta_{n-2} (quadratic extrapolation)
+  float *thm3_hi = nullptr, *thm3_lo = nullptr;  // theta_{n-3} (cubic extrapolation)
   double* thm64 = nullptr;
   double* partials = nullptr;   // reduction partials
   int partials_stride = 0;

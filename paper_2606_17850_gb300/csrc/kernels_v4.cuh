@@ -518,31 +518,53 @@ static __global__ void __launch_bounds__(256)
   st4(th_lo + i, make_float4(gl[0], gl[1], gl[2], gl[3]));
 }
 
-// Start of a step with the quadratic extrapolated guess: theta <- 3 theta_n -
-// 3 theta_{n-1} + theta_{n-2} (2 theta_n - theta_{n-1} on the second step, theta_n on
-// the first), history shifted; theta holds the previous step's solution on entry.
+// Start of a time step with an extrapolated guess (double-float, 4 cells per
+// thread): theta <- the polynomial extrapolation of order q through theta_n and the
+// history, and the history moves back by one step (thm <- theta_n, thm2 <- thm,
+// thm3 <- thm2).  q = min(ORD, steps taken, steps taken since the power map last
+// switched): the history before a switch follows another forcing, and extrapolating
+// across the switch gives a worse start than a lower order (measured with the oracle
+// on the 100-step workload shape).
+//   q = 1: 2 t_n - t_{n-1};  q = 2: 3 t_n - 3 t_{n-1} + t_{n-2};
+//   q = 3: 4 t_n - 6 t_{n-1} + 4 t_{n-2} - t_{n-3}.
+template <int ORD>
 static __global__ void __launch_bounds__(256)
-    k_step_extrap2_df_v4(long long n4, const Ctl* ctl, float* th_hi, float* th_lo, float* thm_hi, float* thm_lo,
-                         float* thm2_hi, float* thm2_lo) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n4) return;
+    k_step_extrapq_df_v4(long long n4, const Ctl* ctl, float* th_hi, float* th_lo, float* thm_hi, float* thm_lo,
+                         float* thm2_hi, float* thm2_lo, float* thm3_hi, float* thm3_lo) {
+  const long long q4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q4 >= n4) return;
   const int step = ld_int(&ctl->step);
-  const long long i = 4 * q;
+  const int spm = ld_int(&ctl->steps_per_map), nmaps = ld_int(&ctl->n_maps);
+  const int since = (nmaps > 1 && spm > 0) ? step % spm : step;
+  const int q = min(ORD, min(step, since));
+  const long long i = 4 * q4;
   const float4 ch = ld4(th_hi + i), cl = ld4(th_lo + i), ph = ld4(thm_hi + i), pl = ld4(thm_lo + i);
   const float4 qh = ld4(thm2_hi + i), ql = ld4(thm2_lo + i);
+  float4 rh = z4(), rl = z4();
+  if (ORD >= 3) {
+    rh = ld4(thm3_hi + i);
+    rl = ld4(thm3_lo + i);
+  }
   float gh[4], gl[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const df cur = df_make(cmp(ch, k), cmp(cl, k));
     const df prev = df_make(cmp(ph, k), cmp(pl, k));
     df g = cur;
-    if (step == 1) g = df_sub(df_add(cur, cur), prev);
-    if (step >= 2) {
-      const df prev2 = df_make(cmp(qh, k), cmp(ql, k));
-      g = df_add(df_mul_f(df_sub(cur, prev), 3.0f), prev2);
+    if (q == 1) g = df_sub(df_add(cur, cur), prev);
+    if (q == 2) g = df_add(df_mul_f(df_sub(cur, prev), 3.0f), df_make(cmp(qh, k), cmp(ql, k)));
+    if (ORD >= 3 && q == 3) {
+      // 4 (t_n - t_{n-1}) - 2 (t_{n-1} - t_{n-2}) + (t_{n-2} - t_{n-3}) + t_{n-2}
+      const df p2 = df_make(cmp(qh, k), cmp(ql, k)), p3 = df_make(cmp(rh, k), cmp(rl, k));
+      g = df_add(df_sub(df_mul_f(df_sub(cur, prev), 4.0f), df_mul_f(df_sub(prev, p2), 2.0f)),
+                 df_add(df_sub(p2, p3), p2));
     }
     gh[k] = g.hi;
     gl[k] = g.lo;
+  }
+  if (ORD >= 3) {
+    st4(thm3_hi + i, qh);
+    st4(thm3_lo + i, ql);
   }
   st4(thm2_hi + i, ph);
   st4(thm2_lo + i, pl);

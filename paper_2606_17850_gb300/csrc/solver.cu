@@ -48,7 +48,7 @@ struct Plan {
   int pc_spmv = 0;          // stencil applications per preconditioner application
   // vectorised FP32 kernels (nx % 4 == 0): grid of the z-walk kernels and the update
   bool extrap = false;  // extrapolated initial guess in a step loop
-  int extrap_order = 1;  // 1 linear, 2 quadratic
+  int extrap_order = 1;  // 1 linear, 2 quadratic, 3 cubic
   bool uni = false;     // layer-table coefficients (grid with one conductivity per layer)
   // temporal blocking of the FP32 Chebyshev tail: chunks of fused steps over a
   // pool of four FP32 buffers {zc0, zc1, zc2, mu} (indices 0..3)
@@ -1038,9 +1038,12 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
     if (theta64(P))
       k_step_extrap64<<<nb1(n), 256, 0, st>>>(n, g->theta[0], g->theta_n, g->thm64);
     else
-      if (P.extrap_order == 2)
-        k_step_extrap2_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->ctl, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo,
-                                                     g->thm2_hi, g->thm2_lo);
+      if (P.extrap_order == 3)
+        k_step_extrapq_df_v4<3><<<P.nbu4, 256, 0, st>>>(n / 4, g->ctl, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo,
+                                                        g->thm2_hi, g->thm2_lo, g->thm3_hi, g->thm3_lo);
+      else if (P.extrap_order == 2)
+        k_step_extrapq_df_v4<2><<<P.nbu4, 256, 0, st>>>(n / 4, g->ctl, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo,
+                                                        g->thm2_hi, g->thm2_lo, nullptr, nullptr);
       else if (P.v4)
         k_step_extrap_df_v4<<<P.nbu4, 256, 0, st>>>(n / 4, g->th_hi, g->th_lo, g->thm_hi, g->thm_lo);
       else
@@ -1396,15 +1399,15 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
   Plan P;
   const bool transient = (kind == KIND_STEP || kind == KIND_RUN);
-  if (o->guess < 0 || o->guess > 2) return th_fail(TH_EINVAL, "guess must be 0, 1 or 2");
+  if (o->guess < 0 || o->guess > 3) return th_fail(TH_EINVAL, "guess must be 0, 1, 2 or 3");
   // with h = 0 every face of G is adiabatic: G 1 = 0 and the steady system is singular
   if (!transient && !(g->h > 0.0))
     return th_fail(TH_EINVAL, "a steady solve needs h > 0 (h = 0 leaves G singular)");
   const double toff = (kind == KIND_ADJ) ? 0.0 : g->t_amb;  // the adjoint state has no offset
   TH_TRY(make_plan(g, transient ? dt : 0.0, o, pdtype, transient, P, s));
   P.extrap = (kind == KIND_RUN && o->guess >= 1);
-  // quadratic extrapolation: the vectorised double-float path only (linear elsewhere)
-  P.extrap_order = (o->guess == 2 && P.v4 && o->precision != TH_PREC_FP64 && !P.ad) ? 2 : 1;
+  // quadratic and cubic extrapolation: the vectorised double-float path only (linear elsewhere)
+  P.extrap_order = (o->guess >= 2 && P.v4 && o->precision != TH_PREC_FP64 && !P.ad) ? o->guess : 1;
   if (P.extrap) {
     const size_t n = (size_t)g->n;
     auto al = [&](auto** p, size_t bytes) -> th_status {
@@ -1418,9 +1421,13 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
     TH_TRY(al(&g->thm_hi, n * sizeof(float)));
     TH_TRY(al(&g->thm_lo, n * sizeof(float)));
     TH_TRY(al(&g->thm64, n * sizeof(double)));
-    if (P.extrap_order == 2) {
+    if (P.extrap_order >= 2) {
       TH_TRY(al(&g->thm2_hi, n * sizeof(float)));
       TH_TRY(al(&g->thm2_lo, n * sizeof(float)));
+    }
+    if (P.extrap_order >= 3) {
+      TH_TRY(al(&g->thm3_hi, n * sizeof(float)));
+      TH_TRY(al(&g->thm3_lo, n * sizeof(float)));
     }
   }
   TH_TRY(ensure_stage(g, 0));

@@ -417,7 +417,7 @@ def test_transient_step(prec, nx):
     assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
 
 
-@pytest.mark.parametrize("guess", [0, 1, 2])
+@pytest.mark.parametrize("guess", [0, 1, 2, 3])
 @pytest.mark.parametrize("graph", [0, 1])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_run_transient_schedule(graph, prec, guess):
@@ -430,6 +430,27 @@ def test_run_transient_schedule(graph, prec, guess):
     T = cuda(np.full(nx * ny * st.L, st.t_amb))
     T, stats = g.run_transient([cuda(m) for m in maps], spm, n_steps, dt, T, precision=prec, tol_rel=1e-10,
                                cheb_degree=6, use_graph=graph, guess=guess)
+    sched = [maps[(s // spm) % 2].astype(np.float64) for s in range(n_steps)]
+    ref = osolve.transient(nx, ny, st, sched, dt, np.full(nx * ny * st.L, st.t_amb))[-1]
+    assert stats["steps"] == n_steps and stats["status"] == 0
+    assert osolve.rise_relative_error(T.cpu().numpy(), ref, st.t_amb) <= 1e-6
+
+
+@pytest.mark.parametrize("guess", [2, 3])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_run_transient_high_order_guess_across_switches(graph, guess):
+    """Quadratic and cubic extrapolated guesses on a schedule long enough to reach the
+    full order before and after a power-map switch (steps 3-4 and 8-10 run cubic; the
+    order drops to 0 at the switch and rebuilds), against the oracle's trajectory."""
+    st = ti.stack_c2()
+    nx, ny, dt = 44, 26, 1e-4
+    maps = [ti.power_cells(st, nx, ny, [ti.density_floorplan(nx, ny, s + j) for j in (0, 1)], np.float32)
+            for s in (40, 42)]
+    n_steps, spm = 11, 5
+    g = grid_of(nx, ny, st)
+    T = cuda(np.full(nx * ny * st.L, st.t_amb))
+    T, stats = g.run_transient([cuda(m) for m in maps], spm, n_steps, dt, T, tol_rel=1e-10, cheb_degree=8,
+                               use_graph=graph, guess=guess)
     sched = [maps[(s // spm) % 2].astype(np.float64) for s in range(n_steps)]
     ref = osolve.transient(nx, ny, st, sched, dt, np.full(nx * ny * st.L, st.t_amb))[-1]
     assert stats["steps"] == n_steps and stats["status"] == 0
@@ -815,7 +836,7 @@ def test_empty_runs():
     assert solve_batched([], [], []) == []
 
 
-@pytest.mark.parametrize("guess", [1, 2])
+@pytest.mark.parametrize("guess", [1, 2, 3])
 @pytest.mark.parametrize("graph", [0, 1])
 def test_run_transient_conductivity_map(guess, graph):
     """Per-cell conductivities (per-face kernels, no layer table) with the
