@@ -63,9 +63,11 @@ KERNEL_BYTES = {
     "ad_cheb_a3": 28,    # A3 in FP16 (8) + z_m, z_{m-1}, r, 1/diag (16) + z_{m+1} (4)
     "ad_spmv_early": 32, # D4, gx gy gz FP32 (16) + p (8) + mu (8)
     "ad_spmv_late": 48,  # D4, gx gy gz FP64 (32) + p (8) + mu (8)
-    # one multigrid V-cycle; level 0: two smoothing sweeps (b, x, gx gy gz, s, m, w: 32 read
-    # + 4 written each) and the restriction (x, b, faces, s: 24); coarser levels add 1/3
-    "mg_vcycle": 124,
+    # one multigrid V-cycle on the layer table; finest level: pre-smoothing from zero
+    # (b in, x out: 8), restriction (x, b in, 1/4 of a coarse b out: 9), post-smoothing
+    # (b, x, 1/4 of the coarse correction in, z out: 13); every coarser level a quarter
+    # of the one above: 30 x 4/3
+    "mg_vcycle": 40,
     # fused Chebyshev steps on per-face arrays: z_m, z_{m-1}, r, gx, gy, gz read once (24)
     # + z_{m+S}, z_{m+S-1} written (8)
     "cheb_tbf4": 32,

@@ -406,6 +406,114 @@ __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, in
   }
 }
 
+// ---------------------------------------------------------------- coarse levels, column tiles
+// Layer-uniform coarse levels are small: their kernels are bound by memory latency,
+// not bandwidth.  A block takes 8 x 4 columns and every layer, one thread per cell:
+// each thread forms its cell's residual with one round of independent loads into
+// shared memory, then one warp runs the 32 columns' tridiagonal solves from shared
+// memory (the smoother) or the block sums its 2 x 2 aggregates (the restriction).
+// Same arithmetic as k_mg_smooth / k_mg_restrict with the level's table.
+#define MG_CT_X 8
+#define MG_CT_Y 4
+
+template <int LMAX>
+__device__ __forceinline__ float mg_ct_residual(const MGUni<LMAX>& U, int nx, int ny, int L, int x, int y, int z,
+                                                float bi, float xi, const float* __restrict__ xin,
+                                                const float* __restrict__ xc, int nxc, long long pxyc) {
+  // the iterate at a neighbour: x_in + P x_c (the coarse correction read on the fly)
+  auto val = [&](int xx, int yy, int zz) -> float {
+    float t = xin[(long long)xx + (long long)nx * ((long long)yy + (long long)ny * zz)];
+    if (xc) t += xc[(xx >> 1) + (long long)nxc * (yy >> 1) + pxyc * zz];
+    return t;
+  };
+  float a = U.s[z] * xi;
+  if (x + 1 < nx) a += U.gx[z] * (xi - val(x + 1, y, z));
+  if (x > 0) a += U.gx[z] * (xi - val(x - 1, y, z));
+  if (y + 1 < ny) a += U.gy[z] * (xi - val(x, y + 1, z));
+  if (y > 0) a += U.gy[z] * (xi - val(x, y - 1, z));
+  if (z + 1 < L) a += U.gz[z] * (xi - val(x, y, z + 1));
+  if (z > 0) a += U.gz[z > 0 ? z - 1 : 0] * (xi - val(x, y, z - 1));
+  return bi - a;
+}
+
+// x_out = x + omega T^-1 (b - A x), x = x_in (+ P x_c) or 0.  Block (32, LMAX).
+template <int LMAX>
+__global__ void __launch_bounds__(32 * LMAX) k_mg_smooth_ct(const Ctl* ctl, int nx, int ny, int L,
+                                                           const __grid_constant__ MGUni<LMAX> U,
+                                                           const float* __restrict__ b,
+                                                           const float* __restrict__ xin,
+                                                           const float* __restrict__ xc, int nxc, int nyc,
+                                                           float* __restrict__ xout, float omega) {
+  if (ld_int(&ctl->done)) return;
+  __shared__ float sr[LMAX][32], sx[LMAX][32];
+  const int t = threadIdx.x, z = threadIdx.y;
+  const int x = blockIdx.x * MG_CT_X + (t % MG_CT_X), y = blockIdx.y * MG_CT_Y + (t / MG_CT_X);
+  const bool col = x < nx && y < ny;
+  const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+  float res = 0.f, xi = 0.f;
+  if (col && z < L) {
+    const float bi = b[i];
+    if (xin) {
+      xi = xin[i];
+      if (xc) xi += xc[(x >> 1) + (long long)nxc * (y >> 1) + (long long)nxc * nyc * z];
+      res = mg_ct_residual<LMAX>(U, nx, ny, L, x, y, z, bi, xi, xin, xc, nxc, (long long)nxc * nyc);
+    } else {
+      res = bi;
+    }
+  }
+  sr[z][t] = res;
+  sx[z][t] = xi;
+  __syncthreads();
+  if (z == 0 && col) {  // one warp: the 32 columns' Thomas solves
+    const int cs = (int)(x + 1 < nx) + (int)(x > 0) + 3 * ((int)(y + 1 < ny) + (int)(y > 0));
+    float dprev = 0.f;
+#pragma unroll
+    for (int zz = 0; zz < LMAX; ++zz) {
+      if (zz >= L) break;
+      const float gb = zz > 0 ? U.gz[zz > 0 ? zz - 1 : 0] : 0.f;
+      dprev = (sr[zz][t] + gb * dprev) * U.m[cs][zz];
+      sr[zz][t] = dprev;
+    }
+    float dn = 0.f;
+#pragma unroll
+    for (int zz = LMAX - 1; zz >= 0; --zz) {
+      if (zz >= L) continue;
+      const float d = sr[zz][t] + U.w[cs][zz] * dn;
+      dn = d;
+      sr[zz][t] = sx[zz][t] + omega * d;
+    }
+  }
+  __syncthreads();
+  if (col && z < L) xout[i] = sr[z][t];
+}
+
+// b_c = P^T (b - A x) for complete 2 x 2 aggregates (even nx, ny).  Block (32, LMAX).
+template <int LMAX>
+__global__ void __launch_bounds__(32 * LMAX) k_mg_restrict_ct(const Ctl* ctl, int nx, int ny, int L,
+                                                             const __grid_constant__ MGUni<LMAX> U,
+                                                             const float* __restrict__ b,
+                                                             const float* __restrict__ x, int nxc, int nyc,
+                                                             float* __restrict__ bc) {
+  if (ld_int(&ctl->done)) return;
+  __shared__ float sr[LMAX][32];
+  const int t = threadIdx.x, z = threadIdx.y;
+  const int cx = t % MG_CT_X, cy = t / MG_CT_X;
+  const int xx = blockIdx.x * MG_CT_X + cx, yy = blockIdx.y * MG_CT_Y + cy;
+  float r = 0.f;
+  if (xx < nx && yy < ny && z < L) {
+    const long long i = (long long)xx + (long long)nx * ((long long)yy + (long long)ny * z);
+    r = mg_ct_residual<LMAX>(U, nx, ny, L, xx, yy, z, b[i], x[i], x, nullptr, 1, 0);
+  }
+  sr[z][t] = r;
+  __syncthreads();
+  if (((cx | cy) & 1) == 0 && z < L) {
+    const int X = xx >> 1, Y = yy >> 1;
+    if (X < nxc && Y < nyc)
+      bc[(long long)X + (long long)nxc * ((long long)Y + (long long)nyc * z)] =
+          (sr[z][t] + sr[z][t + 1]) + (sr[z][t + MG_CT_X] + sr[z][t + MG_CT_X + 1]);
+  }
+}
+
 // coarsest level: x = C b with the dense inverse C (n x n, FP32), a warp per row
 __global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, const float* __restrict__ C,
                                                      const float* __restrict__ b, float* __restrict__ x) {
@@ -451,6 +559,12 @@ struct MGHier {
   std::vector<MGLevelH> lv;
   bool uni = false;   // finest level from the layer table
   MGUni<32> tab{};    // its coefficients and Thomas factors (first L layers used)
+  // Levels whose coefficients depend only on the layer (and on which in-plane
+  // neighbours exist): the finest level of a layer-uniform grid and every coarser
+  // level reached through complete 2 x 2 aggregates (even nx, ny above it).  Their
+  // tables replace the per-cell arrays in the smoother and the restriction.
+  std::vector<char> luni;
+  std::vector<MGUni<32>> ltab;
   float* cinv = nullptr;  // dense inverse of the coarsest operator
   int nc = 0;
   ~MGHier() {
@@ -564,35 +678,66 @@ th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s) {
     k_mg_zfactors<<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(l.nx, l.ny, L, l.gx, l.gy, l.gz, l.s, l.m, l.w);
     TH_CHECK_LAUNCH();
   }
-  // finest level of a layer-uniform grid: coefficients and Thomas factors per case
+  // layer-uniform levels: coefficients and Thomas factors per in-plane case
   h->uni = g->uniform;
-  if (h->uni) {
-    const LayerTab& T = g->tab_host;
-    std::memset(&h->tab, 0, sizeof(h->tab));
-    for (int z = 0; z < L; ++z) {
-      h->tab.s[z] = T.s32[z];
-      h->tab.gx[z] = T.gxl[z];
-      h->tab.gy[z] = T.gyl[z];
-      h->tab.gz[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
-    }
+  const size_t nlv = h->lv.size();
+  h->luni.assign(nlv, 0);
+  h->ltab.assign(nlv, MGUni<32>{});
+  auto factors = [&](MGUni<32>& t) {
     for (int nyf = 0; nyf < 3; ++nyf)
       for (int nxf = 0; nxf < 3; ++nxf) {
         const int c = nxf + 3 * nyf;
         double wprev = 0.0;
         for (int z = 0; z < L; ++z) {  // the order of k_mg_zfactors: s, x faces, y faces, z faces
-          double b = h->tab.s[z];
-          for (int q = 0; q < nxf; ++q) b += h->tab.gx[z];
-          for (int q = 0; q < nyf; ++q) b += h->tab.gy[z];
-          if (z + 1 < L) b += h->tab.gz[z];
-          const double gb = (z > 0) ? (double)h->tab.gz[z - 1] : 0.0;
+          double b = t.s[z];
+          for (int q = 0; q < nxf; ++q) b += t.gx[z];
+          for (int q = 0; q < nyf; ++q) b += t.gy[z];
+          if (z + 1 < L) b += t.gz[z];
+          const double gb = (z > 0) ? (double)t.gz[z - 1] : 0.0;
           if (z > 0) b += gb;
           const double mz = 1.0 / (b - gb * wprev);
-          const double wz = (z + 1 < L) ? (double)h->tab.gz[z] * mz : 0.0;
-          h->tab.m[c][z] = (float)mz;
-          h->tab.w[c][z] = (float)wz;
+          const double wz = (z + 1 < L) ? (double)t.gz[z] * mz : 0.0;
+          t.m[c][z] = (float)mz;
+          t.w[c][z] = (float)wz;
           wprev = wz;
         }
       }
+  };
+  if (h->uni) {
+    const LayerTab& T = g->tab_host;
+    MGUni<32>& t0 = h->ltab[0];
+    std::memset(&t0, 0, sizeof(t0));
+    for (int z = 0; z < L; ++z) {
+      t0.s[z] = T.s32[z];
+      t0.gx[z] = T.gxl[z];
+      t0.gy[z] = T.gyl[z];
+      t0.gz[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
+    }
+    factors(t0);
+    h->luni[0] = 1;
+    // a coarse level of complete 2 x 2 aggregates: per-cell term and vertical face
+    // summed over the 4 fine cells, in-plane faces over the 2 crossing ones (FP32, in
+    // k_mg_coarsen's order, so the table equals the per-cell arrays)
+    for (size_t k = 0; k + 1 < nlv; ++k) {
+      if (!h->luni[k] || h->lv[k].nx % 2 != 0 || h->lv[k].ny % 2 != 0) break;
+      const MGUni<32>& f = h->ltab[k];
+      MGUni<32>& t = h->ltab[k + 1];
+      std::memset(&t, 0, sizeof(t));
+      for (int z = 0; z < L; ++z) {
+        float sz = 0.f, gz = 0.f;
+        for (int q = 0; q < 4; ++q) {
+          sz += f.s[z];
+          gz += f.gz[z];
+        }
+        t.s[z] = sz;
+        t.gz[z] = gz;
+        t.gx[z] = f.gx[z] + f.gx[z];
+        t.gy[z] = f.gy[z] + f.gy[z];
+      }
+      factors(t);
+      h->luni[k + 1] = 1;
+    }
+    h->tab = h->ltab[0];
   }
   // dense inverse of the coarsest operator (at most 4 x 4 columns x L layers)
   const MGLevelH& c = h->lv.back();
@@ -634,33 +779,55 @@ th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s) {
   return TH_OK;
 }
 
+// the table of level k (layer-uniform levels only)
 template <int LMAX>
-static MGUni<LMAX> uni_of(const MGHier* h) {
+static MGUni<LMAX> uni_of(const MGHier* h, int k) {
   MGUni<LMAX> u;
   std::memset(&u, 0, sizeof(u));
+  const MGUni<32>& t = h->ltab[k];
   for (int z = 0; z < LMAX; ++z) {
-    u.s[z] = h->tab.s[z];
-    u.gx[z] = h->tab.gx[z];
-    u.gy[z] = h->tab.gy[z];
-    u.gz[z] = h->tab.gz[z];
+    u.s[z] = t.s[z];
+    u.gx[z] = t.gx[z];
+    u.gy[z] = t.gy[z];
+    u.gz[z] = t.gz[z];
     for (int c = 0; c < 9; ++c) {
-      u.m[c][z] = h->tab.m[c][z];
-      u.w[c][z] = h->tab.w[c][z];
+      u.m[c][z] = t.m[c][z];
+      u.w[c][z] = t.w[c][z];
     }
   }
   return u;
 }
 
-// the vectorised finest-level kernels apply (layer table, nx % 4 == 0, <= 12 layers:
+static bool mg_uni(const MGHier* h, int k) { return k < (int)h->luni.size() && h->luni[k]; }
+
+// coarse layer-uniform levels of complete aggregates up to 256 x 256 columns run the
+// column-tile kernels (latency-bound sizes); the finest level and larger levels keep
+// the 4-column bandwidth kernels (measured: a 512 x 512 x 8 level is slower in
+// column tiles)
+static bool mg_ct(const thermal_grid* g, int k) {
+  const MGHier* h = g->mg;
+  return k > 0 && mg_uni(h, k) && h->lv[k].nx % 2 == 0 && h->lv[k].ny % 2 == 0 &&
+         (long long)h->lv[k].nx * h->lv[k].ny <= 65536;
+}
+
+// the vectorised kernels apply (a layer-uniform level, nx % 4 == 0, <= 12 layers:
 // 4 columns x 12 layers of the iterate and the forward sweep fit the registers)
-static bool mg_v4(const thermal_grid* g, int k) { return k == 0 && g->mg->uni && g->nx % 4 == 0 && g->L <= 12; }
+static bool mg_v4(const thermal_grid* g, int k) {
+  return mg_uni(g->mg, k) && g->mg->lv[k].nx % 4 == 0 && g->L <= 12;
+}
 
 template <int LMAX>
 static th_status smooth(thermal_grid* g, int k, const float* b, const float* xin, const float* xc, int nxc, int nyc,
                         float* xout, cudaStream_t s) {
   const MGHier* h = g->mg;
   const MGLevelH& l = h->lv[k];
-  const MGUni<LMAX> U = uni_of<LMAX>(h);
+  const MGUni<LMAX> U = uni_of<LMAX>(h, k);
+  if (mg_ct(g, k)) {
+    k_mg_smooth_ct<LMAX><<<dim3((l.nx + MG_CT_X - 1) / MG_CT_X, (l.ny + MG_CT_Y - 1) / MG_CT_Y), dim3(32, LMAX), 0,
+                           s>>>(g->ctl, l.nx, l.ny, g->L, U, b, xin, xc, nxc, nyc, xout, MG_OMEGA);
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  }
   if constexpr (LMAX == 8 || LMAX == 12) {
     if (mg_v4(g, k)) {
       k_mg_smooth4<LMAX><<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U, b,
@@ -670,7 +837,7 @@ static th_status smooth(thermal_grid* g, int k, const float* b, const float* xin
       return TH_OK;
     }
   }
-  if (k == 0 && h->uni)
+  if (mg_uni(h, k))
     k_mg_smooth<LMAX, true><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, xin, xc, nxc,
                                                                         nyc, xout, MG_OMEGA);
   else
@@ -685,7 +852,13 @@ static th_status restrict_(thermal_grid* g, int k, const float* b, const float* 
   const MGHier* h = g->mg;
   const MGLevelH& l = h->lv[k];
   const MGLevelH& c = h->lv[k + 1];
-  const MGUni<LMAX> U = uni_of<LMAX>(h);
+  const MGUni<LMAX> U = uni_of<LMAX>(h, k);
+  if (mg_ct(g, k)) {
+    k_mg_restrict_ct<LMAX><<<dim3((l.nx + MG_CT_X - 1) / MG_CT_X, (l.ny + MG_CT_Y - 1) / MG_CT_Y), dim3(32, LMAX), 0,
+                             s>>>(g->ctl, l.nx, l.ny, g->L, U, b, x, c.nx, c.ny, bc);
+    TH_CHECK_LAUNCH();
+    return TH_OK;
+  }
   if constexpr (LMAX == 8 || LMAX == 12) {
     if (mg_v4(g, k)) {
       k_mg_restrict4<LMAX><<<dim3((l.nx / 4 + 31) / 32, (l.ny + 7) / 8), dim3(32, 8), 0, s>>>(g->ctl, l.nx, l.ny, g->L, U,
@@ -694,7 +867,7 @@ static th_status restrict_(thermal_grid* g, int k, const float* b, const float* 
       return TH_OK;
     }
   }
-  if (k == 0 && h->uni)
+  if (mg_uni(h, k))
     k_mg_restrict<LMAX, true><<<col_grid(l.nx, l.ny), dim3(32, 8), 0, s>>>(g->ctl, dev_of(l, g->L), U, b, x, c.nx,
                                                                           c.ny, bc);
   else

@@ -480,11 +480,14 @@ def test_run_transient_long_schedule(prec):
 
 @pytest.mark.parametrize("nx,ny,mk,dt", [(37, 21, "c2", 1e-4), (37, 21, "c2", 0.0), (9, 30, "mol", 0.0),
                                          (3, 2, "c1", 0.0), (64, 64, "c1", 1e-4), (36, 30, "mol", 0.0),
-                                         (68, 22, "mol", 1e-4)])
+                                         (68, 22, "mol", 1e-4), (128, 64, "c2", 0.0), (64, 32, "mol", 1e-4),
+                                         (72, 40, "c2", 0.0)])
 def test_mg_vcycle_matches_oracle(nx, ny, mk, dt):
     """One V-cycle (aggregation semi-coarsening, damped z-line Jacobi, exact coarsest
     solve) in FP32 on the GPU against the oracle's FP64 V-cycle, on odd sizes, a
-    single-level grid and a grid with six levels."""
+    single-level grid, grids whose levels are layer-uniform down to the coarsest
+    (coefficient tables, 4-column kernels on every level with nx % 4 == 0) and one
+    that turns to per-cell arrays part-way (72 -> 36 -> 18 columns)."""
     from oracle import multigrid as mg
     st = STACKS[mk]()
     A = disc.assemble(nx, ny, st, dt=dt if dt > 0 else None).tocsr()
