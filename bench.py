@@ -600,8 +600,8 @@ def precond_section(args, opts, trajectory, maps, nsteps, st):
 
 def batched_section(args):
     """64 independent stacks of uneven size (128^2x4 .. 512^2x8, k perturbed +-20%),
-    steady, FP32 PCG (Chebyshev, degree 30) + FP64 refinement to 1e-8, in one
-    persistent cooperative launch per rank.  With several ranks the stacks are
+    steady, FP32 PCG + FP64 refinement to 1e-8, in one persistent cooperative launch
+    per rank, with the multigrid V-cycle and with Chebyshev-30 as the preconditioner.  With several ranks the stacks are
     sharded (contiguous balanced shares, ``dist.solve_sharded``): each rank solves its
     share in one launch, the job time is the slowest rank's, and the per-instance
     results are gathered on the host.  No data-path collective."""
@@ -612,8 +612,8 @@ def batched_section(args):
     from paper_2606_17850_gb300.dist import max_over_ranks, rank_world, shard, solve_sharded
     insts = ti.c4_instances()
     rank, world = rank_world()
-    o = dict(tol_rel=1e-8, precond="cheb", cheb_degree=30)
     timing = {}
+    o = {}
 
     def solve_shard(idx):
         grids = [ThermalGrid.from_stack(insts[i].nx, insts[i].ny, insts[i].stack) for i in idx]
@@ -630,19 +630,28 @@ def batched_section(args):
             g.close()
         return res
 
-    res = solve_sharded(len(insts), solve_shard, rank, world)
-    ms = max_over_ranks(timing.get("ms", 0.0), device="cuda")
     n = sum(i.n for i in insts)
-    st = [res[i] for i in range(len(insts))]
-    return {"workload": "64 steady stacks of uneven size (128^2x4, 256^2x6, 384^2x8, 512^2x8; k x U[0.8,1.2])",
-            "unknowns": n, "ms_per_batch_solve": ms, "max_rel_res": max(s["rel_res"] for s in st),
-            "status": max(s["status"] for s in st), "inner_it_sum": sum(s["inner_it"] for s in st),
-            "max_inner_it": max(s["inner_it"] for s in st), "ranks": world,
-            "instances_per_rank": [len(shard(len(insts), r, world)) for r in range(world)],
-            "tiles": {f"{insts[i].nx}x{insts[i].ny}x{insts[i].stack.L}":
-                      f"128 x {8 * st[i]['tile_rows']} columns x {st[i]['tile_layers']} layers"
-                      for i in range(len(insts))},
-            "launch": "one cooperative persistent kernel per rank for its share of the 64 instances"}
+    out = {"workload": "64 steady stacks of uneven size (128^2x4, 256^2x6, 384^2x8, 512^2x8; k x U[0.8,1.2])",
+           "unknowns": n, "ranks": world,
+           "instances_per_rank": [len(shard(len(insts), r, world)) for r in range(world)],
+           "launch": "one cooperative persistent kernel per rank for its share of the 64 instances"}
+    for name, oo in (("multigrid", dict(tol_rel=1e-8, precond="mg")),
+                     ("chebyshev30", dict(tol_rel=1e-8, precond="cheb", cheb_degree=30))):
+        o.clear()
+        o.update(oo)
+        res = solve_sharded(len(insts), solve_shard, rank, world)
+        ms = max_over_ranks(timing.get("ms", 0.0), device="cuda")
+        st = [res[i] for i in range(len(insts))]
+        out[name] = {"ms_per_batch_solve": ms, "max_rel_res": max(s["rel_res"] for s in st),
+                     "status": max(s["status"] for s in st), "inner_it_sum": sum(s["inner_it"] for s in st),
+                     "max_inner_it": max(s["inner_it"] for s in st),
+                     "tiles": {f"{insts[i].nx}x{insts[i].ny}x{insts[i].stack.L}":
+                               f"128 x {8 * st[i]['tile_rows']} columns x {st[i]['tile_layers']} layers"
+                               for i in range(len(insts))}}
+    best = min(("multigrid", "chebyshev30"), key=lambda k: out[k]["ms_per_batch_solve"])
+    out["ms_per_batch_solve"] = out[best]["ms_per_batch_solve"]
+    out["preconditioner"] = best
+    return out
 
 
 def adjoint_section(args):

@@ -32,6 +32,7 @@
 
 #include "internal.h"
 #include "kernels_v4.cuh"
+#include "mg_device.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -65,6 +66,18 @@ struct BArgs {
   double* partials;  // [2][ntiles]
   int pc, k, scaled;
   int max_sweeps;    // safety cap on inner sweeps of the whole batch
+  // multigrid preconditioner (pc == TH_PC_MG): every instance's hierarchy, and for
+  // each level index k the work list of 32 x 8-column tiles of the instances that
+  // smooth on level k (entries [mgt_off[k], mgt_off[k+1]) of mgt: instance, tile).
+  // The offsets live in device memory: an array member of this by-value argument
+  // made ptxas keep the whole argument block on the stack (spill loads 292 -> 540
+  // bytes in every instantiation, 0.93 -> 1.13 s for the 64-stack Chebyshev batch).
+  const MGBDesc* mg;
+  const int2* mgt;
+  const int* mgt_off;  // [MG_BMAXL + 1]
+  int mg_maxnl;
+  const int2* mg_l0;  // per instance: first entry and count of its level-0 tiles
+  double* mg_part;    // r^T z partial per level-0 tile
 };
 
 // loop scalars of one instance, read once per tile
@@ -295,13 +308,162 @@ __device__ void cheb_tail(const BArgs& A, cg::grid_group& grid) {
   }
 }
 
+// ---------------------------------------------------------------- multigrid phases
+
+// placeholder table for the per-cell variant of the level routines (levels without a
+// layer-uniform table read their per-cell arrays; the table argument is unused there)
+static __constant__ MGUni<8> c_mg_none;
+
+// One phase over the level-k tile list: body(instance, tile within its level, entry)
+// for the tiles of instances whose inner solve is active (checked once per instance
+// run, the flag cannot change within a phase).
+template <class F>
+__device__ void mg_phase(const BArgs& A, int k, F body) {
+  __shared__ int s_act;
+  const int tid = thread_linear_id();
+  int cur = -1;
+  bool act = false;
+  const int t0 = __ldg(A.mgt_off + k), t1 = __ldg(A.mgt_off + k + 1);
+  for (int t = t0 + (int)blockIdx.x; t < t1; t += gridDim.x) {
+    const int2 e = __ldg(A.mgt + t);
+    if (e.x != cur) {
+      __syncthreads();
+      if (tid == 0) s_act = active(A.inst[e.x].ctl, ACT_INNER);
+      __syncthreads();
+      act = s_act != 0;
+      cur = e.x;
+    }
+    if (act) body(e.x, e.y, t);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ MGDev mg_dev(const MGBDesc& D, int k, int L) {
+  const MGBLevel& l = D.lv[k];
+  return MGDev{l.nx, l.ny, L, l.gx, l.gy, l.gz, l.s, l.m, l.w};
+}
+
+// z = M^-1 r for every active instance: one V-cycle (as mg_vcycle of the single-grid
+// path), instances of different depths in the same phases; the last post-smoothing
+// also reduces r^T z.  Inlined (the multigrid instantiation spills about 1.1 KB a
+// thread, yet measured faster than the cycle as an out-of-line call, 314 vs 330 ms
+// for the 64 stacks, or at two blocks per SM without the register cap, 414 ms).
+__device__ void mg_vcycle_batched(const BArgs& A, cg::grid_group& grid) {
+  __shared__ float rowsum[8][32];
+  __shared__ double red[32];
+  const int tid = thread_linear_id();
+  for (int k = 0; k + 1 < A.mg_maxnl; ++k) {  // down: pre-smooth from zero, restrict
+    mg_phase(A, k, [&](int ii, int tile, int) {
+      const MGBDesc& D = A.mg[ii];
+      const BInst& I = A.inst[ii];
+      const MGBLevel& l = D.lv[k];
+      const int tbx = (l.nx + 31) / 32;
+      const int x = (tile % tbx) * 32 + threadIdx.x, y = (tile / tbx) * 8 + threadIdx.y;
+      const float* b = (k == 0) ? I.r : l.b;
+      float* xo = (k == 0) ? l.xt : l.x;
+      if (x < l.nx && y < l.ny) {
+        if (l.uni)
+          mg_smooth_column<8, true>(mg_dev(D, k, I.d.L), l.t, x, y, b, nullptr, nullptr, 1, 1, xo, kMGOmega, false);
+        else
+          mg_smooth_column<8, false>(mg_dev(D, k, I.d.L), c_mg_none, x, y, b, nullptr, nullptr, 1, 1, xo, kMGOmega,
+                                     false);
+      }
+    });
+    grid.sync();
+    mg_phase(A, k, [&](int ii, int tile, int) {
+      const MGBDesc& D = A.mg[ii];
+      const BInst& I = A.inst[ii];
+      const MGBLevel& l = D.lv[k];
+      const MGBLevel& c = D.lv[k + 1];
+      const int tbx = (l.nx + 31) / 32;
+      if (l.uni)
+        mg_restrict_tile<8, true>(mg_dev(D, k, I.d.L), l.t, tile % tbx, tile / tbx, (k == 0) ? I.r : l.b,
+                                  (k == 0) ? l.xt : l.x, c.nx, c.ny, c.b, rowsum);
+      else
+        mg_restrict_tile<8, false>(mg_dev(D, k, I.d.L), c_mg_none, tile % tbx, tile / tbx, (k == 0) ? I.r : l.b,
+                                   (k == 0) ? l.xt : l.x, c.nx, c.ny, c.b, rowsum);
+    });
+    grid.sync();
+  }
+  // coarsest level of every active instance: the dense solve, one block at a time
+  {
+    int cur = -1;
+    for (int j = blockIdx.x; j < A.ninst; j += gridDim.x) {
+      if (!active(A.inst[j].ctl, ACT_INNER)) continue;
+      const MGBDesc& D = A.mg[j];
+      const MGBLevel& c = D.lv[D.nl - 1];
+      mg_coarsest_rows(D.nc, D.cinv, c.b, c.x, tid >> 5, block_threads() >> 5);
+      cur = j;
+    }
+    (void)cur;
+  }
+  grid.sync();
+  for (int k = A.mg_maxnl - 2; k >= 0; --k) {  // up: prolongated correction + post-smooth
+    mg_phase(A, k, [&](int ii, int tile, int t) {
+      const MGBDesc& D = A.mg[ii];
+      const BInst& I = A.inst[ii];
+      const MGBLevel& l = D.lv[k];
+      const MGBLevel& c = D.lv[k + 1];
+      const int tbx = (l.nx + 31) / 32;
+      const int x = (tile % tbx) * 32 + threadIdx.x, y = (tile / tbx) * 8 + threadIdx.y;
+      const float* b = (k == 0) ? I.r : l.b;
+      const float* xin = (k == 0) ? l.xt : l.x;
+      const float* xc = (k + 1 == D.nl - 1) ? c.x : c.xt;
+      float* out = (k == 0) ? I.zc[0] : l.xt;
+      float rz = 0.f;
+      if (x < l.nx && y < l.ny) {
+        if (l.uni)
+          rz = mg_smooth_column<8, true>(mg_dev(D, k, I.d.L), l.t, x, y, b, xin, xc, c.nx, c.ny, out, kMGOmega,
+                                         k == 0);
+        else
+          rz = mg_smooth_column<8, false>(mg_dev(D, k, I.d.L), c_mg_none, x, y, b, xin, xc, c.nx, c.ny, out,
+                                          kMGOmega, k == 0);
+      }
+      if (k == 0) {  // r^T z of the tile
+        const float ws = warp_sum(rz);
+        if ((tid & 31) == 0) red[tid >> 5] = (double)ws;
+        __syncthreads();
+        if (tid == 0) {
+          double sum = 0.0;
+          for (int w = 0; w < (block_threads() >> 5); ++w) sum += red[w];
+          A.mg_part[t - __ldg(A.mgt_off)] = sum;
+        }
+        __syncthreads();
+      }
+    });
+    grid.sync();
+  }
+  // r^T z per instance (fixed order), then beta
+  for (int j = blockIdx.x; j < A.ninst; j += gridDim.x) {
+    const Ctl* c0 = A.inst[j].ctl;
+    if (!active(c0, ACT_INNER)) continue;
+    const int2 rg = __ldg(A.mg_l0 + j);
+    double sum = 0.0;
+    for (int q = rg.x + tid; q < rg.x + rg.y; q += block_threads()) sum += __ldcg(A.mg_part + q);
+    sum = warp_sum(sum);
+    if ((tid & 31) == 0) red[tid >> 5] = sum;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < (block_threads() >> 5); ++w) tot += red[w];
+      Ctl* ctl = A.inst[j].ctl;
+      ctl->rz_next = tot;
+      ctl_set_beta(ctl);
+    }
+    __syncthreads();
+  }
+  grid.sync();
+}
+
 // Three co-resident blocks per SM (at most 80 registers a thread): the memory-bound
 // phases need the occupancy more than the rarely run FP64 residual phase needs
 // registers (measured: 0.92 s vs 1.12 s with two blocks per SM for the 64 stacks).
-template <typename TP>
+// MGP: the multigrid instantiation (its V-cycle phases are compiled only there, so
+// the other preconditioners keep their register allocation)
+template <typename TP, bool MGP>
 __global__ void __launch_bounds__(TH_BX* TH_BY4, 3) k_batched(BArgs A) {
   cg::grid_group grid = cg::this_grid();
-  const int rz_here = (A.pc != TH_PC_CHEB || A.k == 1) ? 1 : 0;
+  const int rz_here = (A.pc == TH_PC_NONE || A.pc == TH_PC_JACOBI || (A.pc == TH_PC_CHEB && A.k == 1)) ? 1 : 0;
   auto zfinal = [&](const BInst& I) -> const float* {
     if (A.pc == TH_PC_NONE) return I.r;
     if (A.pc == TH_PC_CHEB) return I.zc[(A.k - 1) % 3];
@@ -330,16 +492,19 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3) k_batched(BArgs A) {
         r = make_float4(r.x * C.rscale, r.y * C.rscale, r.z * C.rscale, r.w * C.rscale);
         st4(I.r + i, r);
         st4(I.dv + i, z4());
-        const float4 z = z_of4(A, I, i, r);
-        if (A.pc != TH_PC_NONE) st4(I.zc[0] + i, z);
         v[0] += dot4(r, r);
-        v[1] += dot4(r, z);
+        if (!MGP) {  // multigrid: z and r^T z come from the V-cycle
+          const float4 z = z_of4(A, I, i, r);
+          if (A.pc != TH_PC_NONE) st4(I.zc[0] + i, z);
+          v[1] += dot4(r, z);
+        }
       });
     });
     grid.sync();
     finish<2>(A, ACT_OUTER, [&](Ctl* ctl, const double (&t)[2]) { fin_update(ctl, t[0], t[1], true, rz_here); });
     grid.sync();
     if (A.pc == TH_PC_CHEB) cheb_tail(A, grid);
+    if (MGP) mg_vcycle_batched(A, grid);
     int parity = 0;
     while (any_active(A, ACT_INNER) && sweeps < A.max_sweeps) {
       ++sweeps;
@@ -377,16 +542,19 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, 3) k_batched(BArgs A) {
           st4(I.dv + i, make_float4(d.x + alpha * p.x, d.y + alpha * p.y, d.z + alpha * p.z, d.w + alpha * p.w));
           r = make_float4(r.x - alpha * m.x, r.y - alpha * m.y, r.z - alpha * m.z, r.w - alpha * m.w);
           st4(I.r + i, r);
-          const float4 z = z_of4(A, I, i, r);
-          if (A.pc != TH_PC_NONE) st4(I.zc[0] + i, z);
           v[0] += dot4(r, r);
-          v[1] += dot4(r, z);
+          if (!MGP) {
+            const float4 z = z_of4(A, I, i, r);
+            if (A.pc != TH_PC_NONE) st4(I.zc[0] + i, z);
+            v[1] += dot4(r, z);
+          }
         });
       });
       grid.sync();
       finish<2>(A, ACT_INNER, [&](Ctl* ctl, const double (&t)[2]) { fin_update(ctl, t[0], t[1], false, rz_here); });
       grid.sync();
       if (A.pc == TH_PC_CHEB) cheb_tail(A, grid);
+      if (MGP) mg_vcycle_batched(A, grid);
       parity ^= 1;
     }
     // theta += ||r|| d, then the true FP64 residual decides the outer loop
@@ -472,9 +640,10 @@ static Ctl batch_ctl(const thermal_solve_opts* o, double tol, int max_outer, int
 
 // One cooperative launch of the persistent kernel over the instances hi (tile lists
 // built from each instance's row blocks per tile); *ms = its duration (CUDA events).
+// mgd (multigrid preconditioner only): each instance's hierarchy, aligned with hi
 static th_status launch_batch(std::vector<BInst>& hi, const std::vector<thermal_grid*>& gs, const Ctl* ctl0,
                               int power_dtype, const thermal_solve_opts* opts, int k, int max_sweeps,
-                              cudaStream_t s, float* ms) {
+                              cudaStream_t s, float* ms, const std::vector<MGBDesc>* mgd = nullptr) {
   const int n = (int)hi.size();
   std::vector<int> tile_inst;
   int ntiles = 0;
@@ -506,11 +675,60 @@ static th_status launch_batch(std::vector<BInst>& hi, const std::vector<thermal_
   A.k = k;
   A.scaled = opts->cheb_scaled ? 1 : 0;
   A.max_sweeps = max_sweeps;
+  // multigrid: per level index, the 32 x 8-column tiles of the instances that smooth
+  // on that level (instance by instance, so each instance's level-0 tiles are one range)
+  DevArr<MGBDesc> dmg;
+  DevArr<int2> dmgt, dml0;
+  DevArr<int> dmgo;
+  DevArr<double> dmgp;
+  A.mg = nullptr;
+  A.mgt = nullptr;
+  A.mgt_off = nullptr;
+  A.mg_l0 = nullptr;
+  A.mg_part = nullptr;
+  A.mg_maxnl = 0;
+  if (opts->precond == TH_PC_MG) {
+    if (!mgd || (int)mgd->size() != n) return th_fail(TH_ESTATE, "batched multigrid without hierarchies");
+    int maxnl = 0;
+    for (const MGBDesc& D : *mgd) maxnl = std::max(maxnl, D.nl);
+    std::vector<int2> lst;
+    std::vector<int2> l0(n, make_int2(0, 0));
+    std::vector<int> off(MG_BMAXL + 1, 0);
+    for (int lvl = 0; lvl + 1 < maxnl; ++lvl) {
+      off[lvl] = (int)lst.size();
+      for (int i = 0; i < n; ++i) {
+        const MGBDesc& D = (*mgd)[i];
+        if (lvl > D.nl - 2) continue;
+        const int nt = ((D.lv[lvl].nx + 31) / 32) * ((D.lv[lvl].ny + 7) / 8);
+        if (lvl == 0) l0[i] = make_int2((int)lst.size(), nt);
+        for (int t = 0; t < nt; ++t) lst.push_back(make_int2(i, t));
+      }
+    }
+    for (int lvl = std::max(maxnl - 1, 0); lvl <= MG_BMAXL; ++lvl) off[lvl] = (int)lst.size();
+    TH_TRY(dmg.alloc(n));
+    TH_TRY(dmgt.alloc(lst.size()));
+    TH_TRY(dmgo.alloc(off.size()));
+    TH_TRY(dml0.alloc(n));
+    TH_TRY(dmgp.alloc(std::max(1, off[1] - off[0])));
+    TH_CUDA(cudaMemcpyAsync(dmg.p, mgd->data(), sizeof(MGBDesc) * n, cudaMemcpyHostToDevice, s));
+    if (!lst.empty())
+      TH_CUDA(cudaMemcpyAsync(dmgt.p, lst.data(), sizeof(int2) * lst.size(), cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(dml0.p, l0.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, s));
+    TH_CUDA(cudaMemcpyAsync(dmgo.p, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s));
+    A.mg = dmg.p;
+    A.mgt = dmgt.p;
+    A.mgt_off = dmgo.p;
+    A.mg_l0 = dml0.p;
+    A.mg_part = dmgp.p;
+    A.mg_maxnl = maxnl;
+  }
   // co-resident grid: every block must be resident for the grid-wide barriers
   int dev = 0, sms = 0, per_sm = 0;
   TH_CUDA(cudaGetDevice(&dev));
   TH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  void* fn = power_dtype == TH_F64 ? (void*)k_batched<double> : (void*)k_batched<float>;
+  void* fn = opts->precond == TH_PC_MG
+                 ? (power_dtype == TH_F64 ? (void*)k_batched<double, true> : (void*)k_batched<float, true>)
+                 : (power_dtype == TH_F64 ? (void*)k_batched<double, false> : (void*)k_batched<float, false>);
   TH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH_BX * TH_BY4, 0));
   if (per_sm < 1) return th_fail(TH_ECUDA, "batched kernel cannot be resident");
   const int nblocks = std::max(1, std::min(ntiles, sms * per_sm));
@@ -528,7 +746,7 @@ static th_status launch_batch(std::vector<BInst>& hi, const std::vector<thermal_
 }
 
 // Tile autotuner: the tile shape of each size class (nx, ny, layers, coefficient
-// source), chosen once per process by timing a fixed amount of work (one refinement
+// source) and preconditioner, chosen once per process by timing a fixed amount of work (one refinement
 // step with three inner iterations, from theta = 0) on the batch's instances of the
 // class, launched together as in the real solve, with each candidate: row blocks per tile (1 or 2 blocks of 128 x 8 columns) times
 // layers per tile (all, half, a quarter).  More rows or layers per tile mean fewer
@@ -536,9 +754,9 @@ static th_status launch_batch(std::vector<BInst>& hi, const std::vector<thermal_
 // threads with loads in flight (the z-walk keeps the layer below and above in
 // registers, so a layer chunk re-reads one plane at each end).
 struct BClass {
-  int nx, ny, L, uni;
+  int nx, ny, L, uni, pc, k;  // the preconditioner's phases weigh differently
   bool operator<(const BClass& o) const {
-    return std::tie(nx, ny, L, uni) < std::tie(o.nx, o.ny, o.L, o.uni);
+    return std::tie(nx, ny, L, uni, pc, k) < std::tie(o.nx, o.ny, o.L, o.uni, o.pc, o.k);
   }
 };
 struct BShape { int rows, zc; };
@@ -546,11 +764,12 @@ static std::mutex g_rows_mu;
 static std::map<BClass, BShape> g_rows;
 
 static th_status tune_rows(std::vector<BInst>& hi, const std::vector<thermal_grid*>& gs, int power_dtype,
-                           const thermal_solve_opts* opts, int k, cudaStream_t s) {
+                           const thermal_solve_opts* opts, int k, cudaStream_t s,
+                           const std::vector<MGBDesc>* mgd) {
   // instances of each size class in this batch
   std::map<BClass, std::vector<size_t>> classes;
   for (size_t i = 0; i < hi.size(); ++i)
-    classes[BClass{hi[i].d.nx, hi[i].d.ny, hi[i].d.L, hi[i].uni}].push_back(i);
+    classes[BClass{hi[i].d.nx, hi[i].d.ny, hi[i].d.L, hi[i].uni, opts->precond, k}].push_back(i);
   for (auto& kv : classes) {
     const BClass& key = kv.first;
     const std::vector<size_t>& members = kv.second;
@@ -578,7 +797,9 @@ static th_status tune_rows(std::vector<BInst>& hi, const std::vector<thermal_gri
       // outputs go to each grid's scratch (the caller's T is not touched)
       std::vector<BInst> sub;
       std::vector<thermal_grid*> sg;
+      std::vector<MGBDesc> smg;
       for (size_t i : members) {
+        if (mgd) smg.push_back((*mgd)[i]);
         thermal_grid* g = gs[i];
         if (!g->stage_T) {
           if (cudaMalloc((void**)&g->stage_T, sizeof(double) * (size_t)g->n) != cudaSuccess) {
@@ -600,8 +821,8 @@ static th_status tune_rows(std::vector<BInst>& hi, const std::vector<thermal_gri
           I.zl = c.zc;
         }
         float ms = 0.f;
-        TH_TRY(launch_batch(sub, sg, c0.data(), power_dtype, opts, k, 3, s, &ms));  // warm-up
-        TH_TRY(launch_batch(sub, sg, c0.data(), power_dtype, opts, k, 3, s, &ms));
+        TH_TRY(launch_batch(sub, sg, c0.data(), power_dtype, opts, k, 3, s, &ms, mgd ? &smg : nullptr));  // warm-up
+        TH_TRY(launch_batch(sub, sg, c0.data(), power_dtype, opts, k, 3, s, &ms, mgd ? &smg : nullptr));
         if (ms < best) {
           best = ms;
           chosen = c;
@@ -626,10 +847,13 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
   std::vector<std::vector<float>> c1s(n), c2s(n);
   std::vector<double> lmins(n), lmaxs(n);
   const int k = opts->precond == TH_PC_CHEB ? opts->cheb_degree : 1;
+  const bool mg = opts->precond == TH_PC_MG;
+  std::vector<MGBDesc> mgd(mg ? n : 0);
   for (int i = 0; i < n; ++i) {
     thermal_grid* g = grids[i];
     TH_TRY(grid_ensure_tab(g, 0.0, s));
     TH_TRY(grid_ensure_workspace(g, false, s));
+    if (mg) TH_TRY(mg_batch_levels(g, &mgd[i], s));
     float inv_theta = 1.0f;
     if (opts->precond == TH_PC_CHEB)
       TH_TRY(solver_cheb_coeffs(g, 0.0, opts, c1s[i], c2s[i], &inv_theta, &lmins[i], &lmaxs[i], s));
@@ -671,11 +895,11 @@ static th_status persistent(thermal_grid* const* grids, int n, const void* const
     hi[i].c1 = coef.p + (size_t)(2 * i) * k;
     hi[i].c2 = coef.p + (size_t)(2 * i + 1) * k;
   }
-  TH_TRY(tune_rows(hi, gs, power_dtype, opts, k, s));
+  TH_TRY(tune_rows(hi, gs, power_dtype, opts, k, s, mg ? &mgd : nullptr));
   std::vector<Ctl> c0(n, batch_ctl(opts, opts->tol_rel, opts->max_outer, opts->max_inner));
   float ms = 0.f;
   TH_TRY(launch_batch(hi, gs, c0.data(), power_dtype, opts, k,
-                      std::max(1, opts->max_outer) * std::max(1, opts->max_inner), s, &ms));
+                      std::max(1, opts->max_outer) * std::max(1, opts->max_inner), s, &ms, mg ? &mgd : nullptr));
   th_status first_bad = TH_OK;
   for (int i = 0; i < n; ++i) {
     Ctl h;
@@ -732,11 +956,16 @@ extern "C" th_status thermal_solve_batched(thermal_grid* const* grids, int n, co
         return th_fail(TH_EINVAL, "the same output buffer T appears twice in the batch");
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // the persistent kernel covers the mixed path with the Jacobi, Chebyshev and no
-    // preconditioner on grids with nx % 4 == 0; other combinations run the instances
-    // one after another through the single-grid solver
+    // the persistent kernel covers the mixed path with the Jacobi, Chebyshev, multigrid
+    // and no preconditioner on grids with nx % 4 == 0; other combinations run the
+    // instances one after another through the single-grid solver
+    // multigrid in the persistent kernel: at most 8 layers and at least two levels
+    // (max(nx, ny) > 8) on every instance
+    bool mg_ok = true;
+    for (int i = 0; i < n; ++i) mg_ok = mg_ok && grids[i]->L <= 8 && std::max(grids[i]->nx, grids[i]->ny) > 8;
     const bool fused = all_dev && v4 && opts->precision != TH_PREC_FP64 &&
-                       (opts->precond == TH_PC_NONE || opts->precond == TH_PC_JACOBI || opts->precond == TH_PC_CHEB) &&
+                       (opts->precond == TH_PC_NONE || opts->precond == TH_PC_JACOBI || opts->precond == TH_PC_CHEB ||
+                        (opts->precond == TH_PC_MG && mg_ok)) &&
                        opts->batched_mode == 0;
     if (fused) return persistent(grids, n, power, power_dtype, T, opts, stats, s);
     return sequential(grids, n, power, power_dtype, T, opts, stats, s);

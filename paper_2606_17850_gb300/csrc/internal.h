@@ -15,6 +15,7 @@
 
 #include "../../include/thermal.h"
 #include "common.cuh"
+#include "mg_device.cuh"
 
 // ------------------------------------------------------------------ errors
 
@@ -152,6 +153,25 @@ struct MGHier;
 void mg_free(MGHier* h);
 th_status grid_ensure_mg(thermal_grid* g, double dt, cudaStream_t s);
 th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s);
+// The multigrid hierarchy of one grid as plain device pointers, for the batched
+// persistent solve: per level the dimensions, the per-cell coefficients and Thomas
+// factors, and the work vectors x, xt, b; the coarsest level's dense inverse.
+#define MG_BMAXL 12
+struct MGBLevel {
+  int nx, ny;
+  const float *gx, *gy, *gz, *s, *m, *w;
+  float *x, *xt, *b;
+  int uni;       // layer-uniform level of a stack with at most 8 layers: `t` holds its table
+  MGUni<8> t;
+};
+struct MGBDesc {
+  int nl, nc;
+  const float* cinv;
+  MGBLevel lv[MG_BMAXL];
+};
+// Builds (or reuses) the hierarchy of g for the steady matrix and fills *out;
+// TH_EINVAL when it has more than MG_BMAXL levels.
+th_status mg_batch_levels(thermal_grid* g, MGBDesc* out, cudaStream_t s);
 th_status mg_rz(thermal_grid* g, const float* r, const float* z, cudaStream_t s);
 dim3 grid_blocks(const thermal_grid* g);
 Dims grid_dims(const thermal_grid* g);

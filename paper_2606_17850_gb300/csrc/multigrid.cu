@@ -23,10 +23,11 @@
 #include <vector>
 
 #include "internal.h"
+#include "mg_device.cuh"
 
 namespace {
 
-constexpr float MG_OMEGA = 0.8f;
+constexpr float MG_OMEGA = kMGOmega;
 constexpr int MG_COARSEST = 8;
 
 __device__ __forceinline__ long long idx3(int nx, int ny, int x, int y, int z) {
@@ -102,42 +103,7 @@ __global__ void k_mg_zfactors(int nx, int ny, int L, const float* __restrict__ g
   }
 }
 
-struct MGDev {  // one level, by value into kernels
-  int nx, ny, L;
-  const float *gx, *gy, *gz, *s, *m, *w;
-};
-
-// Finest level of a grid with one conductivity per layer: the coefficients and the
-// Thomas factors depend only on the layer and on which in-plane neighbours exist
-// (case nxf + 3 nyf, nxf/nyf = number of x/y neighbours), so they come from this
-// table (kernel parameters) instead of per-cell arrays.
-template <int LMAX>
-struct MGUni {
-  float s[LMAX], gx[LMAX], gy[LMAX], gz[LMAX];  // gz: face to the layer above (0 on top)
-  float m[9][LMAX], w[9][LMAX];
-};
-
-// coefficient access of one cell (layer z, in-plane case c) for either source
-template <int LMAX, bool UNI>
-struct MGC {
-  const MGDev& v;
-  const MGUni<LMAX>& U;
-  __device__ __forceinline__ float s(long long i, int z) const { return UNI ? U.s[z] : v.s[i]; }
-  __device__ __forceinline__ float gxr(long long i, int z) const { return UNI ? U.gx[z] : v.gx[i]; }
-  __device__ __forceinline__ float gxl(long long i, int z) const { return UNI ? U.gx[z] : v.gx[i - 1]; }
-  __device__ __forceinline__ float gyu(long long i, int z) const { return UNI ? U.gy[z] : v.gy[i]; }
-  __device__ __forceinline__ float gyd(long long i, int z) const { return UNI ? U.gy[z] : v.gy[i - v.nx]; }
-  __device__ __forceinline__ float gza(long long i, int z) const { return UNI ? U.gz[z] : v.gz[i]; }
-  __device__ __forceinline__ float gzb(long long i, int z, long long pxy) const {
-    return UNI ? U.gz[z > 0 ? z - 1 : 0] : v.gz[i - pxy];
-  }
-  __device__ __forceinline__ float m(long long i, int z, int c) const { return UNI ? U.m[c][z] : v.m[i]; }
-  __device__ __forceinline__ float w(long long i, int z, int c) const { return UNI ? U.w[c][z] : v.w[i]; }
-};
-
-// x_out = x + omega T^-1 (b - A x) per column, x = x_in (+ P x_c: the prolongated
-// coarse correction, read on the fly) or 0 (x_in == nullptr).  One thread per
-// column; the column (LMAX >= L layers) stays in registers.
+// x_out = x + omega T^-1 (b - A x) per column (mg_smooth_column), one thread per column
 template <int LMAX, bool UNI>
 __global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, const __grid_constant__ MGUni<LMAX> U,
                                                    const float* __restrict__ b, const float* __restrict__ xin,
@@ -147,96 +113,17 @@ __global__ void __launch_bounds__(256) k_mg_smooth(const Ctl* ctl, MGDev v, cons
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= v.nx || y >= v.ny) return;
-  const MGC<LMAX, UNI> C{v, U};
-  const int cs = (x + 1 < v.nx) + (x > 0) + 3 * ((y + 1 < v.ny) + (y > 0));
-  const int L = v.L;
-  const long long pxy = (long long)v.nx * v.ny;
-  const long long pxyc = (long long)nxc * nyc;
-  auto val = [&](int xx, int yy, int z) -> float {
-    if (!xin) return 0.f;
-    float t = xin[idx3(v.nx, v.ny, xx, yy, z)];
-    if (xc) t += xc[(xx >> 1) + (long long)nxc * (yy >> 1) + pxyc * z];
-    return t;
-  };
-  float xv[LMAX], dp[LMAX];
-  // current iterate of the column
-#pragma unroll
-  for (int z = 0; z < LMAX; ++z) xv[z] = (z < L) ? val(x, y, z) : 0.f;
-  // forward sweep: residual and Thomas elimination
-  float dprev = 0.f;
-#pragma unroll
-  for (int z = 0; z < LMAX; ++z) {
-    if (z >= L) break;
-    const long long i = idx3(v.nx, v.ny, x, y, z);
-    float res = b[i];
-    if (xin) {
-      const float xi = xv[z];
-      float a = C.s(i, z) * xi;
-      if (x + 1 < v.nx) a += C.gxr(i, z) * (xi - val(x + 1, y, z));
-      if (x > 0) a += C.gxl(i, z) * (xi - val(x - 1, y, z));
-      if (y + 1 < v.ny) a += C.gyu(i, z) * (xi - val(x, y + 1, z));
-      if (y > 0) a += C.gyd(i, z) * (xi - val(x, y - 1, z));
-      if (z + 1 < L) a += C.gza(i, z) * (xi - xv[z + 1 < LMAX ? z + 1 : z]);
-      if (z > 0) a += C.gzb(i, z, pxy) * (xi - xv[z > 0 ? z - 1 : 0]);
-      res -= a;
-    }
-    const float gb = (z > 0) ? C.gzb(i, z, pxy) : 0.f;
-    dprev = (res + gb * dprev) * C.m(i, z, cs);
-    dp[z] = dprev;
-  }
-  // back substitution and the damped update
-  float dn = 0.f;
-#pragma unroll
-  for (int zz = LMAX - 1; zz >= 0; --zz) {
-    if (zz >= L) continue;
-    const int z = zz;
-    const long long i = idx3(v.nx, v.ny, x, y, z);
-    const float dz = dp[z] + C.w(i, z, cs) * dn;
-    dn = dz;
-    xout[i] = xv[z] + omega * dz;
-  }
+  mg_smooth_column<LMAX, UNI>(v, U, x, y, b, xin, xc, nxc, nyc, xout, omega, false);
 }
 
-// b_c = P^T (b - A x): one thread per fine column computes its residual layer by
-// layer; the x pair of an aggregate (adjacent lanes) is summed with a shuffle, the
-// y pair (adjacent block rows) through shared memory.  Block (32, 8): every
-// aggregate lies inside one block.
+// b_c = P^T (b - A x) (mg_restrict_tile), block (32, 8)
 template <int LMAX, bool UNI>
 __global__ void __launch_bounds__(256) k_mg_restrict(const Ctl* ctl, MGDev v, const __grid_constant__ MGUni<LMAX> U,
                                                      const float* __restrict__ b, const float* __restrict__ x,
                                                      int nxc, int nyc, float* __restrict__ bc) {
   if (ld_int(&ctl->done)) return;
-  const MGC<LMAX, UNI> C{v, U};
   __shared__ float rowsum[8][32];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int xx = blockIdx.x * 32 + tx, yy = blockIdx.y * 8 + ty;
-  const bool in = xx < v.nx && yy < v.ny;
-  const long long pxy = (long long)v.nx * v.ny;
-#pragma unroll
-  for (int z = 0; z < LMAX; ++z) {
-    if (z >= v.L) break;
-    float r = 0.f;
-    if (in) {
-      const long long i = idx3(v.nx, v.ny, xx, yy, z);
-      const float xi = x[i];
-      float a = C.s(i, z) * xi;
-      if (xx + 1 < v.nx) a += C.gxr(i, z) * (xi - x[i + 1]);
-      if (xx > 0) a += C.gxl(i, z) * (xi - x[i - 1]);
-      if (yy + 1 < v.ny) a += C.gyu(i, z) * (xi - x[i + v.nx]);
-      if (yy > 0) a += C.gyd(i, z) * (xi - x[i - v.nx]);
-      if (z + 1 < v.L) a += C.gza(i, z) * (xi - x[i + pxy]);
-      if (z > 0) a += C.gzb(i, z, pxy) * (xi - x[i - pxy]);
-      r = b[i] - a;
-    }
-    r += __shfl_xor_sync(0xffffffffu, r, 1);  // x pair (2X, 2X+1); 0 from a column outside the grid
-    rowsum[ty][tx] = r;
-    __syncthreads();
-    if (((tx | ty) & 1) == 0) {
-      const int X = xx >> 1, Y = yy >> 1;
-      if (X < nxc && Y < nyc) bc[idx3(nxc, nyc, X, Y, z)] = rowsum[ty][tx] + rowsum[ty + 1][tx];
-    }
-    __syncthreads();
-  }
+  mg_restrict_tile<LMAX, UNI>(v, U, blockIdx.x, blockIdx.y, b, x, nxc, nyc, bc, rowsum);
 }
 
 // ---------------------------------------------------------------- finest level, vectorised
@@ -518,14 +405,8 @@ __global__ void __launch_bounds__(32 * LMAX) k_mg_restrict_ct(const Ctl* ctl, in
 __global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, const float* __restrict__ C,
                                                      const float* __restrict__ b, float* __restrict__ x) {
   if (ld_int(&ctl->done)) return;
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int warp = blockIdx.x * nw + (threadIdx.x >> 5);
-  for (int row = warp; row < n; row += nw * gridDim.x) {
-    float acc = 0.f;
-    for (int j = lane; j < n; j += 32) acc += C[(long long)row * n + j] * b[j];
-    acc = warp_sum(acc);
-    if (lane == 0) x[row] = acc;
-  }
+  const int nw = blockDim.x >> 5;
+  mg_coarsest_rows(n, C, b, x, blockIdx.x * nw + (threadIdx.x >> 5), nw * gridDim.x);
 }
 
 // r^T z with FP32 products and FP64 sums, then beta (the preconditioner's dot product)
@@ -933,5 +814,34 @@ th_status mg_rz(thermal_grid* g, const float* r, const float* z, cudaStream_t s)
   k_mg_rz<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, g->ctl, r, z, g->partials, g->partials_stride,
                                                       g->counters);
   TH_CHECK_LAUNCH();
+  return TH_OK;
+}
+
+th_status mg_batch_levels(thermal_grid* g, MGBDesc* out, cudaStream_t s) {
+  TH_TRY(grid_ensure_mg(g, 0.0, s));
+  const MGHier* h = g->mg;
+  const int nl = (int)h->lv.size();
+  if (nl > MG_BMAXL) return th_fail(TH_EINVAL, "multigrid hierarchy deeper than %d levels", MG_BMAXL);
+  std::memset(out, 0, sizeof(*out));
+  out->nl = nl;
+  out->nc = h->nc;
+  out->cinv = h->cinv;
+  for (int k = 0; k < nl; ++k) {
+    const MGLevelH& l = h->lv[k];
+    MGBLevel& d = out->lv[k];
+    d.nx = l.nx;
+    d.ny = l.ny;
+    d.gx = l.gx;
+    d.gy = l.gy;
+    d.gz = l.gz;
+    d.s = l.s;
+    d.m = l.m;
+    d.w = l.w;
+    d.x = l.x;
+    d.xt = l.xt;
+    d.b = l.b;
+    d.uni = (g->L <= 8 && mg_uni(h, k)) ? 1 : 0;
+    if (d.uni) d.t = uni_of<8>(h, k);
+  }
   return TH_OK;
 }

@@ -171,10 +171,12 @@ def test_fullsize_adjoint_c5(c5, pc):
 
 # ----------------------------------------------------------------- batched: 64 uneven stacks
 
-def test_fullsize_batched_c4():
-    """The 64-instance batch (about 6e7 unknowns) in one persistent launch; every
-    instance converges and sampled instances (one per size class) meet the
-    relative residual against the oracle's own CSR matrix."""
+@pytest.mark.parametrize("pc", ["cheb", "mg"])
+def test_fullsize_batched_c4(pc):
+    """The 64-instance batch (about 6e7 unknowns) in one persistent launch, with the
+    Chebyshev and the multigrid preconditioner; every instance converges and sampled
+    instances (one per size class) meet the relative residual against the oracle's
+    own CSR matrix."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     import __graft_entry__ as ge
@@ -184,7 +186,7 @@ def test_fullsize_batched_c4():
     grids = [ThermalGrid.from_stack(i.nx, i.ny, i.stack) for i in insts]
     powers = [torch.from_numpy(i.power).cuda() for i in insts]
     Ts = [torch.empty(i.n, dtype=torch.float64, device="cuda") for i in insts]
-    stats = solve_batched(grids, powers, Ts, tol_rel=1e-8, precond="cheb", cheb_degree=30)
+    stats = solve_batched(grids, powers, Ts, tol_rel=1e-8, precond=pc, cheb_degree=30)
     assert all(s["status"] == 0 and s["rel_res"] <= 1e-8 for s in stats)
     seen = set()
     for inst, T in zip(insts, Ts):

@@ -664,6 +664,32 @@ def test_batched_matches_oracle(mode, pc):
         assert osolve.rise_relative_error(T.cpu().numpy(), ref, inst.stack.t_amb) <= 1e-6
 
 
+def test_batched_multigrid_matches_oracle():
+    """The multigrid V-cycle inside the persistent batched kernel: uneven instances
+    (the 64-stack recipe at 1/4 size: 32^2 x 4 to 128^2 x 8, hierarchies of 3 to 5
+    levels in the same phases), one of them with a per-cell conductivity map; every
+    instance against the oracle, and the same answers as the instances solved one
+    after another through the single-grid multigrid path."""
+    from paper_2606_17850_gb300 import solve_batched
+    insts = ti.c4_instances(n=9, scale=4)
+    grids = [grid_of(i.nx, i.ny, i.stack) for i in insts]
+    kmap = _kmap(insts[0].stack, insts[0].nx, insts[0].ny, 31)
+    grids[0].set_conductivity_map(cuda(kmap))
+    powers = [cuda(i.power) for i in insts]
+    Ts = [torch.empty(i.n, dtype=torch.float64, device="cuda") for i in insts]
+    stats = solve_batched(grids, powers, Ts, tol_rel=1e-10, precond="mg")
+    assert len({(i.nx, i.stack.L) for i in insts}) > 2
+    for j, (inst, T, s) in enumerate(zip(insts, Ts, stats)):
+        ref = osolve.steady(inst.nx, inst.ny, inst.stack, inst.power.astype(np.float64),
+                            k_cell=kmap if j == 0 else None)
+        assert s["status"] == 0 and s["rel_res"] <= 1e-10, (j, s)
+        assert osolve.rise_relative_error(T.cpu().numpy(), ref, inst.stack.t_amb) <= 1e-6, j
+    Ts2 = [torch.empty(i.n, dtype=torch.float64, device="cuda") for i in insts]
+    solve_batched(grids, powers, Ts2, tol_rel=1e-10, precond="mg", batched_mode=1)
+    for T, T2, inst in zip(Ts, Ts2, insts):
+        assert (T - T2).abs().max().item() <= 1e-7 * (T2 - inst.stack.t_amb).abs().max().item()
+
+
 def test_batched_conductivity_map_and_ragged_tiles():
     """One persistent launch over instances with a per-cell conductivity map (per-face
     kernels), ragged 128 x 8 tiles (nx = 132, ny = 13) and the layer-table kernels;
