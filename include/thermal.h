@@ -361,6 +361,11 @@ th_status thermal_grad(thermal_grid* g, const double* T, const double* dJdT, voi
  * T buffer of its own (a handle or a T pointer that appears twice is TH_EINVAL; to
  * solve several power maps on one geometry, create one grid per map).  The power
  * maps may be shared.
+ * With batched_mode 0 the batch runs as one persistent cooperative launch when every
+ * grid has nx % 4 == 0, the precision is not TH_PREC_FP64 and the preconditioner is
+ * none, Jacobi, Chebyshev or multigrid (multigrid: every instance at most 8 layers
+ * and max(nx, ny) > 8); otherwise the instances run one after another through the
+ * single-grid solver, with the same results up to rounding order.
  */
 th_status thermal_solve_batched(thermal_grid* const* grids, int n, const void* const* power,
                                 int power_dtype, double* const* T, const thermal_solve_opts* opts,
