@@ -14,6 +14,12 @@ equations and algorithms:
   of the method's result), relative residuals, the error metric of Sec. 5.1.
 * ``adjoint``        - the log-sum-exp hotspot objective and its adjoint gradient
   with respect to the power map and the per-layer conductivities.
+* ``precision``      - the reduced-precision pieces of the paper's adaptive scheme
+  (Sec. 4.4): Quad-Diag storage (Sec. 4.2), the FP32/16 product of Algorithm 3 and
+  the early-to-late stage switch, Eqs. (switch_a-c).
+* ``multigrid``      - the geometric multigrid V-cycle (not in the paper: the
+  alternative preconditioner), aggregation, Galerkin coarse operators, damped
+  z-line Jacobi smoothing and an exact coarsest solve.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference
 leg of ``bench.py`` may import it.  The GPU library never imports, links or runs

@@ -666,12 +666,12 @@ def test_batched_matches_oracle(mode, pc):
 
 def test_batched_multigrid_matches_oracle():
     """The multigrid V-cycle inside the persistent batched kernel: uneven instances
-    (the 64-stack recipe at 1/4 size: 32^2 x 4 to 128^2 x 8, hierarchies of 3 to 5
+    (the 64-stack recipe at 1/8 size: 16^2 x 4 to 64^2 x 8, hierarchies of 3 to 5
     levels in the same phases), one of them with a per-cell conductivity map; every
     instance against the oracle, and the same answers as the instances solved one
     after another through the single-grid multigrid path."""
     from paper_2606_17850_gb300 import solve_batched
-    insts = ti.c4_instances(n=9, scale=4)
+    insts = ti.c4_instances(n=9, scale=8)
     grids = [grid_of(i.nx, i.ny, i.stack) for i in insts]
     kmap = _kmap(insts[0].stack, insts[0].nx, insts[0].ny, 31)
     grids[0].set_conductivity_map(cuda(kmap))
