@@ -45,11 +45,15 @@
 // test hook: limit of the wait on a barrier phase that nothing completes
 #define TB_TEST_WAIT_NS 2000000ull
 
+// The step works on layer pairs (2k, 2k+1): the per-layer constants of a pair sit
+// side by side, as the operands of Blackwell's paired FP32 instructions, and the
+// in-plane faces are stored negated (d - gx (v_E + v_W) ... becomes fused
+// multiply-adds without a negation).
 template <int LMAX>
-struct TBParams {
-  float c1[TB_H], c2[TB_H];     // Chebyshev step coefficients of this chunk
-  float d[LMAX];                // diagonal of a cell with all four in-plane faces
-  float gx[LMAX], gy[LMAX];     // in-plane face conductances per layer
+struct __align__(8) TBParams {
+  float2 c1[TB_H], c2[TB_H];    // Chebyshev step coefficients of this chunk, (c, c)
+  float2 d[LMAX / 2];           // diagonal of a cell with all four in-plane faces
+  float2 ngx[LMAX / 2], ngy[LMAX / 2];  // -(in-plane face conductances)
   float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
   float z1s;                    // first chunk: z_1 = z1s D^-1 r, formed from the staged r
@@ -127,6 +131,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
   if (ld_int(&ctl->done)) return;
   constexpr int H = STEPS;
   constexpr int TX = TB_EX - 2 * H, TY = EY - 2 * H;  // interior of a tile
+  static_assert(LMAX % 2 == 0, "layers are processed in pairs");
+  constexpr int LP = LMAX / 2;  // layer pairs
   constexpr int PL = EY * TB_EX;  // floats per layer plane
   constexpr int SL = EY * TB_BW;  // floats per staged layer
   extern __shared__ __align__(128) float tb_dyn[];
@@ -206,20 +212,25 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     // over z_{m-1}, so no register moves are needed.  A row that skips a step keeps
     // stale values in the swapped arrays; it lies outside the valid region from then
     // on and is read only by rows that are outside it too.
-    float za[LMAX], zb[LMAX], rr[LMAX], inv[LMAX], rs[LMAX];
+    // Registers hold layer pairs (2k, 2k+1); iv is 1/D (last chunk, unscaled
+    // residual) or -1/D (the scaled inner chunks' fused multiply-add).
+    float2 za[LP], zb[LP], rr[LP], iv[LP], rs[LP];
     const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
-    for (int z = 0; z < LMAX; ++z) {
+    for (int k = 0; k < LP; ++k) {
+      const int z0 = 2 * k, z1 = 2 * k + 1;
       if (!FIRST) {
-        za[z] = stage[z * SL + st];
-        zb[z] = stage[(LMAX + z) * SL + st];
+        za[k] = make_float2(stage[z0 * SL + st], stage[z1 * SL + st]);
+        zb[k] = make_float2(stage[(LMAX + z0) * SL + st], stage[(LMAX + z1) * SL + st]);
       }
-      rr[z] = stage[(2 * LMAX + z) * SL + st];
-      inv[z] = P.invd[nxf + 3 * nyf][z];
-      rs[z] = (SCALED && !LAST) ? rr[z] * inv[z] : rr[z];  // D^-1 r, fixed over the chunk
+      rr[k] = make_float2(stage[(2 * LMAX + z0) * SL + st], stage[(2 * LMAX + z1) * SL + st]);
+      const float i0 = P.invd[nxf + 3 * nyf][z0], i1 = P.invd[nxf + 3 * nyf][z1];
+      iv[k] = (SCALED && !LAST) ? make_float2(-i0, -i1) : make_float2(i0, i1);
+      rs[k] = (SCALED && !LAST) ? make_float2(rr[k].x * i0, rr[k].y * i1) : rr[k];  // D^-1 r, fixed
       if (FIRST) {
-        za[z] = (SCALED ? rr[z] * inv[z] : rr[z]) * P.z1s;
-        zb[z] = 0.f;
+        za[k] = SCALED ? make_float2(rr[k].x * i0 * P.z1s, rr[k].y * i1 * P.z1s)
+                       : make_float2(rr[k].x * P.z1s, rr[k].y * P.z1s);
+        zb[k] = make_float2(0.f, 0.f);
       }
     }
     __syncthreads();  // staging buffer consumed by every thread
@@ -233,26 +244,33 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     // neighbour offsets inside a plane; a missing neighbour reads the cell itself
     const int oR = tid + ((gx + 1 < d.nx) ? 1 : 0), oL = tid - ((gx > 0) ? 1 : 0);
     const int oU = tid + ((gy + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gy > 0) ? TB_EX : 0);
-    auto step = [&](const float (&C)[LMAX], float (&N)[LMAX], const int j) {
-      float* pl = plane + (j & 1) * LMAX * PL;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    auto step = [&](const float2 (&C)[LP], float2 (&N)[LP], const int j) {
+      float2* pl = reinterpret_cast<float2*>(plane) + (j & 1) * LP * PL;
 #pragma unroll
-      for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = C[z];
+      for (int k = 0; k < LP; ++k) pl[k * PL + tid] = C[k];
       __syncthreads();
       // rows outside the shrinking valid region skip the step as whole warps
       const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
       if (upd) {
 #pragma unroll
-        for (int z = 0; z < LMAX; ++z) {
-          const float v = C[z];
-          const float* q = pl + z * PL;
-          float a = P.d[z] * v;
-          a = fmaf(-P.gx[z], q[oR] + q[oL], a);
-          a = fmaf(-P.gy[z], q[oU] + q[oD], a);
-          if (z + 1 < LMAX) a = fmaf(-P.gzu[z], C[z + 1 < LMAX ? z + 1 : z], a);
-          if (z > 0) a = fmaf(-P.gzd[z], C[z > 0 ? z - 1 : z], a);
+        for (int k = 0; k < LP; ++k) {
+          const float2 v = C[k];
+          const float2* q = pl + k * PL;
+          // per layer, in this order: d v, then the x pair, the y pair, the layer
+          // above and the layer below (each lane rounds as the one-layer form would)
+          float2 a = __fmul2_rn(P.d[k], v);
+          a = __ffma2_rn(P.ngx[k], __fadd2_rn(q[oR], q[oL]), a);
+          a = __ffma2_rn(P.ngy[k], __fadd2_rn(q[oU], q[oD]), a);
+          a.x = fmaf(-P.gzu[2 * k], v.y, a.x);
+          if (2 * k + 2 < LMAX) a.y = fmaf(-P.gzu[2 * k + 1], C[k + 1 < LP ? k + 1 : k].x, a.y);
+          if (k > 0) a.x = fmaf(-P.gzd[2 * k], C[k > 0 ? k - 1 : k].y, a.x);
+          a.y = fmaf(-P.gzd[2 * k + 1], v.x, a.y);
           // the last chunk keeps r for z^T r and scales the residual instead
-          const float res = !SCALED ? rr[z] - a : (LAST ? (rr[z] - a) * inv[z] : fmaf(-inv[z], a, rs[z]));
-          N[z] = fmaf(P.c2[j], res, fmaf(P.c1[j], v - N[z], v));
+          const float2 res = !SCALED ? __ffma2_rn(a, m1, rr[k])
+                                     : (LAST ? __fmul2_rn(__ffma2_rn(a, m1, rr[k]), iv[k])
+                                             : __ffma2_rn(iv[k], a, rs[k]));
+          N[k] = __ffma2_rn(P.c2[j], res, __ffma2_rn(P.c1[j], __ffma2_rn(N[k], m1, v), v));
         }
       }
     };
@@ -262,8 +280,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       else step(za, zb, j);
     }
     // the interior columns hold z_{m+STEPS} and z_{m+STEPS-1}
-    const float(&cur)[LMAX] = (STEPS & 1) ? zb : za;
-    const float(&prv)[LMAX] = (STEPS & 1) ? za : zb;
+    const float2(&cur)[LP] = (STEPS & 1) ? zb : za;
+    const float2(&prv)[LP] = (STEPS & 1) ? za : zb;
     const bool interior = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
     if (interior) {
       const long long base = (long long)gx + (long long)d.nx * gy;
@@ -271,9 +289,10 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       for (int z = 0; z < LMAX; ++z) {
         if (z < L) {
           const long long i = base + d.pxy * z;
-          out_cur[i] = cur[z];
-          if (out_prev) out_prev[i] = prv[z];
-          if (LAST) part[0] += rr[z] * cur[z];
+          const float c = (z & 1) ? cur[z >> 1].y : cur[z >> 1].x;
+          out_cur[i] = c;
+          if (out_prev) out_prev[i] = (z & 1) ? prv[z >> 1].y : prv[z >> 1].x;
+          if (LAST) part[0] += ((z & 1) ? rr[z >> 1].y : rr[z >> 1].x) * c;
         }
       }
     }

@@ -545,31 +545,35 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   TBParams<LM> prm;
   std::memset(&prm, 0, sizeof(prm));
   for (int j = 0; j < TB_H; ++j) {
-    prm.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
-    prm.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+    const float c1 = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f, c2 = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+    prm.c1[j] = make_float2(c1, c1);
+    prm.c2[j] = make_float2(c2, c2);
   }
   prm.z1s = (float)P.inv_theta;
   prm.expire_test = P.expire_test;
   const LayerTab& T = g->tab_host;
   const int L = P.d.L;
+  float* dz = &prm.d[0].x;  // layer z at component z of the pair arrays
+  float* ngx = &prm.ngx[0].x;
+  float* ngy = &prm.ngy[0].x;
   for (int z = 0; z < L; ++z) {
-    const float sz = T.s32[z];
-    prm.gx[z] = T.gxl[z];
-    prm.gy[z] = T.gyl[z];
+    const float sz = T.s32[z], gx = T.gxl[z], gy = T.gyl[z];
+    ngx[z] = -gx;
+    ngy[z] = -gy;
     prm.gzu[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
     prm.gzd[z] = (z > 0) ? T.gzl[z - 1] : 0.f;
     // diagonal summed in the one-step kernels' order: s, +x, -x, +y, -y, +z, -z
     for (int nyf = 0; nyf < 3; ++nyf)
       for (int nxf = 0; nxf < 3; ++nxf) {
         float dg = sz;
-        dg += nxf >= 1 ? prm.gx[z] : 0.f;
-        dg += nxf >= 2 ? prm.gx[z] : 0.f;
-        dg += nyf >= 1 ? prm.gy[z] : 0.f;
-        dg += nyf >= 2 ? prm.gy[z] : 0.f;
+        dg += nxf >= 1 ? gx : 0.f;
+        dg += nxf >= 2 ? gx : 0.f;
+        dg += nyf >= 1 ? gy : 0.f;
+        dg += nyf >= 2 ? gy : 0.f;
         dg += prm.gzu[z];
         dg += prm.gzd[z];
         prm.invd[nxf + 3 * nyf][z] = 1.0f / dg;
-        if (nxf == 2 && nyf == 2) prm.d[z] = dg;
+        if (nxf == 2 && nyf == 2) dz[z] = dg;
       }
   }
   CUtensorMap mc, mp, mr;
