@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
 #define TBF_EY 24
 
 template <int LMAX>
-struct TBFParams {
-  float c1[TB_H], c2[TB_H];  // Chebyshev step coefficients of this chunk
+struct __align__(8) TBFParams {
+  float2 c1[TB_H], c2[TB_H];  // Chebyshev step coefficients of this chunk, (c, c)
   float s[LMAX];             // per-layer diagonal term: h dx dy (top) + c dx dy dz / dt
   float z1s;                 // first chunk: z_1 = z1s D^-1 r
   int expire_test;           // test hook of the bounded wait (as in k_cheb_tb)
@@ -349,7 +349,9 @@ __global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
   constexpr int EY = TBF_EY;
   constexpr int H = STEPS;
   constexpr int TX = TB_EX - 2 * H, TY = EY - 2 * H;  // interior of a tile
-  constexpr int PL = EY * TB_EX;                        // floats per layer plane
+  static_assert(LMAX % 2 == 0, "layers are processed in pairs");
+  constexpr int LP = LMAX / 2;
+  constexpr int PL = EY * TB_EX;                        // floats per layer plane (float2 per pair plane)
   constexpr int SL = EY * TB_BW;                        // floats per staged layer
   extern __shared__ __align__(128) float tb_dyn[];
   float* tb_sm = tb_dyn + (((128u - (tb_smem(tb_dyn) & 127u)) & 127u) >> 2);  // 128-byte aligned
@@ -420,18 +422,20 @@ __global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
     const int gyi = ty * TY - H + ey;
     const int st = ey * TB_BW + ex + (x0 - (x0 & ~3));  // this column in a staged layer
     const bool inside = gxi >= 0 && gxi < d.nx && gyi >= 0 && gyi < d.ny;
-    float za[LMAX], zb[LMAX], rr[LMAX], inv[LMAX], fx[LMAX], fy[LMAX], fyd[LMAX], fz[LMAX];
+    // layer pairs (k, k + LP) as in k_cheb_tb: PR(a, z) is layer z of pair array a
+    float2 za[LP], zb[LP], rr[LP], inv[LP], fx[LP], fy[LP], fyd[LP], fz[LP];
+#define PR(a, z) ((z) < LP ? (a)[(z) < LP ? (z) : 0].x : (a)[(z) >= LP ? (z) - LP : 0].y)
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
       if (!FIRST) {
-        za[z] = stage[z * SL + st];
-        zb[z] = stage[(LMAX + z) * SL + st];
+        PR(za, z) = stage[z * SL + st];
+        PR(zb, z) = stage[(LMAX + z) * SL + st];
       }
-      rr[z] = stage[(2 * LMAX + z) * SL + st];
-      fx[z] = stage[(3 * LMAX + z) * SL + st];
-      fy[z] = stage[(4 * LMAX + z) * SL + st];
-      fyd[z] = ey > 0 ? stage[(4 * LMAX + z) * SL + st - TB_BW] : 0.f;
-      fz[z] = stage[(5 * LMAX + z) * SL + st];
+      PR(rr, z) = stage[(2 * LMAX + z) * SL + st];
+      PR(fx, z) = stage[(3 * LMAX + z) * SL + st];
+      PR(fy, z) = stage[(4 * LMAX + z) * SL + st];
+      PR(fyd, z) = ey > 0 ? stage[(4 * LMAX + z) * SL + st - TB_BW] : 0.f;
+      PR(fz, z) = stage[(5 * LMAX + z) * SL + st];
     }
     // The diagonal in the one-step kernels' order: s, +x, -x, +y, -y, +z, -z.  A first
     // chunk forms z_1 = z1s D^-1 r on every column of the grown tile (step 0 reads the
@@ -441,22 +445,24 @@ __global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
     const long long cbase = (long long)gxi + (long long)d.nx * gyi;
 #pragma unroll
     for (int z = 0; z < LMAX; ++z) {
-      const float fxw = __shfl_up_sync(0xffffffffu, fx[z], 1);
+      const float fxz = PR(fx, z);
+      const float fxw = __shfl_up_sync(0xffffffffu, fxz, 1);
       float dg = P.s[z];
-      dg += fx[z];
+      dg += fxz;
       dg += ex > 0 ? fxw : 0.f;
-      dg += fy[z];
-      dg += fyd[z];
-      dg += fz[z];
-      dg += z > 0 ? fz[z > 0 ? z - 1 : 0] : 0.f;
+      dg += PR(fy, z);
+      dg += PR(fyd, z);
+      dg += PR(fz, z);
+      dg += z > 0 ? PR(fz, z > 0 ? z - 1 : 0) : 0.f;
       float iv = 1.0f / dg;
       if (ring && z < L) iv = __ldg(invd + cbase + d.pxy * z);
-      inv[z] = (z < L && inside) ? iv : 0.f;  // columns outside the grid stay 0
+      PR(inv, z) = (z < L && inside) ? iv : 0.f;  // columns outside the grid stay 0
       if (FIRST) {
-        za[z] = rr[z] * inv[z] * P.z1s;
-        zb[z] = 0.f;
+        PR(za, z) = PR(rr, z) * PR(inv, z) * P.z1s;
+        PR(zb, z) = 0.f;
       }
     }
+#undef PR
     __syncthreads();  // staging buffer consumed by every thread
     const int tn = t + gridDim.x;
     int txn = tx, tyn = ty;
@@ -467,26 +473,31 @@ __global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
     }
     const int oR = tid + ((gxi + 1 < d.nx) ? 1 : 0), oL = tid - ((gxi > 0) ? 1 : 0);
     const int oU = tid + ((gyi + 1 < d.ny) ? TB_EX : 0), oD = tid - ((gyi > 0) ? TB_EX : 0);
-    auto step = [&](const float (&C)[LMAX], float (&N)[LMAX], const int j) {
-      float* pl = plane + (j & 1) * LMAX * PL;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    auto step = [&](const float2 (&C)[LP], float2 (&N)[LP], const int j) {
+      float2* pl = reinterpret_cast<float2*>(plane) + (j & 1) * LP * PL;
 #pragma unroll
-      for (int z = 0; z < LMAX; ++z) pl[z * PL + tid] = C[z];
+      for (int k = 0; k < LP; ++k) pl[k * PL + tid] = C[k];
       __syncthreads();
       const bool upd = inside && ex > j && ex < TB_EX - 1 - j && ey > j && ey < EY - 1 - j;
 #pragma unroll
-      for (int z = 0; z < LMAX; ++z) {
-        const float fxw = __shfl_up_sync(0xffffffffu, fx[z], 1);  // every lane: outside the branch
+      for (int k = 0; k < LP; ++k) {
+        // the west lane's +x faces (every lane: outside the branch)
+        const float2 fxw = make_float2(__shfl_up_sync(0xffffffffu, fx[k].x, 1), __shfl_up_sync(0xffffffffu, fx[k].y, 1));
         if (upd) {
-          const float v = C[z];
-          const float* q = pl + z * PL;
-          float a = fx[z] * q[oR];
-          a = fmaf(fxw, q[oL], a);
-          a = fmaf(fy[z], q[oU], a);
-          a = fmaf(fyd[z], q[oD], a);
-          if (z + 1 < LMAX) a = fmaf(fz[z], C[z + 1 < LMAX ? z + 1 : z], a);
-          if (z > 0) a = fmaf(fz[z > 0 ? z - 1 : 0], C[z > 0 ? z - 1 : z], a);
-          const float res = fmaf(inv[z], rr[z] + a, -v);  // D^-1 (r - A v)
-          N[z] = fmaf(P.c2[j], res, fmaf(P.c1[j], v - N[z], v));
+          const float2 v = C[k];
+          const float2* q = pl + k * PL;
+          // per layer: +x, -x, +y, -y, the layer above, the layer below
+          float2 a = __fmul2_rn(fx[k], q[oR]);
+          a = __ffma2_rn(fxw, q[oL], a);
+          a = __ffma2_rn(fy[k], q[oU], a);
+          a = __ffma2_rn(fyd[k], q[oD], a);
+          if (k + 1 < LP) a = __ffma2_rn(fz[k], C[k + 1 < LP ? k + 1 : k], a);
+          else a.x = fmaf(fz[k].x, C[0].y, a.x);  // layer LP - 1 below LP; the top layer has none
+          if (k > 0) a = __ffma2_rn(fz[k > 0 ? k - 1 : k], C[k > 0 ? k - 1 : k], a);
+          else a.y = fmaf(fz[LP - 1].x, C[LP - 1].x, a.y);  // layer LP above LP - 1; layer 0 has none
+          const float2 res = __ffma2_rn(inv[k], __fadd2_rn(rr[k], a), __fmul2_rn(v, m1));  // D^-1 (r - A v)
+          N[k] = __ffma2_rn(P.c2[j], res, __ffma2_rn(P.c1[j], __ffma2_rn(N[k], m1, v), v));
         }
       }
     };
@@ -495,8 +506,8 @@ __global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
       if (j & 1) step(zb, za, j);
       else step(za, zb, j);
     }
-    const float(&cur)[LMAX] = (STEPS & 1) ? zb : za;
-    const float(&prv)[LMAX] = (STEPS & 1) ? za : zb;
+    const float2(&cur)[LP] = (STEPS & 1) ? zb : za;
+    const float2(&prv)[LP] = (STEPS & 1) ? za : zb;
     const bool interior = inside && ex >= H && ex < H + TX && ey >= H && ey < H + TY;
     if (interior) {
       const long long base = (long long)gxi + (long long)d.nx * gyi;
@@ -504,9 +515,11 @@ __global__ void __launch_bounds__(TB_EX * TBF_EY, 1)
       for (int z = 0; z < LMAX; ++z) {
         if (z < L) {
           const long long i = base + d.pxy * z;
-          out_cur[i] = cur[z];
-          if (out_prev) out_prev[i] = prv[z];
-          if (LAST) part[0] += rr[z] * cur[z];
+          const int k = z < LP ? z : z - LP;
+          const float c = z < LP ? cur[k].x : cur[k].y;
+          out_cur[i] = c;
+          if (out_prev) out_prev[i] = z < LP ? prv[k].x : prv[k].y;
+          if (LAST) part[0] += (z < LP ? rr[k].x : rr[k].y) * c;
         }
       }
     }

@@ -604,8 +604,9 @@ static th_status tbf_launch(const Plan& P, const VecSet<float>& V, cudaStream_t 
   TBFParams<LM> prm;
   std::memset(&prm, 0, sizeof(prm));
   for (int j = 0; j < TB_H; ++j) {
-    prm.c1[j] = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f;
-    prm.c2[j] = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+    const float c1 = j < c.steps ? (float)P.c1[c.m0 + j] : 0.f, c2 = j < c.steps ? (float)P.c2[c.m0 + j] : 0.f;
+    prm.c1[j] = make_float2(c1, c1);
+    prm.c2[j] = make_float2(c2, c2);
   }
   for (int z = 0; z < P.d.L; ++z) prm.s[z] = g->tab_host.s32[z];
   prm.z1s = (float)P.inv_theta;
