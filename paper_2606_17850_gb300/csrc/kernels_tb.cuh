@@ -45,16 +45,17 @@
 // test hook: limit of the wait on a barrier phase that nothing completes
 #define TB_TEST_WAIT_NS 2000000ull
 
-// The step works on layer pairs (2k, 2k+1): the per-layer constants of a pair sit
-// side by side, as the operands of Blackwell's paired FP32 instructions, and the
-// in-plane faces are stored negated (d - gx (v_E + v_W) ... becomes fused
-// multiply-adds without a negation).
+// The step works on layer pairs (k, k + LMAX/2): the per-layer constants of a pair
+// sit side by side, as the operands of Blackwell's paired FP32 instructions, so a
+// pair's vertical neighbours are the pairs k + 1 and k - 1 (except across the
+// middle of the column, one scalar term at each end); the faces are stored negated
+// (d v - gx (v_E + v_W) - ... becomes fused multiply-adds without a negation).
 template <int LMAX>
 struct __align__(8) TBParams {
   float2 c1[TB_H], c2[TB_H];    // Chebyshev step coefficients of this chunk, (c, c)
   float2 d[LMAX / 2];           // diagonal of a cell with all four in-plane faces
   float2 ngx[LMAX / 2], ngy[LMAX / 2];  // -(in-plane face conductances)
-  float gzu[LMAX], gzd[LMAX];   // face to the layer above / below (0 at the stack ends)
+  float2 ngzu[LMAX / 2], ngzd[LMAX / 2];  // -(face to the layer above / below), 0 at the ends
   float invd[9][LMAX];          // 1 / diagonal for (x faces present) + 3 (y faces present)
   float z1s;                    // first chunk: z_1 = z1s D^-1 r, formed from the staged r
   int expire_test;              // test hook: the first wait of each CTA runs out (see below)
@@ -212,13 +213,13 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
     // over z_{m-1}, so no register moves are needed.  A row that skips a step keeps
     // stale values in the swapped arrays; it lies outside the valid region from then
     // on and is read only by rows that are outside it too.
-    // Registers hold layer pairs (2k, 2k+1); iv is 1/D (last chunk, unscaled
+    // Registers hold layer pairs (k, k + LP); iv is 1/D (last chunk, unscaled
     // residual) or -1/D (the scaled inner chunks' fused multiply-add).
     float2 za[LP], zb[LP], rr[LP], iv[LP], rs[LP];
     const int nxf = (gx + 1 < d.nx) + (gx > 0), nyf = (gy + 1 < d.ny) + (gy > 0);
 #pragma unroll
     for (int k = 0; k < LP; ++k) {
-      const int z0 = 2 * k, z1 = 2 * k + 1;
+      const int z0 = k, z1 = k + LP;
       if (!FIRST) {
         za[k] = make_float2(stage[z0 * SL + st], stage[z1 * SL + st]);
         zb[k] = make_float2(stage[(LMAX + z0) * SL + st], stage[(LMAX + z1) * SL + st]);
@@ -262,10 +263,10 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
           float2 a = __fmul2_rn(P.d[k], v);
           a = __ffma2_rn(P.ngx[k], __fadd2_rn(q[oR], q[oL]), a);
           a = __ffma2_rn(P.ngy[k], __fadd2_rn(q[oU], q[oD]), a);
-          a.x = fmaf(-P.gzu[2 * k], v.y, a.x);
-          if (2 * k + 2 < LMAX) a.y = fmaf(-P.gzu[2 * k + 1], C[k + 1 < LP ? k + 1 : k].x, a.y);
-          if (k > 0) a.x = fmaf(-P.gzd[2 * k], C[k > 0 ? k - 1 : k].y, a.x);
-          a.y = fmaf(-P.gzd[2 * k + 1], v.x, a.y);
+          if (k + 1 < LP) a = __ffma2_rn(P.ngzu[k], C[k + 1 < LP ? k + 1 : k], a);
+          else a.x = fmaf(P.ngzu[k].x, C[0].y, a.x);  // layer LP - 1 below LP; the top layer has none
+          if (k > 0) a = __ffma2_rn(P.ngzd[k], C[k > 0 ? k - 1 : k], a);
+          else a.y = fmaf(P.ngzd[0].y, C[LP - 1].x, a.y);  // layer LP above LP - 1; layer 0 has none
           // the last chunk keeps r for z^T r and scales the residual instead
           const float2 res = !SCALED ? __ffma2_rn(a, m1, rr[k])
                                      : (LAST ? __fmul2_rn(__ffma2_rn(a, m1, rr[k]), iv[k])
@@ -289,10 +290,11 @@ __global__ void __launch_bounds__(TB_EX * EY, 1)
       for (int z = 0; z < LMAX; ++z) {
         if (z < L) {
           const long long i = base + d.pxy * z;
-          const float c = (z & 1) ? cur[z >> 1].y : cur[z >> 1].x;
+          const int k = z < LP ? z : z - LP;
+          const float c = z < LP ? cur[k].x : cur[k].y;
           out_cur[i] = c;
-          if (out_prev) out_prev[i] = (z & 1) ? prv[z >> 1].y : prv[z >> 1].x;
-          if (LAST) part[0] += ((z & 1) ? rr[z >> 1].y : rr[z >> 1].x) * c;
+          if (out_prev) out_prev[i] = z < LP ? prv[k].x : prv[k].y;
+          if (LAST) part[0] += (z < LP ? rr[k].x : rr[k].y) * c;
         }
       }
     }

@@ -553,15 +553,15 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
   prm.expire_test = P.expire_test;
   const LayerTab& T = g->tab_host;
   const int L = P.d.L;
-  float* dz = &prm.d[0].x;  // layer z at component z of the pair arrays
-  float* ngx = &prm.ngx[0].x;
-  float* ngy = &prm.ngy[0].x;
+  // layer z is component (z < LM/2 ? x : y) of pair z % (LM/2)
+  auto at = [](float2* a, int z) -> float& { return z < LM / 2 ? a[z].x : a[z - LM / 2].y; };
   for (int z = 0; z < L; ++z) {
     const float sz = T.s32[z], gx = T.gxl[z], gy = T.gyl[z];
-    ngx[z] = -gx;
-    ngy[z] = -gy;
-    prm.gzu[z] = (z + 1 < L) ? T.gzl[z] : 0.f;
-    prm.gzd[z] = (z > 0) ? T.gzl[z - 1] : 0.f;
+    const float gzu = (z + 1 < L) ? T.gzl[z] : 0.f, gzd = (z > 0) ? T.gzl[z - 1] : 0.f;
+    at(prm.ngx, z) = -gx;
+    at(prm.ngy, z) = -gy;
+    at(prm.ngzu, z) = -gzu;
+    at(prm.ngzd, z) = -gzd;
     // diagonal summed in the one-step kernels' order: s, +x, -x, +y, -y, +z, -z
     for (int nyf = 0; nyf < 3; ++nyf)
       for (int nxf = 0; nxf < 3; ++nxf) {
@@ -570,10 +570,10 @@ static th_status tb_launch(const Plan& P, const VecSet<float>& V, cudaStream_t s
         dg += nxf >= 2 ? gx : 0.f;
         dg += nyf >= 1 ? gy : 0.f;
         dg += nyf >= 2 ? gy : 0.f;
-        dg += prm.gzu[z];
-        dg += prm.gzd[z];
+        dg += gzu;
+        dg += gzd;
         prm.invd[nxf + 3 * nyf][z] = 1.0f / dg;
-        if (nxf == 2 && nyf == 2) dz[z] = dg;
+        if (nxf == 2 && nyf == 2) at(prm.d, z) = dg;
       }
   }
   CUtensorMap mc, mp, mr;
