@@ -44,7 +44,13 @@ def cuda(a, dtype=None):
 # nx % 4 != 0 runs the scalar kernels, nx % 4 == 0 the vectorised z-walk kernels
 SHAPES = [(70, 19, "c1"), (37, 45, "c2"), (33, 9, "mol"), (5, 3, "c2"),
           (72, 19, "c1"), (36, 45, "c2"), (132, 9, "mol"), (4, 3, "c2")]
-STACKS = {"c1": ti.stack_c1, "c2": ti.stack_c2, "mol": ti.stack_mol}
+STACKS = {"c1": ti.stack_c1, "c2": ti.stack_c2, "mol": ti.stack_mol,
+          # 5, 6 and 7 layers: the fused kernels pair layer k with layer k + 4, so these
+          # put real and zero-padded layers in the same pair
+          "l5": lambda: ti.Stack((ti.si(), ti.bond(), ti.si(name="si1"), ti.tim(), ti.cu()), h=1e4),
+          "l6": ti.stack_c1_split_cu,
+          "l7": lambda: ti.Stack((ti.si(name="si0"), ti.bond(name="b0"), ti.si(name="si1"), ti.bond(name="b1"),
+                                  ti.tim(), ti.cu(500.0, "cu0"), ti.cu(500.0, "cu1")), h=1e4)}
 
 
 # ----------------------------------------------------------------- A1: setup
@@ -289,11 +295,11 @@ def test_chebyshev_chain_from_oracle_lanczos(nx, ny, mk, m, scaled):
 
 @pytest.mark.parametrize("k", [2, 5, 8, 12])
 @pytest.mark.parametrize("dt", [0.0, 1e-4])
-@pytest.mark.parametrize("mk", ["c2", "c1", "mol"])
+@pytest.mark.parametrize("mk", ["c2", "c1", "mol", "l5", "l6", "l7"])
 def test_fused_chebyshev_equals_stepwise(k, dt, mk):
     """Temporal blocking (1..4 steps per launch, TMA-staged tiles) computes the same
     polynomial as one launch per step: tiles with ragged x/y tails, 1..3 chunks,
-    8 layers, 4 layers (zero-padded to 8) and 10 layers (the 12-layer variant)."""
+    8 layers, 4 to 7 layers (zero-padded to 8) and 10 layers (the 12-layer variant)."""
     st = STACKS[mk]()
     nx, ny = 76, 37           # nx % 32 != 0 and ny % 16 != 0: partial tiles on both axes
     g = grid_of(nx, ny, st)
@@ -307,11 +313,11 @@ def test_fused_chebyshev_equals_stepwise(k, dt, mk):
 
 @pytest.mark.parametrize("k", [2, 5, 8, 12])
 @pytest.mark.parametrize("dt", [0.0, 1e-4])
-@pytest.mark.parametrize("mk", ["c2", "c1"])
+@pytest.mark.parametrize("mk", ["c2", "c1", "l5", "l7"])
 def test_fused_chebyshev_per_face_equals_stepwise(k, dt, mk):
     """Fused chunks on per-face arrays (a per-cell conductivity map; 32 x 24 tiles with
     the faces staged beside the vectors) compute the same polynomial as one launch per
-    step: ragged tiles on both axes, 8 layers and 4 layers (zero-padded)."""
+    step: ragged tiles on both axes, 8 layers and 4, 5 and 7 layers (zero-padded)."""
     st = STACKS[mk]()
     nx, ny = 76, 37
     g = grid_of(nx, ny, st)
