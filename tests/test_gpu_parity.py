@@ -306,9 +306,15 @@ def test_fused_chebyshev_equals_stepwise(k, dt, mk):
     r = cuda(ti.random_vector(nx * ny * st.L, 5).astype(np.float32))
     z1 = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=1)
     scale = z1.abs().max().item()
+    # The fused chunks take the product in expanded form, d v - sum_f g_f v_f, the
+    # one-step kernel in difference form, sum_f g_f (v - v_f); in steady state d is
+    # the sum of the faces, so the expanded form rounds at the level of d |v|: a few
+    # FP32 ulps of max|z| per step (the Jacobi-scaled terms are at most |v|), summed
+    # over the k - 1 steps.  Measured up to 1.2e-6 of max|z| (5 layers, steady, k 8).
+    tol = max(1e-6, 2.5e-7 * k)
     for fuse in (0, 2, 3, 4):
         zf = g.precond(r, dt, precond="cheb", cheb_degree=k, cheb_fuse=fuse)
-        assert (zf - z1).abs().max().item() <= 1e-6 * scale, fuse
+        assert (zf - z1).abs().max().item() <= tol * scale, fuse
 
 
 @pytest.mark.parametrize("k", [2, 5, 8, 12])
