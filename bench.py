@@ -702,7 +702,7 @@ def kernel_table(grid, n, reps, peak, peak_kind):
 
 # source files that define each profiled kernel: a committed DRAM-traffic figure is
 # used only while these files are unchanged
-KERNEL_SOURCES = {"cheb_tb4": ["kernels_tb.cuh"], "cheb_tbf3": ["kernels_tb.cuh"], "cheb_f32": ["kernels_v4.cuh"]}
+KERNEL_SOURCES = {"cheb_tb4": ["kernels_tb.cuh"], "cheb_tbf4": ["kernels_tb.cuh"], "cheb_f32": ["kernels_v4.cuh"]}
 
 
 def traffic_from_profiles(kernel):
