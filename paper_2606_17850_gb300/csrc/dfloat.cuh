@@ -86,6 +86,62 @@ __device__ __forceinline__ df ldf_mul(df a, df b) {
   return df_make(p, e);
 }
 
+// Two double-float values per operation (lanes x and y), on Blackwell's paired FP32
+// instructions: every helper below performs, lane by lane, the same round-to-nearest
+// operations in the same order as its one-value form above, so each lane's result is
+// bit-identical to it.  A difference x - y is the fused multiply-add y * (-1) + x
+// (exact product, one rounding: the same as the subtraction).
+struct df2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ df2 df2_make(float2 h, float2 l) {
+  df2 r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+__device__ __forceinline__ df2 df2_of(df a, df b) {
+  return df2_make(make_float2(a.hi, b.hi), make_float2(a.lo, b.lo));
+}
+__device__ __forceinline__ float2 f2_sub(float2 x, float2 y) {
+  return __ffma2_rn(y, make_float2(-1.f, -1.f), x);
+}
+
+// df_sub: TwoSum of (a.hi, -b.hi), low parts, Fast2Sum
+__device__ __forceinline__ df2 df2_sub(df2 a, df2 b) {
+  const float2 s = f2_sub(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);                           // s - a   (= (-b) rounded part)
+  const float2 e0 = f2_sub(f2_sub(a.hi, f2_sub(s, bb)), __fadd2_rn(b.hi, bb));  // (a - (s - bb)) + (-b - bb)
+  const float2 e = __fadd2_rn(e0, f2_sub(a.lo, b.lo));
+  const float2 h = __fadd2_rn(s, e);
+  return df2_make(h, f2_sub(e, f2_sub(h, s)));
+}
+
+// ldf_add: TwoSum of the high parts, the low parts added without renormalising
+__device__ __forceinline__ df2 ldf2_add(df2 a, df2 b) {
+  const float2 s = __fadd2_rn(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);
+  const float2 e0 = __fadd2_rn(f2_sub(a.hi, f2_sub(s, bb)), f2_sub(b.hi, bb));
+  return df2_make(s, __fadd2_rn(e0, __fadd2_rn(a.lo, b.lo)));
+}
+
+// ldf_sub: ldf_add of (a, -b)
+__device__ __forceinline__ df2 ldf2_sub(df2 a, df2 b) {
+  const float2 s = f2_sub(a.hi, b.hi);
+  const float2 bb = f2_sub(s, a.hi);
+  const float2 e0 = f2_sub(f2_sub(a.hi, f2_sub(s, bb)), __fadd2_rn(b.hi, bb));
+  return df2_make(s, __fadd2_rn(e0, f2_sub(a.lo, b.lo)));
+}
+
+// ldf_mul: exact high product and the two cross terms
+__device__ __forceinline__ df2 ldf2_mul(df2 a, df2 b) {
+  const float2 p = __fmul2_rn(a.hi, b.hi);
+  const float2 np = __fmul2_rn(p, make_float2(-1.f, -1.f));
+  const float2 e = __ffma2_rn(a.lo, b.hi, __ffma2_rn(a.hi, b.lo, __ffma2_rn(a.hi, b.hi, np)));
+  return df2_make(p, e);
+}
+
 // FP64 <-> double-float (used once per solve at the boundary, not in the loops)
 __host__ __device__ __forceinline__ void df_split(double v, float* h, float* l) {
   const float a = (float)v;

@@ -331,7 +331,9 @@ struct ResidInit {
 // Otherwise the per-face arrays: fh = FP32 high parts, fl = low parts g - (float)g
 // (zero on the domain boundary), six face products per cell.
 template <typename TP, int ZI, bool UNI>
-__global__ void __launch_bounds__(TH_BX* TH_BY4, UNI ? 3 : 2)  // layer table: 80 registers, three blocks per SM
+// two blocks per SM (128 registers): the layer-table form on paired instructions
+// spills at three (80 registers) and measured slower there (76.1 vs 72.3 us)
+__global__ void __launch_bounds__(TH_BX* TH_BY4, 2)
     k_residual_df_v4(Dims d, int zc, Ctl* ctl, const LayerTab* tab, Faces32 fh, Faces32 fl,
                      const float* __restrict__ th_hi, const float* __restrict__ th_lo, const TP* const* ptab,
                      const float* __restrict__ thn_hi, const float* __restrict__ thn_lo, float* __restrict__ r,
@@ -397,6 +399,50 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, UNI ? 3 : 2)  // layer table: 8
         }
       }
       float o[4];
+      if constexpr (UNI) {
+        // cells (0, 1) and (2, 3) in the two lanes of the paired instructions; per
+        // cell: the power, the sink and transient terms, then the normalised
+        // neighbour differences with unnormalised sums, products and accumulation
+        // (as in the per-face form below)
+        float bhv[4];
+        const df2 gx2 = df2_of(gx, gx), gy2 = df2_of(gy, gy), ga2 = df2_of(ga, ga), gb2 = df2_of(gb, gb);
+        const df2 sk2 = df2_of(sk, sk), cd2 = df2_of(cd, cd);
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+          const int k0 = 2 * pr, k1 = 2 * pr + 1;
+          auto pair = [&](const float4& h, const float4& l) {
+            return df2_make(make_float2(cmp(h, k0), cmp(h, k1)), make_float2(cmp(l, k0), cmp(l, k1)));
+          };
+          const df2 t = pair(hc, lc);
+          const df2 tr = pr ? df2_make(make_float2(hc.w, hr1), make_float2(lc.w, lr1))
+                            : df2_make(make_float2(hc.y, hc.z), make_float2(lc.y, lc.z));
+          const df2 tl = pr ? df2_make(make_float2(hc.y, hc.z), make_float2(lc.y, lc.z))
+                            : df2_make(make_float2(hl1, hc.x), make_float2(ll1, lc.x));
+          df2 acc = df2_of(pv[k0], pv[k1]);
+          if (sk.hi != 0.f) acc = ldf2_sub(acc, ldf2_mul(sk2, t));
+          float bh0 = pv[k0].hi, bh1 = pv[k1].hi;
+          if (thn_hi) {
+            acc = ldf2_add(acc, ldf2_mul(cd2, df2_sub(pair(nh, nl), t)));
+            bh0 = __fmaf_rn(cd.hi, cmp(nh, k0), bh0);
+            bh1 = __fmaf_rn(cd.hi, cmp(nh, k1), bh1);
+          }
+          const df2 dx = ldf2_add(df2_sub(t, tr), df2_sub(t, tl));
+          const df2 dy = ldf2_add(df2_sub(t, pair(hu, lu)), df2_sub(t, pair(hd, ld_)));
+          acc = ldf2_sub(acc, ldf2_mul(gx2, dx));
+          acc = ldf2_sub(acc, ldf2_mul(gy2, dy));
+          acc = ldf2_sub(acc, ldf2_mul(ga2, df2_sub(t, pair(ha, la))));
+          acc = ldf2_sub(acc, ldf2_mul(gb2, df2_sub(t, pair(hbz, lbz))));
+          o[k0] = acc.hi.x + acc.lo.x;
+          o[k1] = acc.hi.y + acc.lo.y;
+          bhv[k0] = bh0;
+          bhv[k1] = bh1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          v[0] += o[k] * o[k];
+          v[1] += bhv[k] * bhv[k];
+        }
+      } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const df t = df_make(cmp(hc, k), cmp(lc, k));
@@ -414,26 +460,18 @@ __global__ void __launch_bounds__(TH_BX* TH_BY4, UNI ? 3 : 2)  // layer table: 8
         }
         // the neighbour differences are normalised (their high parts often cancel
         // exactly); the sums, products and the accumulation run unnormalised
-        if (UNI) {
-          const df dx = ldf_add(df_sub(t, tr), df_sub(t, tl));
-          const df dy = ldf_add(df_sub(t, tu), df_sub(t, td));
-          acc = ldf_sub(acc, ldf_mul(gx, dx));
-          acc = ldf_sub(acc, ldf_mul(gy, dy));
-          acc = ldf_sub(acc, ldf_mul(ga, df_sub(t, ta)));
-          acc = ldf_sub(acc, ldf_mul(gb, df_sub(t, tb)));
-        } else {
-          const df gR = df_make(cmp(gxh, k), cmp(gxl_, k));
-          const df gL = (k == 0) ? df_make(gLh, gLl) : df_make(cmp(gxh, k - 1), cmp(gxl_, k - 1));
-          acc = ldf_sub(acc, ldf_mul(gR, df_sub(t, tr)));
-          acc = ldf_sub(acc, ldf_mul(gL, df_sub(t, tl)));
-          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gyh, k), cmp(gyl_, k)), df_sub(t, tu)));
-          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gdh, k), cmp(gdl, k)), df_sub(t, td)));
-          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gah, k), cmp(gal, k)), df_sub(t, ta)));
-          acc = ldf_sub(acc, ldf_mul(df_make(cmp(gbh, k), cmp(gbl, k)), df_sub(t, tb)));
-        }
+        const df gR = df_make(cmp(gxh, k), cmp(gxl_, k));
+        const df gL = (k == 0) ? df_make(gLh, gLl) : df_make(cmp(gxh, k - 1), cmp(gxl_, k - 1));
+        acc = ldf_sub(acc, ldf_mul(gR, df_sub(t, tr)));
+        acc = ldf_sub(acc, ldf_mul(gL, df_sub(t, tl)));
+        acc = ldf_sub(acc, ldf_mul(df_make(cmp(gyh, k), cmp(gyl_, k)), df_sub(t, tu)));
+        acc = ldf_sub(acc, ldf_mul(df_make(cmp(gdh, k), cmp(gdl, k)), df_sub(t, td)));
+        acc = ldf_sub(acc, ldf_mul(df_make(cmp(gah, k), cmp(gal, k)), df_sub(t, ta)));
+        acc = ldf_sub(acc, ldf_mul(df_make(cmp(gbh, k), cmp(gbl, k)), df_sub(t, tb)));
         o[k] = acc.hi + acc.lo;
         v[0] += o[k] * o[k];
         v[1] += bh * bh;
+      }
       }
       st4(r + i, make_float4(o[0], o[1], o[2], o[3]));
       if (ZI >= 0) {
