@@ -4,11 +4,19 @@ The solve path shards by independent problems: every rank runs its own
 trajectories (replicas) or its own share of a batch of stacks, with no data-path
 collective.  Only the timing and the per-instance results are combined: the job
 time is the maximum over ranks, and each rank's results are gathered on the host.
+
+One grid over several ranks is partitioned into y-slabs (all layers of a range of
+rows per rank; the few layers of a stack are never split).  The 7-point product is
+point-wise (Sec. 4.1), so a slab needs only the boundary rows of its two
+y-neighbours: one row per product, and S rows before a chunk of S Chebyshev steps,
+which need no reductions (Sec. 4.3) and so no exchange inside the chunk.  The slab
+helpers below give the rows, halos and exchange plan of that partition.
 """
 from __future__ import annotations
 
-from typing import Callable, Dict, List, Optional
+from typing import Callable, Dict, List, Optional, Tuple
 
+import numpy as np
 import torch
 import torch.distributed as dist
 
@@ -62,3 +70,48 @@ def solve_sharded(n_items: int, solve_shard: Callable[[List[int]], Dict[int, obj
     for p in parts:
         out.update(p or {})
     return out
+
+
+# ---------------------------------------------------------------- y-slab partition
+
+
+def slab_rows(ny: int, rank: int, world: int) -> Tuple[int, int]:
+    """Rows [y0, y1) of this rank's slab (contiguous, balanced; every layer)."""
+    r = shard(ny, rank, world)
+    return r.start, r.stop
+
+
+def slab_halo(ny: int, rank: int, world: int, width: int) -> Tuple[int, int]:
+    """Rows [h0, h1) a slab reads for `width` stencil applications with no exchange
+    in between: its own rows and `width` rows of each y-neighbour (1 for a product,
+    S for a chunk of S Chebyshev steps).  Every slab must be at least `width` rows
+    high, so that a halo comes from the adjacent slab only."""
+    if width < 0:
+        raise ValueError("width >= 0")
+    if world > 1 and min(len(shard(ny, q, world)) for q in range(world)) < width:
+        raise ValueError(f"slabs of {ny} rows over {world} ranks are thinner than a {width}-row halo")
+    y0, y1 = slab_rows(ny, rank, world)
+    return max(0, y0 - width), min(ny, y1 + width)
+
+
+def halo_exchange_plan(ny: int, rank: int, world: int, width: int) -> List[Tuple[int, Tuple[int, int], Tuple[int, int]]]:
+    """This rank's halo exchange before `width` stencil applications: one entry per
+    y-neighbour, (peer, rows sent to it [a, b), rows received from it [c, d)).  What
+    a rank sends to a peer is what that peer receives from it."""
+    h0, h1 = slab_halo(ny, rank, world, width)
+    y0, y1 = slab_rows(ny, rank, world)
+    plan = []
+    if width > 0 and rank > 0:
+        plan.append((rank - 1, (y0, min(y1, y0 + width)), (h0, y0)))
+    if width > 0 and rank + 1 < world:
+        plan.append((rank + 1, (max(y0, y1 - width), y1), (y1, h1)))
+    return plan
+
+
+def slab_cells(nx: int, ny: int, layers: int, a: int, b: int) -> np.ndarray:
+    """Indices i = x + nx (y + ny z) of rows [a, b) in every layer, in the order of
+    the global vector (layer, then row, then column)."""
+    z = np.arange(layers, dtype=np.int64)[:, None, None]
+    y = np.arange(a, b, dtype=np.int64)[None, :, None]
+    x = np.arange(nx, dtype=np.int64)[None, None, :]
+    return (x + nx * (y + ny * z)).reshape(-1)
