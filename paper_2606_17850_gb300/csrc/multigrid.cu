@@ -409,13 +409,23 @@ __global__ void __launch_bounds__(256) k_mg_coarsest(const Ctl* ctl, int n, cons
   mg_coarsest_rows(n, C, b, x, blockIdx.x * nw + (threadIdx.x >> 5), nw * gridDim.x);
 }
 
-// r^T z with FP32 products and FP64 sums, then beta (the preconditioner's dot product)
-__global__ void k_mg_rz(long long n, Ctl* ctl, const float* __restrict__ r, const float* __restrict__ z,
-                        double* partials, int stride, unsigned* counter) {
+// r^T z with FP32 products and FP64 sums, then beta (the preconditioner's dot
+// product); grid-stride over a few resident blocks per SM, so that the last-block
+// reduction sums few partials
+__global__ void __launch_bounds__(256) k_mg_rz(long long n, Ctl* ctl, const float* __restrict__ r,
+                                               const float* __restrict__ z, double* partials, int stride,
+                                               unsigned* counter) {
   if (ld_int(&ctl->done)) return;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long step = (long long)gridDim.x * blockDim.x, t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n4 = n / 4;
+  const float4* r4 = reinterpret_cast<const float4*>(r);
+  const float4* z4p = reinterpret_cast<const float4*>(z);
   float v[1] = {0.f};
-  if (i < n) v[0] = r[i] * z[i];
+  for (long long q = t0; q < n4; q += step) {
+    const float4 a = __ldcg(r4 + q), b = __ldcg(z4p + q);
+    v[0] += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+  }
+  for (long long i = 4 * n4 + t0; i < n; i += step) v[0] += r[i] * z[i];
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
   ctl->rz_next = tot[0];
@@ -811,8 +821,14 @@ th_status mg_vcycle(thermal_grid* g, const float* r, float* z, cudaStream_t s) {
 
 th_status mg_rz(thermal_grid* g, const float* r, const float* z, cudaStream_t s) {
   const long long n = g->n;
-  k_mg_rz<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, g->ctl, r, z, g->partials, g->partials_stride,
-                                                      g->counters);
+  static int sms[64] = {0};
+  int dev = 0;
+  TH_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < 64 && sms[dev] == 0) TH_CUDA(cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev));
+  const long long want = (n / 4 + 255) / 256;
+  const int per = (dev >= 0 && dev < 64 && sms[dev] > 0) ? 4 * sms[dev] : 608;
+  const unsigned nb = (unsigned)std::max(1LL, std::min<long long>(want, std::min(per, g->partials_stride)));
+  k_mg_rz<<<nb, 256, 0, s>>>(n, g->ctl, r, z, g->partials, g->partials_stride, g->counters);
   TH_CHECK_LAUNCH();
   return TH_OK;
 }
