@@ -238,28 +238,33 @@ __global__ void __launch_bounds__(256, 2) k_mg_smooth4(const Ctl* ctl, int nx, i
 
 // b_c = P^T (b - A x) on the vectorised finest level: 4 fine columns give 2 aggregate
 // partial sums per layer; the y pair is summed through shared memory.  Block (32, 8).
+// The column walks its layers keeping the layer below and the current one in
+// registers (one new layer of x per step), and holds every layer's pair sums until a
+// single block barrier, so the layers' loads are not serialised by barriers.
 template <int LMAX>
 __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, int ny, int L,
                                                       const __grid_constant__ MGUni<LMAX> U,
                                                       const float* __restrict__ b, const float* __restrict__ x,
                                                       int nxc, int nyc, float* __restrict__ bc) {
   if (ld_int(&ctl->done)) return;
-  __shared__ float2 rowsum[8][32];
+  __shared__ float2 rowsum[LMAX][8][32];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int x0 = 4 * (blockIdx.x * 32 + tx), y = blockIdx.y * 8 + ty;
   const bool in = x0 < nx && y < ny;
   const long long pxy = (long long)nx * ny;
   const bool hasL = x0 > 0, hasR = x0 + 4 < nx, hasD = y > 0, hasU = y + 1 < ny;
+  if (in) {
+    const long long i0 = (long long)x0 + (long long)nx * y;
+    float4 xbv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 xc = mg_ld4(x + i0);
 #pragma unroll
-  for (int z = 0; z < LMAX; ++z) {
-    if (z >= L) break;
-    float2 r2 = make_float2(0.f, 0.f);
-    if (in) {
-      const long long i = (long long)x0 + (long long)nx * y + pxy * z;
-      const float4 xc = mg_ld4(x + i), bv = mg_ld4(b + i);
+    for (int z = 0; z < LMAX; ++z) {
+      if (z >= L) break;
+      const long long i = i0 + pxy * z;
+      const float4 bv = mg_ld4(b + i);
       const float4 xu = hasU ? mg_ld4(x + i + nx) : xc, xd = hasD ? mg_ld4(x + i - nx) : xc;
       const float4 xa = (z + 1 < L) ? mg_ld4(x + i + pxy) : xc;
-      const float4 xbv = (z > 0) ? mg_ld4(x + i - pxy) : xc;
+      const float4 xbz = (z > 0) ? xbv : xc;
       const float xl = hasL ? x[i - 1] : xc.x, xr = hasR ? x[i + 4] : xc.w;
       const float gx = U.gx[z], gy = U.gy[z], ga = U.gz[z], gbz = z > 0 ? U.gz[z > 0 ? z - 1 : 0] : 0.f;
       float r[4];
@@ -274,22 +279,30 @@ __global__ void __launch_bounds__(256) k_mg_restrict4(const Ctl* ctl, int nx, in
         a += gy * (xi - mg_c4(xu, k));
         a += gy * (xi - mg_c4(xd, k));
         a += ga * (xi - mg_c4(xa, k));
-        a += gbz * (xi - mg_c4(xbv, k));
+        a += gbz * (xi - mg_c4(xbz, k));
         r[k] = mg_c4(bv, k) - a;
       }
-      r2 = make_float2(r[0] + r[1], r[2] + r[3]);
+      rowsum[z][ty][tx] = make_float2(r[0] + r[1], r[2] + r[3]);
+      xbv = xc;
+      xc = xa;
     }
-    rowsum[ty][tx] = r2;
-    __syncthreads();
-    if ((ty & 1) == 0) {
-      const int X0 = x0 >> 1, Y = y >> 1;
-      if (X0 < nxc && Y < nyc) {
-        const float2 a = rowsum[ty][tx], c = rowsum[ty + 1][tx];
+  } else {
+#pragma unroll
+    for (int z = 0; z < LMAX; ++z)
+      if (z < L) rowsum[z][ty][tx] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if ((ty & 1) == 0) {
+    const int X0 = x0 >> 1, Y = y >> 1;
+    if (X0 < nxc && Y < nyc) {
+#pragma unroll
+      for (int z = 0; z < LMAX; ++z) {
+        if (z >= L) break;
+        const float2 a = rowsum[z][ty][tx], c = rowsum[z][ty + 1][tx];
         *reinterpret_cast<float2*>(bc + X0 + (long long)nxc * Y + (long long)nxc * nyc * z) =
             make_float2(a.x + c.x, a.y + c.y);
       }
     }
-    __syncthreads();
   }
 }
 
