@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--degree", type=int, default=24, help="Chebyshev degree k (SpMVs per application)")
+    ap.add_argument("--degree", type=int, default=29, help="Chebyshev degree k (SpMVs per application)")
     ap.add_argument("--guess", type=int, default=3,
                     help="transient initial guess: 0 previous step (the paper's warm start), "
                          "1 linear extrapolation from the two previous steps, 2 quadratic from three, "

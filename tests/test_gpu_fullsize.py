@@ -1,5 +1,5 @@
 """The bench workload at full size (1024 x 1024 x 8, 8.4M unknowns), in the launch
-configuration bench.py times (mixed FP32/FP64, Chebyshev degree 24 in fused 4-step
+configuration bench.py times (mixed FP32/FP64, Chebyshev degree 29 in fused 4-step
 chunks, inner tolerance 1e-4, cubic extrapolated guess, CUDA graph).
 
 The oracle solves the first three backward-Euler steps of the workload exactly
@@ -39,7 +39,7 @@ def setup():
 
 def test_fullsize_first_steps_match_oracle(setup):
     """Steps 1-3 of the 100-step workload in the bench's configuration (tol 1e-8,
-    degree 24 in fused chunks, inner tolerance 1e-4, cubic extrapolated guess, CUDA
+    degree 29 in fused chunks, inner tolerance 1e-4, cubic extrapolated guess, CUDA
     graph) against the oracle's exact backward-Euler steps."""
     inst, g, A = setup
     st = inst.stack
@@ -53,7 +53,7 @@ def test_fullsize_first_steps_match_oracle(setup):
     report = []
     for n_steps in (1, 2, 3):
         T = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
-        _, stats = g.run_transient(maps, 25, n_steps, DT, T, precision="mixed", precond="cheb", cheb_degree=24,
+        _, stats = g.run_transient(maps, 25, n_steps, DT, T, precision="mixed", precond="cheb", cheb_degree=29,
                                    inner_tol=1e-4, tol_rel=1e-8, guess=3, use_graph=1)
         Th = T.cpu().numpy()
         err = osolve.rise_relative_error(Th, T_ref[n_steps - 1], st.t_amb)
@@ -74,7 +74,7 @@ def test_fullsize_steps_residual_and_energy(setup):
     for s in range(3):
         P = maps[s % 4]
         T, stats = g.run_transient([torch.from_numpy(P).cuda()], 25, 1, DT, T, precision="mixed",
-                                   precond="cheb", cheb_degree=24, inner_tol=1e-4, tol_rel=1e-8, use_graph=1)
+                                   precond="cheb", cheb_degree=29, inner_tol=1e-4, tol_rel=1e-8, use_graph=1)
         Th = T.cpu().numpy()
         b = disc.rhs_transient(NX, NY, st, P.astype(np.float64), prev, DT)
         rel = osolve.rel_residual(A, Th, b, st.t_amb)
@@ -92,7 +92,7 @@ def test_fullsize_mixed_matches_fp64_path(setup):
     Td = Tm.clone()
     # the bench's configuration (cubic extrapolation over the 12 steps, maps switching
     # every 4) against the plain FP64 path warm-started from the previous step
-    g.run_transient(maps, 4, 12, DT, Tm, precision="mixed", cheb_degree=24, inner_tol=1e-4, guess=3, tol_rel=1e-10,
+    g.run_transient(maps, 4, 12, DT, Tm, precision="mixed", cheb_degree=29, inner_tol=1e-4, guess=3, tol_rel=1e-10,
                     use_graph=1)
     g.run_transient(maps, 4, 12, DT, Td, precision="fp64", cheb_degree=6, guess=0, tol_rel=1e-10, use_graph=1)
     rise = (Td - st.t_amb).abs().max().item()
