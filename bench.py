@@ -84,6 +84,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=29, help="Chebyshev degree k (SpMVs per application)")
+    ap.add_argument("--fp64-degree", type=int, default=10,
+                    help="Chebyshev degree of the plain FP64 comparison arm (its own best, measured)")
+    ap.add_argument("--adaptive-degree", type=int, default=6,
+                    help="Chebyshev degree of the paper's adaptive scheme (its own best, measured)")
     ap.add_argument("--guess", type=int, default=3,
                     help="transient initial guess: 0 previous step (the paper's warm start), "
                          "1 linear extrapolation from the two previous steps, 2 quadratic from three, "
@@ -416,7 +420,7 @@ def main():
 
     # plain FP64 GPU path on the same trajectory (the baseline the metric compares against)
     if not args.no_fp64:
-        o64 = dict(opts, precision="fp64")
+        o64 = dict(opts, precision="fp64", cheb_degree=args.fp64_degree)
         T64 = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
         trajectory(o64, T64, maps)  # warm-up (graph build)
         barrier()
@@ -428,14 +432,15 @@ def main():
         rise = (T64 - st.t_amb).abs().max().item()
         err = (T_mixed - T64).abs().max().item() / rise
         result["fp64_gpu"] = {"value": ms64 / nsteps, "unit": UNIT, "ms_per_trajectory": ms64,
-                              "inner_it": s64["inner_it"], "final_rel_res": s64["rel_res"]}
+                              "inner_it": s64["inner_it"], "final_rel_res": s64["rel_res"],
+                              "cheb_degree": args.fp64_degree}
         result["speedup_mixed_vs_fp64"] = (ms64 / nsteps) / value
         result["accuracy"] = {"max_abs_diff_mixed_vs_fp64_K": err * rise,
                               "max_rel_diff_vs_rise": err}
 
     # the paper's adaptive mixed-precision PCG (stage switch + hot restart) on the same trajectory
     if not args.no_adaptive:
-        oad = dict(opts, precision="adaptive")
+        oad = dict(opts, precision="adaptive", cheb_degree=args.adaptive_degree)
         Tad = torch.full((inst.n,), st.t_amb, dtype=torch.float64, device="cuda")
         trajectory(oad, Tad, maps)  # warm-up (graph build)
         barrier()
@@ -448,6 +453,7 @@ def main():
         result["adaptive_gpu"] = {
             "value": msad / nsteps, "unit": UNIT, "ms_per_trajectory": msad, "inner_it": sad["inner_it"],
             "stage_switches": sad["stage_switches"], "final_rel_res": sad["rel_res"],
+            "cheb_degree": args.adaptive_degree,
             "max_abs_diff_vs_mixed_K": (Tad - T_mixed).abs().max().item(),
             "note": "FP64 PCG, early stage FP64/32 SpMV, late stage FP64 SpMV (switch on Eqs. switch_a-c, hot "
                     "restart), Chebyshev preconditioner in FP32 with the FP32/16 product of Algorithm 3"}
