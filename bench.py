@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--degree", type=int, default=29, help="Chebyshev degree k (SpMVs per application)")
     ap.add_argument("--fp64-degree", type=int, default=10,
                     help="Chebyshev degree of the plain FP64 comparison arm (its own best, measured)")
+    ap.add_argument("--faces-degree", type=int, default=0,
+                    help="Chebyshev degree of the per-face trajectory (0: the headline's)")
     ap.add_argument("--adaptive-degree", type=int, default=6,
                     help="Chebyshev degree of the paper's adaptive scheme (its own best, measured)")
     ap.add_argument("--guess", type=int, default=3,
@@ -488,7 +490,9 @@ def main():
     if not args.no_ablation:
         result["spmv_ablation"] = ablation_section(grid, inst.n, args.reps, result.get("kernels"), peak)
     if not args.no_faces:
-        result["per_face"] = faces_section(opts, maps, nsteps, st, value, T_mixed)
+        fo = dict(opts, cheb_degree=args.faces_degree) if args.faces_degree > 0 else opts
+        result["per_face"] = faces_section(fo, maps, nsteps, st, value, T_mixed)
+        result["per_face"]["cheb_degree"] = fo["cheb_degree"]
     if not args.no_precond:
         result["preconditioners"] = precond_section(args, opts, trajectory, maps, nsteps, st)
     if not args.no_batched:
