@@ -115,6 +115,10 @@ typedef struct thermal_solve_opts {
                        /* completes, so its bounded wait runs out after 2 ms and the solve   */
                        /* ends with TH_ECUDA ("device wait timed out"); the grid stays usable */
   int reserved[3];
+  double cheb_lam_min; /* Chebyshev interval [cheb_lam_min, cheb_lam_max] of the (scaled)      */
+  double cheb_lam_max; /* operator instead of the Lanczos estimate, when both are set (0 < min */
+                       /* < max; both 0: the estimate).  Ranks that solve one grid by slabs    */
+                       /* must share the whole grid's interval: a slab's own would differ (0) */
 } thermal_solve_opts;
 
 typedef struct thermal_solve_stats {
@@ -238,7 +242,8 @@ th_status thermal_csr_spmv(thermal_grid* g, int variant, int precision, double d
 /*
  * z = M^{-1} r for the preconditioner selected by opts (precond, cheb_degree,
  * cheb_scaled, lanczos_steps), in FP32 (r, z: device float, n_cells).  For
- * TH_PC_CHEB the spectral interval is estimated first (cached per grid and dt).
+ * TH_PC_CHEB the spectral interval is estimated first (cached per grid and dt), unless
+ * opts->cheb_lam_min / cheb_lam_max fix it.
  */
 th_status thermal_precond_apply(thermal_grid* g, double dt, const thermal_solve_opts* opts,
                                 const float* r, float* z, void* stream);
@@ -251,7 +256,8 @@ th_status thermal_precond_apply(thermal_grid* g, double dt, const thermal_solve_
  * [lam_min, lam_max] the preconditioner uses: lam_max = 1.05 * ritz_max,
  * lam_min = max(ritz_min, 1e-7 * lam_max).  The start vector is SplitMix64
  * (Steele, Lea, Flood 2014): element i uses state 0x5EED + (i+1)*0x9E3779B97F4A7C15,
- * its top 53 bits scaled to [0, 1) and mapped to [-1, 1).  Synchronous.
+ * its top 53 bits scaled to [0, 1) and mapped to [-1, 1).  Synchronous.  Always
+ * the estimate: opts->cheb_lam_min / cheb_lam_max are ignored here.
  */
 th_status thermal_spectral_bounds(thermal_grid* g, double dt, const thermal_solve_opts* opts,
                                   double* ritz_min, double* ritz_max, double* lam_min,

@@ -39,6 +39,8 @@ class SolveOpts(C.Structure):
         ("ad_check", C.c_int),
         ("test_wait_expire", C.c_int),
         ("reserved", C.c_int * 3),
+        ("cheb_lam_min", C.c_double),
+        ("cheb_lam_max", C.c_double),
     ]
 
 

@@ -74,6 +74,11 @@ th_status validate_opts(const thermal_solve_opts* o) {
     return th_fail(TH_EINVAL, "unknown preconditioner %d", o->precond);
   if (o->precond == TH_PC_CHEB && (o->cheb_degree < 1 || o->cheb_degree > 1000))
     return th_fail(TH_EINVAL, "cheb_degree must lie in [1, 1000]");
+  if (o->cheb_lam_min != 0.0 || o->cheb_lam_max != 0.0) {
+    if (!std::isfinite(o->cheb_lam_min) || !std::isfinite(o->cheb_lam_max) || !(o->cheb_lam_min > 0.0) ||
+        !(o->cheb_lam_max > o->cheb_lam_min))
+      return th_fail(TH_EINVAL, "cheb_lam_min / cheb_lam_max: both 0, or 0 < min < max");
+  }
   if (o->precond == TH_PC_CHEB && (o->lanczos_steps < 2 || o->lanczos_steps > 1000))
     return th_fail(TH_EINVAL, "lanczos_steps must lie in [2, 1000]");
   if (o->cheb_fuse < 0 || o->cheb_fuse > 4) return th_fail(TH_EINVAL, "cheb_fuse must lie in [0, 4]");

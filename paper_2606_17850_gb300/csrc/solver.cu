@@ -129,6 +129,13 @@ th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* 
                           double* lmin, double* lmax, cudaStream_t s) {
   TH_TRY(grid_ensure_tab(g, dt, s));
   TH_TRY(grid_ensure_workspace(g, false, s));
+  if (o->cheb_lam_max > 0.0) {  // the caller's interval (validated: 0 < min < max)
+    if (rmin) *rmin = o->cheb_lam_min;
+    if (rmax) *rmax = o->cheb_lam_max;
+    if (lmin) *lmin = o->cheb_lam_min;
+    if (lmax) *lmax = o->cheb_lam_max;
+    return TH_OK;
+  }
   const int m = std::min(o->lanczos_steps, 500);
   const LanczosKey key{dt > 0 ? dt : 0.0, o->cheb_scaled ? 1 : 0, m};
   double ra, rb;
@@ -1069,10 +1076,11 @@ static th_status enq_step_copy(const Plan& P, cudaStream_t st) {
 struct GraphKey {
   int kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, expire;
   double dt;
+  double lam_min, lam_max;  // a caller's Chebyshev interval (its coefficients are baked in)
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, expire, dt) <
+    return std::tie(kind, prec, pc, k, scaled, pdtype, lz, extrap, fuse, ad_pairs, expire, dt, lam_min, lam_max) <
            std::tie(o.kind, o.prec, o.pc, o.k, o.scaled, o.pdtype, o.lz, o.extrap, o.fuse, o.ad_pairs, o.expire,
-                    o.dt);
+                    o.dt, o.lam_min, o.lam_max);
   }
 };
 struct GraphEntry {
@@ -1446,7 +1454,8 @@ th_status solver_drive(thermal_grid* g, int kind, double dt, const void* const* 
   TH_CUDA(cudaEventRecord(e0, s));
   if (o->use_graph) {
     const GraphKey key{kind,   P.prec, P.pc, P.k, P.scaled, pdtype, o->lanczos_steps, P.extrap ? P.extrap_order : 0,
-                       o->cheb_fuse, P.ad ? P.ad_pairs : 0, P.expire_test, P.transient ? dt : 0.0};
+                       o->cheb_fuse, P.ad ? P.ad_pairs : 0, P.expire_test, P.transient ? dt : 0.0,
+                       o->cheb_lam_min, o->cheb_lam_max};
     if (!g->graphs) {
       g->graphs = new GraphCache();
       for (auto& sx : g->graphs->cs) TH_CUDA(cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking));
@@ -1567,7 +1576,9 @@ extern "C" th_status thermal_spectral_bounds(thermal_grid* g, double dt, const t
   if (!g) return th_fail(TH_EINVAL, "grid is NULL");
   TH_TRY(validate_opts(opts));
   if (opts->lanczos_steps > 500) return th_fail(TH_EINVAL, "lanczos_steps must be <= 500");
-  return solver_spectral(g, dt, opts, ritz_min, ritz_max, lam_min, lam_max, (cudaStream_t)stream);
+  thermal_solve_opts est = *opts;  // this call reports the estimate, whatever interval opts fixes
+  est.cheb_lam_min = est.cheb_lam_max = 0.0;
+  return solver_spectral(g, dt, &est, ritz_min, ritz_max, lam_min, lam_max, (cudaStream_t)stream);
   ABI_END
 }
 

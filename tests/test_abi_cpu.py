@@ -121,6 +121,18 @@ def test_empty_and_negative_batches(lib):
     assert lib.thermal_solve_batched(None, 0, None, _lib.TH_F64, None, C.byref(o), None, None) == _lib.TH_EINVAL
 
 
+def test_chebyshev_interval_option_validation(lib):
+    """A fixed Chebyshev interval must be both 0 (the Lanczos estimate) or 0 < min < max,
+    finite; anything else is rejected before any device work."""
+    from paper_2606_17850_gb300 import _lib
+    for lo, hi, ok in ((0.0, 0.0, True), (1e-3, 2.0, True), (0.0, 2.0, False), (1e-3, 0.0, False),
+                       (2.0, 1.0, False), (-1.0, 2.0, False), (1e-3, float("inf"), False),
+                       (float("nan"), 2.0, False)):
+        o = _lib.default_opts(cheb_lam_min=lo, cheb_lam_max=hi)
+        st = lib.thermal_solve_batched(None, 0, None, _lib.TH_F64, None, C.byref(o), None, None)
+        assert st == (_lib.TH_OK if ok else _lib.TH_EINVAL), (lo, hi)
+
+
 def test_noalloc_rejects_before_any_device_work(lib):
     """The allocation-free product checks sizes, NULLs and x/y overlap on the host
     before it looks up its scratch or launches anything (placeholder addresses here

@@ -336,6 +336,34 @@ def test_fused_chebyshev_per_face_equals_stepwise(k, dt, mk):
         assert (zf - z1).abs().max().item() <= 1e-6 * scale, fuse
 
 
+@pytest.mark.parametrize("k", [5, 9])
+def test_fused_chebyshev_on_slabs_with_halo(k):
+    """The one-grid multi-GPU partition on one GPU: each y-slab of a grid with a halo,
+    run as a grid of its own through the fused chunks (k - 1 steps: one chunk at
+    k = 5, two at k = 9) with the whole grid's spectral interval, gives the whole
+    grid's preconditioned vector on the slab's rows bit for bit.  The halo rows absorb
+    the sub-grid's artificial edge: k - 1 rows for the steps' reach, plus one because
+    the edge row takes a boundary cell's diagonal in z_1 = D^-1 r / theta (a slab
+    kernel given the whole grid's diagonal needs only the k - 1)."""
+    from paper_2606_17850_gb300.dist import slab_cells, slab_halo, slab_rows
+    st = ti.stack_c2()
+    nx, ny, dt, world = 64, 50, 1e-4, 3
+    g = grid_of(nx, ny, st)
+    _, _, lmin, lmax = g.spectral_bounds(dt)
+    r = ti.random_vector(nx * ny * st.L, 12).astype(np.float32)
+    opts = dict(precond="cheb", cheb_degree=k, cheb_lam_min=lmin, cheb_lam_max=lmax)
+    z = g.precond(cuda(r), dt, **opts).cpu().numpy()
+    for q in range(world):
+        y0, y1 = slab_rows(ny, q, world)
+        h0, h1 = slab_halo(ny, q, world, k)
+        ext = slab_cells(nx, ny, st.L, h0, h1)
+        own = slab_cells(nx, ny, st.L, y0, y1)
+        gs = grid_of(nx, h1 - h0, st)
+        zs = gs.precond(cuda(r[ext]), dt, **opts).cpu().numpy()
+        assert np.array_equal(zs[np.searchsorted(ext, own)], z[own]), q
+        gs.close()
+
+
 def test_fused_chebyshev_per_face_matches_oracle():
     """The per-face fused preconditioner against the oracle's Chebyshev algorithm on
     the assembled per-cell-conductivity matrix (same spectral interval)."""
