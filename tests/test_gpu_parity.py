@@ -353,6 +353,11 @@ def test_fused_chebyshev_on_slabs_with_halo(k):
     r = ti.random_vector(nx * ny * st.L, 12).astype(np.float32)
     opts = dict(precond="cheb", cheb_degree=k, cheb_lam_min=lmin, cheb_lam_max=lmax)
     z = g.precond(cuda(r), dt, **opts).cpu().numpy()
+    # the fixed interval equal to the estimate gives the default result; the estimate
+    # call itself ignores a fixed interval
+    z0 = g.precond(cuda(r), dt, precond="cheb", cheb_degree=k).cpu().numpy()
+    assert np.array_equal(z, z0)
+    assert g.spectral_bounds(dt, cheb_lam_min=1.0, cheb_lam_max=2.0)[2:] == (lmin, lmax)
     for q in range(world):
         y0, y1 = slab_rows(ny, q, world)
         h0, h1 = slab_halo(ny, q, world, k)
