@@ -313,6 +313,18 @@ __device__ __forceinline__ Cell cell_of(const Dims& d) {
   return c;
 }
 
+// the cell of linear index i (grid-stride loops over all cells)
+__device__ __forceinline__ Cell cell_at(const Dims& d, long long i) {
+  Cell c;
+  c.z = (int)(i / d.pxy);
+  const long long r = i - (long long)c.z * d.pxy;
+  c.y = (int)(r / d.nx);
+  c.x = (int)(r - (long long)c.y * d.nx);
+  c.i = i;
+  c.valid = true;
+  return c;
+}
+
 // (A v)_i in difference form and the diagonal A_ii.  `val(j)` returns v_j as TA.
 template <typename TA, typename TC, typename F>
 __device__ __forceinline__ TA stencil_row(const TC* __restrict__ gx, const TC* __restrict__ gy,

@@ -503,14 +503,16 @@ __device__ __forceinline__ double splitmix_uniform(unsigned long long seed, long
 }
 
 // w = start vector; nrm[0] = ||w||.   lz layout: alpha[0..511], nrm[512..1023]
+// The Lanczos kernels walk all cells grid-stride over a few resident blocks per SM,
+// so that their last-block reductions sum few partials.
 __global__ void k_lz_start(Dims d, Ctl* ctl, float* __restrict__ w, unsigned long long seed, double* lz,
                            double* partials, int stride, unsigned* counter) {
-  const Cell c = cell_of(d);
   float v[1] = {0.f};
-  if (c.valid) {
-    const float wi = (float)splitmix_uniform(seed, c.i);
-    w[c.i] = wi;
-    v[0] = wi * wi;
+  const long long step = (long long)gridDim.x * block_threads();
+  for (long long i = (long long)blockIdx.x * block_threads() + thread_linear_id(); i < d.n; i += step) {
+    const float wi = (float)splitmix_uniform(seed, i);
+    w[i] = wi;
+    v[0] += wi * wi;
   }
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
@@ -528,10 +530,11 @@ __global__ void k_lz_spmv(Dims d, Ctl* ctl, const float* __restrict__ gx, const 
                           const float* __restrict__ gz, const LayerTab* tab, const float* __restrict__ isq,
                           const float* __restrict__ w, float* __restrict__ vj, float* __restrict__ u, double* lz,
                           int j, double* partials, int stride, unsigned* counter) {
-  const Cell c = cell_of(d);
   const float inv = __ldcg((const float*)(lz + 3072) + 512 + j);
   float v[1] = {0.f};
-  if (c.valid) {
+  const long long step = (long long)gridDim.x * block_threads();
+  for (long long ii = (long long)blockIdx.x * block_threads() + thread_linear_id(); ii < d.n; ii += step) {
+    const Cell c = cell_at(d, ii);
     auto val = [&](long long k) -> float {
       const float vk = w[k] * inv;
       return SCALED ? vk * isq[k] : vk;
@@ -542,7 +545,7 @@ __global__ void k_lz_spmv(Dims d, Ctl* ctl, const float* __restrict__ gx, const 
     if (SCALED) ai *= isq[c.i];
     vj[c.i] = vi;
     u[c.i] = ai;
-    v[0] = vi * ai;
+    v[0] += vi * ai;
   }
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;
@@ -555,16 +558,16 @@ __global__ void k_lz_spmv(Dims d, Ctl* ctl, const float* __restrict__ gx, const 
 __global__ void k_lz_update(Dims d, Ctl* ctl, const float* __restrict__ u, const float* __restrict__ vj,
                             const float* __restrict__ vprev, float* __restrict__ w, double* lz, int j,
                             double* partials, int stride, unsigned* counter) {
-  const Cell c = cell_of(d);
   const float* lzf = (const float*)(lz + 3072);
   const float a = __ldcg(lzf + j);
   const float b = __ldcg(lzf + 1024 + j);
   float v[1] = {0.f};
-  if (c.valid) {
-    float wi = u[c.i] - a * vj[c.i];
-    if (vprev) wi -= b * vprev[c.i];
-    w[c.i] = wi;
-    v[0] = wi * wi;
+  const long long step = (long long)gridDim.x * block_threads();
+  for (long long i = (long long)blockIdx.x * block_threads() + thread_linear_id(); i < d.n; i += step) {
+    float wi = u[i] - a * vj[i];
+    if (vprev) wi -= b * vprev[i];
+    w[i] = wi;
+    v[0] += wi * wi;
   }
   double tot[1];
   if (!grid_reduce<float, 1>(v, partials, stride, counter, tot)) return;

@@ -125,6 +125,8 @@ static void tridiag_extremes(const std::vector<double>& a, const std::vector<dou
 
 // ------------------------------------------------------------------ Lanczos
 
+static int sm_count();
+
 th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* o, double* rmin, double* rmax,
                           double* lmin, double* lmax, cudaStream_t s) {
   TH_TRY(grid_ensure_tab(g, dt, s));
@@ -145,7 +147,10 @@ th_status solver_spectral(thermal_grid* g, double dt, const thermal_solve_opts* 
     rb = it->second.ritz_max;
   } else {
     const Dims d = grid_dims(g);
-    const dim3 gb = grid_blocks(g), tb(TH_BX, TH_BY);
+    // grid-stride over four blocks per SM (few partials for the reductions)
+    const long long want = (d.n + TH_BX * TH_BY - 1) / (TH_BX * TH_BY);
+    const dim3 gb((unsigned)std::max(1LL, std::min<long long>(want, std::min(4 * sm_count(), g->partials_stride)))),
+        tb(TH_BX, TH_BY);
     float* w = g->zc32[0];
     float* u = g->zc32[1];
     float* vb[2] = {g->zc32[2], g->mu32};
