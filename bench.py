@@ -594,7 +594,7 @@ def precond_section(args, opts, trajectory, maps, nsteps, st):
     P2 = torch.from_numpy(c2.power).cuda()
     for name, o in (("cheb30", dict(precond="cheb", cheb_degree=30)), ("cheb20", dict(precond="cheb", cheb_degree=20)),
                     ("mg", dict(precond="mg")), ("jacobi", dict(precond="jacobi"))):
-        oo = dict(o, tol_rel=1e-8, inner_tol=args.inner_tol)
+        oo = dict(o, tol_rel=1e-8, inner_tol=args.inner_tol, use_graph=1)  # every arm in a CUDA graph
         g2.solve_steady(P2, **oo)  # set-up (Lanczos / hierarchy, graph)
         ms, (T, stt) = _event_ms(lambda: g2.solve_steady(P2, **oo), reps=2)
         out[f"steady_512x512x8_{name}"] = {"ms": ms, "inner_it": stt["inner_it"], "outer_it": stt["outer_it"],
@@ -678,19 +678,18 @@ def adjoint_section(args):
     layers = inst.stack.power_layers()
 
     def run(o):
-        T, _ = g.solve_steady(P, **o)  # set-up (spectral bounds or the multigrid hierarchy)
-
         def one():
             T, s1 = g.solve_steady(P, **o)
             J, w = g.hotspot_lse(T, layers, 2.0)
             dP, dk, s2 = g.grad(T, w, dJdP_dtype=torch.float32, **o)
             return s1, s2, J
 
+        one()  # set-up (spectral bounds or the multigrid hierarchy, the graphs of both solves)
         return _event_ms(one, reps=1)
 
     # steady solves of this stack converge fastest with the multigrid preconditioner
-    ms, (s1, s2, J) = run(dict(precision="mixed", precond="mg", tol_rel=1e-8))
-    ms_cheb, (c1, c2, _) = run(dict(precision="mixed", precond="cheb", cheb_degree=30, tol_rel=1e-8))
+    ms, (s1, s2, J) = run(dict(precision="mixed", precond="mg", tol_rel=1e-8, use_graph=1))
+    ms_cheb, (c1, c2, _) = run(dict(precision="mixed", precond="cheb", cheb_degree=30, tol_rel=1e-8, use_graph=1))
     return {"workload": "2048x2048x10 memory-on-logic stack, forward solve + LSE + adjoint gradient",
             "unknowns": inst.n, "preconditioner": "multigrid V-cycle", "ms_forward_plus_gradient": ms, "J": J,
             "forward_inner_it": s1["inner_it"], "adjoint_inner_it": s2["inner_it"],
